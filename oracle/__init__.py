@@ -1,0 +1,283 @@
+"""FP64 CPU oracle for the importance-sampling shape-overlap estimator.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``; never by the product package. It
+shares no code with the CUDA library (its C source ``oracle.c`` is written
+independently from the paper's equations and the written stream/sampler
+conventions listed at the top of that file).
+
+Pins (``tests/test_oracle_*.py``): Philox words against an independent
+Philox4x32-10 (Triton's CPU interpreter), alias-table mass invariants and
+pick frequencies, sampler moments, the first-order closed form (Eq. fo),
+hard-sphere single-atom volumes (Eq. occ with lambda = 1 and its p = 2 sqrt 2
+counterpart), full inclusion-exclusion (Eq. incexc) against grid quadrature,
+and the IS estimators within 3 SE of those exact values.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+SYMMETRIC = 1
+ANTITHETIC = 2
+TAG_AB, TAG_BA, TAG_SELF = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (gcc, -O2, OpenMP, strict IEEE double)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp",
+                               "-shared", "-fPIC", "-o", tmp, src, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _Set(ctypes.Structure):
+    _fields_ = [("xyz", ctypes.c_void_p), ("radius", ctypes.c_void_p), ("height", ctypes.c_void_p),
+                ("offsets", ctypes.c_void_p), ("n_mol", ctypes.c_int32), ("c_alpha", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "orc_philox4x32_10": [_P, _P, _P],
+    "orc_normal_pair": [ctypes.c_uint32, ctypes.c_uint32, _P],
+    "orc_alias_build": [ctypes.c_int, _P, _P, _P, _P],
+    "orc_mol_tables": [_P, ctypes.c_int32, _P, _P, _P, _P, _P],
+    "orc_draw": [_P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                 ctypes.c_int64, ctypes.c_int, _P, _P],
+    "orc_occupancy": [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, _P, _P],
+    "orc_direction_sums": [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_uint64,
+                           ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _P, _P],
+    "orc_overlap_estimate": [_P, _P, _P, _P, ctypes.c_int64, _P, ctypes.c_uint64, ctypes.c_uint64,
+                             ctypes.c_uint32, ctypes.c_uint32, _P, _P, ctypes.c_int],
+    "orc_union_volume_estimate": [_P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
+                                  ctypes.c_uint32, ctypes.c_uint32, _P, _P, _P, _P, ctypes.c_int],
+    "orc_fo_overlap": [_P, _P, _P, _P, ctypes.c_int64, _P, _P, ctypes.c_int],
+    "orc_mixture_mass": [_P, _P, ctypes.c_int64, _P],
+    "orc_union_volume_ie": [_P, ctypes.c_int32, _P],
+    "orc_union_overlap_ie": [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, ctypes.c_int],
+    "orc_grid": [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_double, ctypes.c_double, _P,
+                 ctypes.c_int],
+    "orc_tanimoto_pairs": [_P, _P, _P, _P, _P, ctypes.c_int64, _P, _P, ctypes.c_uint64,
+                           ctypes.c_uint32, ctypes.c_uint32, _P, _P, _P, _P, ctypes.c_int],
+}
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int if name != "orc_philox4x32_10" else None
+        L.orc_normal_pair.restype = None
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError(f"{what} failed with status {rc}")
+
+
+class OSet:
+    """Keeps host arrays of a molecule set alive for the C oracle."""
+
+    def __init__(self, ms, c_alpha: float = 2.41798793):
+        self.xyz = np.ascontiguousarray(ms.xyz, dtype=np.float32)
+        self.radius = np.ascontiguousarray(ms.radius, dtype=np.float32)
+        self.height = None if ms.height is None else np.ascontiguousarray(ms.height, dtype=np.float32)
+        self.offsets = np.ascontiguousarray(ms.offsets, dtype=np.int32)
+        self.s = _Set(self.xyz.ctypes.data, self.radius.ctypes.data, _ptr(self.height),
+                      self.offsets.ctypes.data, len(self.offsets) - 1, c_alpha)
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.s)
+
+    @property
+    def n_mol(self):
+        return len(self.offsets) - 1
+
+
+def _oset(ms, c_alpha=2.41798793):
+    return ms if isinstance(ms, OSet) else OSet(ms, c_alpha)
+
+
+# ---------------------------------------------------------------- primitives
+
+def philox(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.empty(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(c.ctypes.data, k.ctypes.data, out.ctypes.data)
+    return out
+
+
+def normal_pair(a: int, b: int) -> np.ndarray:
+    out = np.empty(2, dtype=np.float64)
+    lib().orc_normal_pair(a, b, out.ctypes.data)
+    return out
+
+
+def alias_build(v):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    n = len(v)
+    thr = np.empty(n, np.uint32)
+    al = np.empty(n, np.uint8)
+    mass = np.empty(n, np.uint64)
+    _check(lib().orc_alias_build(n, v.ctypes.data, thr.ctypes.data, al.ctypes.data, mass.ctypes.data),
+           "alias_build")
+    return thr, al, mass
+
+
+def mol_tables(ms, idx, c_alpha=2.41798793):
+    s = _oset(ms, c_alpha)
+    n = int(s.offsets[idx + 1] - s.offsets[idx])
+    alpha, v = np.empty(n), np.empty(n)
+    Z = ctypes.c_double()
+    thr, al = np.empty(n, np.uint32), np.empty(n, np.uint8)
+    _check(lib().orc_mol_tables(s.ref, idx, alpha.ctypes.data, v.ctypes.data, ctypes.addressof(Z),
+                                thr.ctypes.data, al.ctypes.data), "mol_tables")
+    return dict(alpha=alpha, v=v, Z=Z.value, thr=thr, alias=al)
+
+
+def draw(ms, idx, seed, stream, tag, n, antithetic=False, c_alpha=2.41798793):
+    s = _oset(ms, c_alpha)
+    r = np.empty((n, 3))
+    comp = np.empty(n, np.int32)
+    _check(lib().orc_draw(s.ref, idx, seed, stream, tag, n, int(antithetic), r.ctypes.data,
+                          comp.ctypes.data), "draw")
+    return r, comp
+
+
+def occupancy(ms, idx, r, pose=None, c_alpha=2.41798793):
+    s = _oset(ms, c_alpha)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    n = len(r)
+    m, u = np.empty(n), np.empty(n)
+    p = None if pose is None else np.ascontiguousarray(pose, dtype=np.float32)
+    _check(lib().orc_occupancy(s.ref, idx, _ptr(p), n, r.ctypes.data, m.ctypes.data, u.ctypes.data),
+           "occupancy")
+    return m, u
+
+
+def direction_sums(A, ia, B, ib, seed, stream, tag, n, flags=0, poseB=None, c_alpha=2.41798793):
+    sa, sb = _oset(A, c_alpha), _oset(B, c_alpha)
+    sums = np.empty(4)
+    ne = ctypes.c_double()
+    p = None if poseB is None else np.ascontiguousarray(poseB, dtype=np.float32)
+    _check(lib().orc_direction_sums(sa.ref, ia, sb.ref, ib, _ptr(p), seed, stream, tag, n, flags,
+                                    sums.ctypes.data, ctypes.addressof(ne)), "direction_sums")
+    return sums, ne.value
+
+
+# ---------------------------------------------------------------- estimators
+
+def overlap_estimate(A, ia, B, ib, seed, n, flags=SYMMETRIC, stream_base=0, poses=None,
+                     n_threads=0, c_alpha=2.41798793):
+    """est[n_pairs, 2], se[n_pairs, 2]: slot 0 first order, slot 1 union."""
+    sa, sb = _oset(A, c_alpha), _oset(B, c_alpha)
+    ia = np.ascontiguousarray(ia, dtype=np.int32)
+    ib = np.ascontiguousarray(ib, dtype=np.int32)
+    npairs = len(ia)
+    est, se = np.empty((npairs, 2)), np.empty((npairs, 2))
+    p = None if poses is None else np.ascontiguousarray(poses, dtype=np.float32)
+    _check(lib().orc_overlap_estimate(sa.ref, ia.ctypes.data, sb.ref, ib.ctypes.data, npairs, _ptr(p),
+                                      seed, stream_base, n, flags, est.ctypes.data, se.ctypes.data,
+                                      n_threads), "overlap_estimate")
+    return est, se
+
+
+def union_volume_estimate(S, idx, seed, n, flags=0, stream_base=0, n_threads=0, c_alpha=2.41798793):
+    """(vol, vol_se, self_overlap, self_se), each [len(idx)]."""
+    s = _oset(S, c_alpha)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    k = len(idx)
+    v, vs, so, ss = np.empty(k), np.empty(k), np.empty(k), np.empty(k)
+    _check(lib().orc_union_volume_estimate(s.ref, idx.ctypes.data, k, seed, stream_base, n, flags,
+                                           v.ctypes.data, vs.ctypes.data, so.ctypes.data,
+                                           ss.ctypes.data, n_threads), "union_volume_estimate")
+    return v, vs, so, ss
+
+
+def fo_overlap(A, ia, B, ib, poses=None, n_threads=0, c_alpha=2.41798793):
+    sa, sb = _oset(A, c_alpha), _oset(B, c_alpha)
+    ia = np.ascontiguousarray(ia, dtype=np.int32)
+    ib = np.ascontiguousarray(ib, dtype=np.int32)
+    out = np.empty(len(ia))
+    p = None if poses is None else np.ascontiguousarray(poses, dtype=np.float32)
+    _check(lib().orc_fo_overlap(sa.ref, ia.ctypes.data, sb.ref, ib.ctypes.data, len(ia), _ptr(p),
+                                out.ctypes.data, n_threads), "fo_overlap")
+    return out
+
+
+def mixture_mass(S, idx=None, c_alpha=2.41798793):
+    s = _oset(S, c_alpha)
+    if idx is None:
+        idx = np.arange(s.n_mol)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    Z = np.empty(len(idx))
+    _check(lib().orc_mixture_mass(s.ref, idx.ctypes.data, len(idx), Z.ctypes.data), "mixture_mass")
+    return Z
+
+
+def union_volume_ie(S, idx=0, c_alpha=2.41798793) -> float:
+    s = _oset(S, c_alpha)
+    V = ctypes.c_double()
+    _check(lib().orc_union_volume_ie(s.ref, idx, ctypes.addressof(V)), "union_volume_ie")
+    return V.value
+
+
+def union_overlap_ie(A, ia, B, ib, poseB=None, n_threads=0, c_alpha=2.41798793) -> float:
+    sa, sb = _oset(A, c_alpha), _oset(B, c_alpha)
+    O = ctypes.c_double()
+    p = None if poseB is None else np.ascontiguousarray(poseB, dtype=np.float32)
+    _check(lib().orc_union_overlap_ie(sa.ref, ia, sb.ref, ib, _ptr(p), ctypes.addressof(O), n_threads),
+           "union_overlap_ie")
+    return O.value
+
+
+def grid(A, ia, B=None, ib=0, h=0.1, pad=6.5, poseB=None, n_threads=0, c_alpha=2.41798793):
+    """dict(VA, VB, OU, OFO, ZA, SA) from midpoint quadrature (spacing h)."""
+    sa = _oset(A, c_alpha)
+    sb = None if B is None else _oset(B, c_alpha)
+    out = np.empty(6)
+    p = None if poseB is None else np.ascontiguousarray(poseB, dtype=np.float32)
+    _check(lib().orc_grid(sa.ref, ia, None if sb is None else sb.ref, ib, _ptr(p), h, pad,
+                          out.ctypes.data, n_threads), "grid")
+    return dict(VA=out[0], VB=out[1], OU=out[2], OFO=out[3], ZA=out[4], SA=out[5])
+
+
+def tanimoto_pairs(Q, iq, D, idd, stream_ids, selfQ, selfD, seed, n, flags=0, n_threads=0,
+                   c_alpha=2.41798793):
+    """Fixed-budget symmetric screen of explicit pairs. Returns dict of
+    [n_pairs, 2] arrays O, seO, T, seT (slot 0 first order, slot 1 union)."""
+    sq, sd = _oset(Q, c_alpha), _oset(D, c_alpha)
+    iq = np.ascontiguousarray(iq, dtype=np.int32)
+    idd = np.ascontiguousarray(idd, dtype=np.int32)
+    st = np.ascontiguousarray(stream_ids, dtype=np.uint64)
+    selfQ = np.ascontiguousarray(selfQ, dtype=np.float64)
+    selfD = np.ascontiguousarray(selfD, dtype=np.float64)
+    k = len(iq)
+    O, sO, T, sT = (np.empty((k, 2)) for _ in range(4))
+    _check(lib().orc_tanimoto_pairs(sq.ref, iq.ctypes.data, sd.ref, idd.ctypes.data, st.ctypes.data, k,
+                                    selfQ.ctypes.data, selfD.ctypes.data, seed, n, flags, O.ctypes.data,
+                                    sO.ctypes.data, T.ctypes.data, sT.ctypes.data, n_threads),
+           "tanimoto_pairs")
+    return dict(O=O, seO=sO, T=T, seT=sT)

@@ -1,0 +1,731 @@
+/*
+ * FP64 CPU oracle for importance-sampling estimation of Gaussian molecular
+ * shape overlap (Tuzharov, Bochenkova, Maximov, arXiv 2607.20766).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path may link, load or
+ * call this file: only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark use it. It shares no code, header, table or constant
+ * generator with the CUDA library; both sides were written independently
+ * from the paper and from the stream/sampler conventions stated below.
+ *
+ * What it computes, each in plain double precision, in the paper's order:
+ *   - atomic Gaussians g_i(r) = p_i exp(-alpha_i |r - c_i|^2)      (Eq. occ)
+ *   - union occupancy u(r) = 1 - prod_i (1 - g_i(r))              (Eq. union)
+ *   - first-order sum m(r) = sum_i g_i(r)                      (Sec. FO, Eq. fo)
+ *   - the mixture proposal q = m/Z, Z = sum_i p_i (pi/alpha_i)^{3/2}, drawn
+ *     exactly: component i with probability v_i/Z, then a normal offset of
+ *     variance 1/(2 alpha_i) per axis                    (Eq. expectation)
+ *   - IS estimators Z * mean(f) with f = m_B (first order) or
+ *     f = (u_A/m_A) u_B (union), sample-variance standard errors (Eq. var,
+ *     Eq. union-is), the symmetrised average over both proposals, the
+ *     Tanimoto and its delta-method SE (Sec. confidence-bounded screening)
+ *   - exact targets: the first-order closed form (Eq. fo), the full
+ *     inclusion-exclusion series (Eq. incexc) for union volumes and union
+ *     overlaps, and midpoint-rule grid quadrature of Eq. union-overlap.
+ *
+ * Conventions the paper leaves open (shared with the CUDA path as a written
+ * specification, implemented separately on each side):
+ *   - alpha_i = c_alpha / R_i^2 (default c_alpha = 2.41798793), height p_i
+ *     (default 2 sqrt 2); v_i = p_i * t * sqrt(t) with t = pi / alpha_i;
+ *     Z = sum of v_i in atom order.
+ *   - Component choice: integer Vose alias table. Masses
+ *     M_i = floor((v_i / Z) * N 2^32), remainder added to the last atom;
+ *     FIFO small/large worklists in atom order; the front large atom stays
+ *     at the front until it turns small. A 32-bit word x picks column
+ *     j = hi32(x N), then atom j if lo32(x N) < thr_j else alias_j.
+ *   - Random words: Philox4x32-10 (Salmon et al., SC'11), key =
+ *     (seed lo, seed hi), counter = (block, stream lo, stream hi, tag).
+ *     Sample pair s uses blocks 2s and 2s+1 (words w0..w7): sample 2s takes
+ *     w0 for the component and normals (n0, n1, n4); sample 2s+1 takes w1
+ *     and (n2, n3, n5), where (n0,n1) = BM(w2,w3), (n2,n3) = BM(w4,w5),
+ *     (n4,n5) = BM(w6,w7). BM(a,b): u1 = ((a>>8)+1) 2^-24, t = 2((b>>8)
+ *     2^-24) - 1, rho = sqrt(-2 ln u1), (rho cos(pi t), rho sin(pi t)).
+ *     Antithetic mode: sample 2s+1 is the reflection c_i - sigma_i z of
+ *     sample 2s, and the pair mean is the statistical unit.
+ *   - Tags: 0 = samples from A (A->B), 1 = samples from B (B->A), 2 = a
+ *     molecule's own volume / self-overlap.
+ *   - SE uses the n-1 sample variance; the symmetrised SE is
+ *     0.5 sqrt(SE_AB^2 + SE_BA^2) (independent streams per direction).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+#define ORC_MAXN 64
+
+enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ERANGE = -4 };
+enum { ORC_SYMMETRIC = 1u, ORC_ANTITHETIC = 2u };
+enum { ORC_TAG_AB = 0u, ORC_TAG_BA = 1u, ORC_TAG_SELF = 2u };
+
+/* A set of molecules as flat arrays (host). p may be NULL (2 sqrt 2). */
+typedef struct {
+  const float* xyz;       /* [n_atoms][3] */
+  const float* radius;    /* [n_atoms] */
+  const float* height;    /* [n_atoms] or NULL */
+  const int32_t* offsets; /* [n_mol + 1] */
+  int32_t n_mol;
+  double c_alpha;         /* <= 0 means 2.41798793 */
+} orc_set;
+
+/* One molecule, expanded to double precision. */
+typedef struct {
+  int n;
+  double c[ORC_MAXN][3];
+  double alpha[ORC_MAXN];
+  double p[ORC_MAXN];
+  double sigma[ORC_MAXN];
+  double v[ORC_MAXN];
+  double Z;
+  uint32_t thr[ORC_MAXN];
+  uint8_t alias[ORC_MAXN];
+} orc_mol;
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10                                                       */
+/* ------------------------------------------------------------------ */
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+    uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+    uint32_t y0 = (uint32_t)(prod1 >> 32) ^ x1 ^ k0;
+    uint32_t y1 = (uint32_t)prod1;
+    uint32_t y2 = (uint32_t)(prod0 >> 32) ^ x3 ^ k1;
+    uint32_t y3 = (uint32_t)prod0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Box-Muller on two 32-bit words, as specified in the header comment. */
+void orc_normal_pair(uint32_t a, uint32_t b, double out[2]) {
+  double u1 = (double)((a >> 8) + 1u) * (1.0 / 16777216.0);
+  double t = 2.0 * ((double)(b >> 8) * (1.0 / 16777216.0)) - 1.0;
+  double rho = sqrt(-2.0 * log(u1));
+  out[0] = rho * cos(ORC_PI * t);
+  out[1] = rho * sin(ORC_PI * t);
+}
+
+/* ------------------------------------------------------------------ */
+/* Mixture weights and alias tables                                    */
+/* ------------------------------------------------------------------ */
+
+/* Integer Vose alias table from positive weights v[0..n-1]. */
+int orc_alias_build(int n, const double* v, uint32_t* thr, uint8_t* alias, uint64_t* mass_out) {
+  if (n < 1 || n > ORC_MAXN) return ORC_ERANGE;
+  const uint64_t ONE = (uint64_t)1 << 32;
+  uint64_t M[ORC_MAXN];
+  double Z = 0.0;
+  for (int i = 0; i < n; ++i) {
+    if (!(v[i] > 0.0)) return ORC_EINVAL;
+    Z += v[i];
+  }
+  const double scale = (double)n * 4294967296.0;
+  uint64_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    M[i] = (uint64_t)floor((v[i] / Z) * scale);
+    total += M[i];
+  }
+  M[n - 1] += (uint64_t)n * ONE - total;
+  if (mass_out) memcpy(mass_out, M, sizeof(uint64_t) * (size_t)n);
+  int small[ORC_MAXN], large[ORC_MAXN];
+  int s_head = 0, s_tail = 0, l_head = 0, l_tail = 0;
+  for (int i = 0; i < n; ++i) {
+    if (M[i] < ONE) small[s_tail++] = i;
+    else large[l_tail++] = i;
+  }
+  while (s_head < s_tail && l_head < l_tail) {
+    int s = small[s_head++];
+    int l = large[l_head];
+    thr[s] = (uint32_t)M[s];
+    alias[s] = (uint8_t)l;
+    M[l] -= ONE - M[s];
+    if (M[l] < ONE) {
+      ++l_head;
+      small[s_tail++] = l;
+    }
+  }
+  while (s_head < s_tail) { int s = small[s_head++]; thr[s] = 0xFFFFFFFFu; alias[s] = (uint8_t)s; }
+  while (l_head < l_tail) { int l = large[l_head++]; thr[l] = 0xFFFFFFFFu; alias[l] = (uint8_t)l; }
+  return ORC_OK;
+}
+
+static int load_mol(const orc_set* S, int32_t idx, const float* pose, orc_mol* m) {
+  if (idx < 0 || idx >= S->n_mol) return ORC_EINVAL;
+  int32_t a0 = S->offsets[idx], a1 = S->offsets[idx + 1];
+  int n = a1 - a0;
+  if (n < 1 || n > ORC_MAXN) return ORC_ERANGE;
+  double ca = S->c_alpha > 0 ? S->c_alpha : 2.41798793;
+  double R[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, t[3] = {0, 0, 0};
+  if (pose) {
+    double w = pose[0], x = pose[1], y = pose[2], z = pose[3];
+    double nq = sqrt(w * w + x * x + y * y + z * z);
+    if (!(nq > 0)) return ORC_EINVAL;
+    w /= nq; x /= nq; y /= nq; z /= nq;
+    R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z); R[0][2] = 2 * (x * z + w * y);
+    R[1][0] = 2 * (x * y + w * z); R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - w * x);
+    R[2][0] = 2 * (x * z - w * y); R[2][1] = 2 * (y * z + w * x); R[2][2] = 1 - 2 * (x * x + y * y);
+    t[0] = pose[4]; t[1] = pose[5]; t[2] = pose[6];
+  }
+  m->n = n;
+  m->Z = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const float* c = S->xyz + 3 * (size_t)(a0 + i);
+    double c0 = c[0], c1 = c[1], c2 = c[2];
+    for (int k = 0; k < 3; ++k) m->c[i][k] = R[k][0] * c0 + R[k][1] * c1 + R[k][2] * c2 + t[k];
+    double r = S->radius[a0 + i];
+    if (!(r > 0)) return ORC_EINVAL;
+    m->alpha[i] = ca / (r * r);
+    m->p[i] = S->height ? (double)S->height[a0 + i] : 2.0 * sqrt(2.0);
+    m->sigma[i] = 1.0 / sqrt(2.0 * m->alpha[i]);
+    double tt = ORC_PI / m->alpha[i];
+    m->v[i] = m->p[i] * tt * sqrt(tt);
+    m->Z += m->v[i];
+  }
+  return orc_alias_build(n, m->v, m->thr, m->alias, NULL);
+}
+
+/* Per-molecule tables (for cross-checking the library's own tables). */
+int orc_mol_tables(const orc_set* S, int32_t idx, double* alpha, double* v, double* Z,
+                   uint32_t* thr, uint8_t* alias) {
+  orc_mol m;
+  int rc = load_mol(S, idx, NULL, &m);
+  if (rc) return rc;
+  for (int i = 0; i < m.n; ++i) {
+    if (alpha) alpha[i] = m.alpha[i];
+    if (v) v[i] = m.v[i];
+    if (thr) thr[i] = m.thr[i];
+    if (alias) alias[i] = m.alias[i];
+  }
+  if (Z) *Z = m.Z;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sampling from the mixture q = m / Z (Eq. expectation)               */
+/* ------------------------------------------------------------------ */
+
+static int pick_component(const orc_mol* m, uint32_t x) {
+  uint64_t prod = (uint64_t)x * (uint64_t)m->n;
+  uint32_t j = (uint32_t)(prod >> 32), f = (uint32_t)prod;
+  return f < m->thr[j] ? (int)j : (int)m->alias[j];
+}
+
+/* Samples 2s and 2s+1 of stream (seed, stream, tag) drawn from molecule m. */
+static void draw_pair(const orc_mol* m, uint64_t seed, uint64_t stream, uint32_t tag, uint32_t s,
+                      int antithetic, double r0[3], double r1[3], int* i0, int* i1) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t c[4] = {2u * s, (uint32_t)stream, (uint32_t)(stream >> 32), tag};
+  uint32_t w[8];
+  orc_philox4x32_10(c, key, w);
+  c[0] = 2u * s + 1u;
+  orc_philox4x32_10(c, key, w + 4);
+  double n01[2], n23[2], n45[2];
+  orc_normal_pair(w[2], w[3], n01);
+  orc_normal_pair(w[4], w[5], n23);
+  orc_normal_pair(w[6], w[7], n45);
+  int a = pick_component(m, w[0]);
+  double z0[3] = {n01[0], n01[1], n45[0]};
+  for (int k = 0; k < 3; ++k) r0[k] = m->c[a][k] + m->sigma[a] * z0[k];
+  *i0 = a;
+  if (antithetic) {
+    for (int k = 0; k < 3; ++k) r1[k] = m->c[a][k] - m->sigma[a] * z0[k];
+    *i1 = a;
+  } else {
+    int b = pick_component(m, w[1]);
+    double z1[3] = {n23[0], n23[1], n45[1]};
+    for (int k = 0; k < 3; ++k) r1[k] = m->c[b][k] + m->sigma[b] * z1[k];
+    *i1 = b;
+  }
+}
+
+/* Draw n samples of one stream (for sampler tests): r[n][3], comp[n]. */
+int orc_draw(const orc_set* S, int32_t idx, uint64_t seed, uint64_t stream, uint32_t tag,
+             int64_t n, int antithetic, double* r, int32_t* comp) {
+  orc_mol m;
+  int rc = load_mol(S, idx, NULL, &m);
+  if (rc) return rc;
+  for (int64_t k = 0; k < n; k += 2) {
+    double a[3], b[3];
+    int ia, ib;
+    draw_pair(&m, seed, stream, tag, (uint32_t)(k / 2), antithetic, a, b, &ia, &ib);
+    memcpy(r + 3 * k, a, sizeof a);
+    if (comp) comp[k] = ia;
+    if (k + 1 < n) {
+      memcpy(r + 3 * (k + 1), b, sizeof b);
+      if (comp) comp[k + 1] = ib;
+    }
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Occupancies (Eq. occ, Eq. union, first-order sum)                   */
+/* ------------------------------------------------------------------ */
+
+static void occupancy(const orc_mol* m, const double r[3], double* msum, double* u) {
+  double s = 0.0, prod = 1.0;
+  for (int i = 0; i < m->n; ++i) {
+    double dx = r[0] - m->c[i][0], dy = r[1] - m->c[i][1], dz = r[2] - m->c[i][2];
+    double g = m->p[i] * exp(-m->alpha[i] * (dx * dx + dy * dy + dz * dz));
+    s += g;
+    prod *= 1.0 - g;
+  }
+  *msum = s;
+  *u = 1.0 - prod;
+}
+
+/* Evaluate m and u of a set member at points r[n][3] (test helper). */
+int orc_occupancy(const orc_set* S, int32_t idx, const float* pose, int64_t n, const double* r,
+                  double* msum, double* u) {
+  orc_mol m;
+  int rc = load_mol(S, idx, pose, &m);
+  if (rc) return rc;
+  for (int64_t k = 0; k < n; ++k) occupancy(&m, r + 3 * k, msum + k, u + k);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* IS sums for one direction: samples from X, other molecule Y         */
+/* sums = {sum f_FO, sum f_FO^2, sum f_U, sum f_U^2}, unit count n_eff   */
+/* ------------------------------------------------------------------ */
+
+static void sums_cross(const orc_mol* X, const orc_mol* Y, uint64_t seed, uint64_t stream,
+                       uint32_t tag, uint32_t n, int antithetic, double sums[4], double* n_eff) {
+  double s[4] = {0, 0, 0, 0};
+  for (uint32_t k = 0; k < n; k += 2) {
+    double r[2][3];
+    int ia, ib;
+    draw_pair(X, seed, stream, tag, k / 2, antithetic, r[0], r[1], &ia, &ib);
+    double ffo[2], fu[2];
+    int cnt = (k + 1 < n) ? 2 : 1;
+    for (int j = 0; j < cnt; ++j) {
+      double mx, ux, my, uy;
+      occupancy(X, r[j], &mx, &ux);
+      occupancy(Y, r[j], &my, &uy);
+      ffo[j] = my;                 /* first order: f = m_Y        */
+      fu[j] = (ux / mx) * uy;      /* union: f = w_X u_Y, w = u/m */
+    }
+    if (antithetic) {
+      double g0 = 0.5 * (ffo[0] + ffo[1]), g1 = 0.5 * (fu[0] + fu[1]);
+      s[0] += g0; s[1] += g0 * g0; s[2] += g1; s[3] += g1 * g1;
+    } else {
+      for (int j = 0; j < cnt; ++j) {
+        s[0] += ffo[j]; s[1] += ffo[j] * ffo[j]; s[2] += fu[j]; s[3] += fu[j] * fu[j];
+      }
+    }
+  }
+  memcpy(sums, s, sizeof s);
+  *n_eff = antithetic ? (double)(n / 2) : (double)n;
+}
+
+/* Own volume and union self-overlap of X: f_V = u/m, f_S = u^2/m. */
+static void sums_self(const orc_mol* X, uint64_t seed, uint64_t stream, uint32_t n, int antithetic,
+                      double sums[4], double* n_eff) {
+  double s[4] = {0, 0, 0, 0};
+  for (uint32_t k = 0; k < n; k += 2) {
+    double r[2][3];
+    int ia, ib;
+    draw_pair(X, seed, stream, ORC_TAG_SELF, k / 2, antithetic, r[0], r[1], &ia, &ib);
+    double fv[2], fs[2];
+    int cnt = (k + 1 < n) ? 2 : 1;
+    for (int j = 0; j < cnt; ++j) {
+      double mx, ux;
+      occupancy(X, r[j], &mx, &ux);
+      fv[j] = ux / mx;
+      fs[j] = ux * ux / mx;
+    }
+    if (antithetic) {
+      double g0 = 0.5 * (fv[0] + fv[1]), g1 = 0.5 * (fs[0] + fs[1]);
+      s[0] += g0; s[1] += g0 * g0; s[2] += g1; s[3] += g1 * g1;
+    } else {
+      for (int j = 0; j < cnt; ++j) {
+        s[0] += fv[j]; s[1] += fv[j] * fv[j]; s[2] += fs[j]; s[3] += fs[j] * fs[j];
+      }
+    }
+  }
+  memcpy(sums, s, sizeof s);
+  *n_eff = antithetic ? (double)(n / 2) : (double)n;
+}
+
+/* Z * mean and Z * sqrt(s^2 / n) with the n-1 sample variance (Eq. var). */
+static void finish(double Z, double sum, double sum2, double n, double* est, double* se) {
+  double mean = sum / n;
+  double var = n > 1 ? (sum2 - sum * mean) / (n - 1.0) : 0.0;
+  if (var < 0) var = 0;
+  *est = Z * mean;
+  *se = Z * sqrt(var / n);
+}
+
+/* Raw one-direction sums (test helper): samples from A[ia] (tag 0) or from
+ * posed B[ib] (tag 1). */
+int orc_direction_sums(const orc_set* A, int32_t ia, const orc_set* B, int32_t ib,
+                       const float* poseB, uint64_t seed, uint64_t stream, uint32_t tag, uint32_t n,
+                       uint32_t flags, double sums[4], double* n_eff) {
+  orc_mol ma, mb;
+  int rc = load_mol(A, ia, NULL, &ma);
+  if (!rc) rc = load_mol(B, ib, poseB, &mb);
+  if (rc) return rc;
+  if (tag == ORC_TAG_BA)
+    sums_cross(&mb, &ma, seed, stream, tag, n, (flags & ORC_ANTITHETIC) != 0, sums, n_eff);
+  else
+    sums_cross(&ma, &mb, seed, stream, tag, n, (flags & ORC_ANTITHETIC) != 0, sums, n_eff);
+  return ORC_OK;
+}
+
+static int nthreads_set(int n_threads) {
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+  return omp_get_max_threads();
+#else
+  (void)n_threads;
+  return 1;
+#endif
+}
+
+/*
+ * Pair overlaps: est[n_pairs][2], se[n_pairs][2] with slot 0 = first order,
+ * slot 1 = union. Pair k uses stream stream_base + k. With ORC_SYMMETRIC
+ * both directions are estimated and averaged; otherwise only A->B.
+ */
+int orc_overlap_estimate(const orc_set* A, const int32_t* ia, const orc_set* B, const int32_t* ib,
+                         int64_t n_pairs, const float* poses, uint64_t seed, uint64_t stream_base,
+                         uint32_t n, uint32_t flags, double* est, double* se, int n_threads) {
+  if (n < 2 || n_pairs < 0) return ORC_EINVAL;
+  if ((flags & ORC_ANTITHETIC) && (n & 1u)) return ORC_EINVAL;
+  nthreads_set(n_threads);
+  int err = 0;
+  const int anti = (flags & ORC_ANTITHETIC) != 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+  for (int64_t k = 0; k < n_pairs; ++k) {
+    orc_mol ma, mb;
+    if (load_mol(A, ia[k], NULL, &ma) || load_mol(B, ib[k], poses ? poses + 7 * k : NULL, &mb)) {
+      err |= 1;
+      continue;
+    }
+    uint64_t stream = stream_base + (uint64_t)k;
+    double s[4], ne, e_fo, s_fo, e_u, s_u;
+    sums_cross(&ma, &mb, seed, stream, ORC_TAG_AB, n, anti, s, &ne);
+    finish(ma.Z, s[0], s[1], ne, &e_fo, &s_fo);
+    finish(ma.Z, s[2], s[3], ne, &e_u, &s_u);
+    if (flags & ORC_SYMMETRIC) {
+      double e2_fo, s2_fo, e2_u, s2_u;
+      sums_cross(&mb, &ma, seed, stream, ORC_TAG_BA, n, anti, s, &ne);
+      finish(mb.Z, s[0], s[1], ne, &e2_fo, &s2_fo);
+      finish(mb.Z, s[2], s[3], ne, &e2_u, &s2_u);
+      e_fo = 0.5 * (e_fo + e2_fo);
+      s_fo = 0.5 * sqrt(s_fo * s_fo + s2_fo * s2_fo);
+      e_u = 0.5 * (e_u + e2_u);
+      s_u = 0.5 * sqrt(s_u * s_u + s2_u * s2_u);
+    }
+    est[2 * k] = e_fo; se[2 * k] = s_fo;
+    est[2 * k + 1] = e_u; se[2 * k + 1] = s_u;
+  }
+  return err ? ORC_EINVAL : ORC_OK;
+}
+
+/*
+ * Union volume V = Z E_q[u/m] (Eq. expectation with f = u/m) and union
+ * self-overlap O_XX = Z E_q[u^2/m] (Eq. union-is with B = A) of molecules
+ * idx[0..n-1]; molecule k uses stream stream_base + k, tag 2.
+ */
+int orc_union_volume_estimate(const orc_set* S, const int32_t* idx, int64_t n_mol, uint64_t seed,
+                              uint64_t stream_base, uint32_t n, uint32_t flags, double* vol,
+                              double* vol_se, double* self_ov, double* self_se, int n_threads) {
+  if (n < 2 || n_mol < 0) return ORC_EINVAL;
+  if ((flags & ORC_ANTITHETIC) && (n & 1u)) return ORC_EINVAL;
+  nthreads_set(n_threads);
+  int err = 0;
+  const int anti = (flags & ORC_ANTITHETIC) != 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+  for (int64_t k = 0; k < n_mol; ++k) {
+    orc_mol m;
+    if (load_mol(S, idx ? idx[k] : (int32_t)k, NULL, &m)) { err |= 1; continue; }
+    double s[4], ne, e, sd;
+    sums_self(&m, seed, stream_base + (uint64_t)k, n, anti, s, &ne);
+    finish(m.Z, s[0], s[1], ne, &e, &sd);
+    vol[k] = e;
+    if (vol_se) vol_se[k] = sd;
+    finish(m.Z, s[2], s[3], ne, &e, &sd);
+    if (self_ov) self_ov[k] = e;
+    if (self_se) self_se[k] = sd;
+  }
+  return err ? ORC_EINVAL : ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* First-order closed form (Eq. fo, with heights p_i p_j)              */
+/* ------------------------------------------------------------------ */
+
+static double fo_closed(const orc_mol* a, const orc_mol* b) {
+  double s = 0.0;
+  for (int i = 0; i < a->n; ++i)
+    for (int j = 0; j < b->n; ++j) {
+      double ai = a->alpha[i], bj = b->alpha[j], sum = ai + bj;
+      double dx = a->c[i][0] - b->c[j][0], dy = a->c[i][1] - b->c[j][1], dz = a->c[i][2] - b->c[j][2];
+      double t = ORC_PI / sum;
+      s += a->p[i] * b->p[j] * t * sqrt(t) * exp(-ai * bj / sum * (dx * dx + dy * dy + dz * dz));
+    }
+  return s;
+}
+
+int orc_fo_overlap(const orc_set* A, const int32_t* ia, const orc_set* B, const int32_t* ib,
+                   int64_t n_pairs, const float* poses, double* out, int n_threads) {
+  nthreads_set(n_threads);
+  int err = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : err)
+  for (int64_t k = 0; k < n_pairs; ++k) {
+    orc_mol ma, mb;
+    if (load_mol(A, ia[k], NULL, &ma) || load_mol(B, ib[k], poses ? poses + 7 * k : NULL, &mb)) {
+      err |= 1;
+      continue;
+    }
+    out[k] = fo_closed(&ma, &mb);
+  }
+  return err ? ORC_EINVAL : ORC_OK;
+}
+
+/* Z of each molecule (= its first-order volume, the integral of m). */
+int orc_mixture_mass(const orc_set* S, const int32_t* idx, int64_t n_mol, double* Z) {
+  for (int64_t k = 0; k < n_mol; ++k) {
+    orc_mol m;
+    int rc = load_mol(S, idx ? idx[k] : (int32_t)k, NULL, &m);
+    if (rc) return rc;
+    Z[k] = m.Z;
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Inclusion-exclusion (Eq. incexc) -- exact union volume / overlap    */
+/* ------------------------------------------------------------------ */
+
+/* Product of the Gaussians of one subset: p = prod p_i, a = sum alpha_i,
+ * b = sum alpha_i c_i, c = sum alpha_i |c_i|^2; its integral is
+ * p (pi/a)^{3/2} exp(-(c - |b|^2 / a)). */
+typedef struct { double p, a, b[3], c; int sign; } orc_subset;
+
+static orc_subset* subsets_of(const orc_mol* m) {
+  size_t ns = (size_t)1 << m->n;
+  orc_subset* T = (orc_subset*)malloc(ns * sizeof(orc_subset));
+  if (!T) return NULL;
+  T[0].p = 1.0; T[0].a = 0.0; T[0].b[0] = T[0].b[1] = T[0].b[2] = 0.0; T[0].c = 0.0; T[0].sign = 1;
+  for (size_t s = 1; s < ns; ++s) {
+    int i = __builtin_ctzll((unsigned long long)s);
+    const orc_subset* pr = &T[s & (s - 1)];
+    orc_subset* q = &T[s];
+    double al = m->alpha[i];
+    q->p = pr->p * m->p[i];
+    q->a = pr->a + al;
+    for (int k = 0; k < 3; ++k) q->b[k] = pr->b[k] + al * m->c[i][k];
+    q->c = pr->c + al * (m->c[i][0] * m->c[i][0] + m->c[i][1] * m->c[i][1] + m->c[i][2] * m->c[i][2]);
+    q->sign = -pr->sign;
+  }
+  return T;
+}
+
+static double subset_integral(double p, double a, const double b[3], double c) {
+  double t = ORC_PI / a;
+  double e = c - (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]) / a;
+  return p * t * sqrt(t) * exp(-e);
+}
+
+/* Neumaier compensated summation. */
+typedef struct { double s, c; } orc_acc;
+static void acc_add(orc_acc* A, double x) {
+  double t = A->s + x;
+  if (fabs(A->s) >= fabs(x)) A->c += (A->s - t) + x;
+  else A->c += (x - t) + A->s;
+  A->s = t;
+}
+
+/* V = sum over non-empty subsets S of (-1)^{|S|+1} I(S). */
+int orc_union_volume_ie(const orc_set* S, int32_t idx, double* V) {
+  orc_mol m;
+  int rc = load_mol(S, idx, NULL, &m);
+  if (rc) return rc;
+  if (m.n > 26) return ORC_ERANGE;
+  orc_subset* T = subsets_of(&m);
+  if (!T) return ORC_EINVAL;
+  size_t ns = (size_t)1 << m.n;
+  orc_acc acc = {0, 0};
+  for (size_t s = 1; s < ns; ++s) acc_add(&acc, -(double)T[s].sign * subset_integral(T[s].p, T[s].a, T[s].b, T[s].c));
+  free(T);
+  *V = acc.s + acc.c;
+  return ORC_OK;
+}
+
+/* O_AB = integral of u_A u_B = sum over non-empty S in A, T in B of
+ * (-1)^{|S|+|T|} I(S + T), S and T taken as disjoint atom multisets. */
+int orc_union_overlap_ie(const orc_set* A, int32_t ia, const orc_set* B, int32_t ib,
+                         const float* poseB, double* O, int n_threads) {
+  orc_mol ma, mb;
+  int rc = load_mol(A, ia, NULL, &ma);
+  if (!rc) rc = load_mol(B, ib, poseB, &mb);
+  if (rc) return rc;
+  if (ma.n > 20 || mb.n > 20) return ORC_ERANGE;
+  orc_subset* TA = subsets_of(&ma);
+  orc_subset* TB = subsets_of(&mb);
+  if (!TA || !TB) { free(TA); free(TB); return ORC_EINVAL; }
+  nthreads_set(n_threads);
+  int64_t na = (int64_t)1 << ma.n, nb = (int64_t)1 << mb.n;
+  double total_s = 0.0, total_c = 0.0;
+#pragma omp parallel
+  {
+    orc_acc acc = {0, 0};
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t s = 1; s < na; ++s) {
+      const orc_subset* x = &TA[s];
+      for (int64_t t = 1; t < nb; ++t) {
+        const orc_subset* y = &TB[t];
+        double b[3] = {x->b[0] + y->b[0], x->b[1] + y->b[1], x->b[2] + y->b[2]};
+        double v = subset_integral(x->p * y->p, x->a + y->a, b, x->c + y->c);
+        acc_add(&acc, (double)(x->sign * y->sign) * v);
+      }
+    }
+#pragma omp critical
+    { total_s += acc.s; total_c += acc.c; }
+  }
+  free(TA);
+  free(TB);
+  *O = total_s + total_c;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Grid quadrature of Eq. union-overlap (independent ground truth)     */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Midpoint rule with spacing h over the joint bounding box of the centres
+ * padded by pad. out = {V_A, V_B, O_AB (union), O_AB (first order),
+ * integral of m_A, integral of u_A^2}. With nB == 0 only A's entries are
+ * meaningful. The Gaussians are separable, so each atom keeps three 1-D
+ * tables of exp(-alpha (x - c)^2).
+ */
+int orc_grid(const orc_set* A, int32_t ia, const orc_set* B, int32_t ib, const float* poseB,
+             double h, double pad, double out[6], int n_threads) {
+  orc_mol ma, mb;
+  int rc = load_mol(A, ia, NULL, &ma);
+  if (rc) return rc;
+  int have_b = B != NULL;
+  if (have_b && (rc = load_mol(B, ib, poseB, &mb))) return rc;
+  if (!have_b) mb.n = 0;
+  if (!(h > 0) || !(pad >= 0)) return ORC_EINVAL;
+  double lo[3], hi[3];
+  for (int k = 0; k < 3; ++k) { lo[k] = 1e300; hi[k] = -1e300; }
+  for (int i = 0; i < ma.n; ++i)
+    for (int k = 0; k < 3; ++k) { lo[k] = fmin(lo[k], ma.c[i][k]); hi[k] = fmax(hi[k], ma.c[i][k]); }
+  for (int i = 0; i < mb.n; ++i)
+    for (int k = 0; k < 3; ++k) { lo[k] = fmin(lo[k], mb.c[i][k]); hi[k] = fmax(hi[k], mb.c[i][k]); }
+  int np[3];
+  for (int k = 0; k < 3; ++k) {
+    lo[k] -= pad; hi[k] += pad;
+    np[k] = (int)ceil((hi[k] - lo[k]) / h);
+  }
+  int nat = ma.n + mb.n;
+  double* tab[3];
+  for (int k = 0; k < 3; ++k) {
+    tab[k] = (double*)malloc(sizeof(double) * (size_t)nat * (size_t)np[k]);
+    if (!tab[k]) return ORC_EINVAL;
+    for (int a = 0; a < nat; ++a) {
+      const double* c = a < ma.n ? ma.c[a] : mb.c[a - ma.n];
+      double al = a < ma.n ? ma.alpha[a] : mb.alpha[a - ma.n];
+      for (int i = 0; i < np[k]; ++i) {
+        double x = lo[k] + (i + 0.5) * h - c[k];
+        tab[k][(size_t)a * np[k] + i] = exp(-al * x * x);
+      }
+    }
+  }
+  nthreads_set(n_threads);
+  double sums[6] = {0, 0, 0, 0, 0, 0};
+#pragma omp parallel
+  {
+    double loc[6] = {0, 0, 0, 0, 0, 0};
+    double pxy[2 * ORC_MAXN];
+#pragma omp for schedule(dynamic, 1)
+    for (int ix = 0; ix < np[0]; ++ix) {
+      for (int iy = 0; iy < np[1]; ++iy) {
+        for (int a = 0; a < nat; ++a) {
+          double p = a < ma.n ? ma.p[a] : mb.p[a - ma.n];
+          pxy[a] = p * tab[0][(size_t)a * np[0] + ix] * tab[1][(size_t)a * np[1] + iy];
+        }
+        double row[6] = {0, 0, 0, 0, 0, 0};
+        for (int iz = 0; iz < np[2]; ++iz) {
+          double mA = 0, qA = 1, mB = 0, qB = 1;
+          for (int a = 0; a < ma.n; ++a) {
+            double g = pxy[a] * tab[2][(size_t)a * np[2] + iz];
+            mA += g; qA *= 1.0 - g;
+          }
+          for (int a = ma.n; a < nat; ++a) {
+            double g = pxy[a] * tab[2][(size_t)a * np[2] + iz];
+            mB += g; qB *= 1.0 - g;
+          }
+          double uA = 1.0 - qA, uB = 1.0 - qB;
+          row[0] += uA; row[1] += uB; row[2] += uA * uB; row[3] += mA * mB; row[4] += mA;
+          row[5] += uA * uA;
+        }
+        for (int t = 0; t < 6; ++t) loc[t] += row[t];
+      }
+    }
+#pragma omp critical
+    for (int t = 0; t < 6; ++t) sums[t] += loc[t];
+  }
+  double dv = h * h * h;
+  for (int t = 0; t < 6; ++t) out[t] = sums[t] * dv;
+  for (int k = 0; k < 3; ++k) free(tab[k]);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Fixed-budget Tanimoto screen (Sec. confidence-bounded screening)    */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Pairs (Q[iq[k]], D[id[k]]), both directions, n samples each, streams
+ * stream_ids[k]. selfQ / selfD hold each molecule's self-overlaps as
+ * [slot 0 = first order, slot 1 = union] (indexed by iq[k] / id[k]).
+ * Outputs (slot 0 first order, slot 1 union), each [n_pairs][2]:
+ * O, seO, T = O / (S - O) with S = O_QQ + O_DD, seT = S / (S - O)^2 seO.
+ */
+int orc_tanimoto_pairs(const orc_set* Q, const int32_t* iq, const orc_set* D, const int32_t* id,
+                       const uint64_t* stream_ids, int64_t n_pairs, const double* selfQ,
+                       const double* selfD, uint64_t seed, uint32_t n, uint32_t flags, double* O,
+                       double* seO, double* T, double* seT, int n_threads) {
+  if (n < 2) return ORC_EINVAL;
+  nthreads_set(n_threads);
+  int err = 0;
+  const int anti = (flags & ORC_ANTITHETIC) != 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+  for (int64_t k = 0; k < n_pairs; ++k) {
+    orc_mol mq, md;
+    if (load_mol(Q, iq[k], NULL, &mq) || load_mol(D, id[k], NULL, &md)) { err |= 1; continue; }
+    double s[4], ne, e1[2], s1[2], e2[2], s2[2];
+    sums_cross(&mq, &md, seed, stream_ids[k], ORC_TAG_AB, n, anti, s, &ne);
+    finish(mq.Z, s[0], s[1], ne, &e1[0], &s1[0]);
+    finish(mq.Z, s[2], s[3], ne, &e1[1], &s1[1]);
+    sums_cross(&md, &mq, seed, stream_ids[k], ORC_TAG_BA, n, anti, s, &ne);
+    finish(md.Z, s[0], s[1], ne, &e2[0], &s2[0]);
+    finish(md.Z, s[2], s[3], ne, &e2[1], &s2[1]);
+    for (int slot = 0; slot < 2; ++slot) {
+      double o = 0.5 * (e1[slot] + e2[slot]);
+      double so = 0.5 * sqrt(s1[slot] * s1[slot] + s2[slot] * s2[slot]);
+      double S = selfQ[2 * (size_t)iq[k] + slot] + selfD[2 * (size_t)id[k] + slot];
+      double den = S - o;
+      O[2 * k + slot] = o;
+      seO[2 * k + slot] = so;
+      T[2 * k + slot] = o / den;
+      seT[2 * k + slot] = fabs(S / (den * den)) * so;
+    }
+  }
+  return err ? ORC_EINVAL : ORC_OK;
+}
