@@ -1,0 +1,186 @@
+/*
+ * shape.h -- C ABI of libshape: importance-sampling estimation of Gaussian
+ * molecular shape overlap on one B300 GPU (sm_103a).
+ *
+ * Method: Tuzharov, Bochenkova, Maximov, "Importance-Sampling Estimation of
+ * Gaussian Molecular Shape Overlap: Exact Union Volumes and
+ * Confidence-Bounded Virtual Screening" (arXiv 2607.20766).
+ *
+ * Conventions for every entry point
+ *   - Return value: SHP_OK (0) or a negative status; shp_last_error() gives
+ *     a message for the calling thread. No exception crosses the ABI.
+ *   - Pointers named *_host are host memory. Every other array argument is
+ *     DEVICE memory owned by the caller (e.g. a torch CUDA tensor), on the
+ *     current device, and must stay valid until the work queued on `stream`
+ *     has finished.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Arguments are checked synchronously; GPU work is queued
+ *     asynchronously on `stream` and results are ready when the stream is.
+ *   - A shp_set is immutable after shape_set_load; concurrent calls on
+ *     different streams may share it. shape_set_free must not race with
+ *     work that still uses the set.
+ *   - Molecules hold 1..SHP_MAX_ATOMS atoms (else SHP_ERANGE).
+ *
+ * Model (Eq. occ, Eq. union, Sec. first-order overlap): atom i has centre
+ * c_i, radius R_i, height p_i (default 2 sqrt 2) and
+ * alpha_i = c_alpha / R_i^2 (default c_alpha = 2.41798793); its Gaussian is
+ * g_i(r) = p_i exp(-alpha_i |r - c_i|^2). m(r) = sum_i g_i(r) is the
+ * first-order density and u(r) = 1 - prod_i (1 - g_i(r)) the union
+ * occupancy. Z = sum_i p_i (pi / alpha_i)^{3/2} = integral of m.
+ *
+ * Random streams: counter-based Philox4x32-10, key = seed, counter =
+ * (block, stream lo, stream hi, tag); the sample layout is fixed so that any
+ * independent implementation of the same specification reproduces every
+ * sample (see the library's design notes).
+ */
+#ifndef SHAPE_H
+#define SHAPE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SHP_OK 0
+#define SHP_EINVAL (-1)   /* bad argument (NULL, negative size, NaN, ...)   */
+#define SHP_ENOMEM (-2)   /* device or host allocation failed               */
+#define SHP_ECUDA (-3)    /* a CUDA runtime call failed                      */
+#define SHP_ERANGE (-4)   /* atom count outside 1..SHP_MAX_ATOMS, index out of range */
+#define SHP_ETIMEOUT (-5) /* a bounded device-side wait gave up              */
+
+#define SHP_MAX_ATOMS 64
+
+/* Monte-Carlo flags */
+#define SHP_SYMMETRIC 1u  /* estimate from both proposals and average (Sec. IS estimator) */
+#define SHP_ANTITHETIC 2u /* pair each draw with its reflection about the component centre */
+
+/* Stream tags (counter word 3) */
+#define SHP_TAG_AB 0u   /* samples drawn from A's mixture, B evaluated */
+#define SHP_TAG_BA 1u   /* samples drawn from B's mixture, A evaluated */
+#define SHP_TAG_SELF 2u /* a molecule's own volume / self-overlap      */
+
+typedef struct shp_set_s* shp_set;
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* shp_last_error(void);
+
+/* ABI version (incremented on any signature change). */
+int shp_version(void);
+
+/*
+ * Load n_mol molecules into device memory (Eq. occ, Eq. expectation).
+ *   xyz_host      [n_atoms][3] float, Angstrom (n_atoms = offsets_host[n_mol])
+ *   radius_host   [n_atoms] float > 0, Angstrom
+ *   height_host   [n_atoms] float > 0, or NULL for 2 sqrt 2
+ *   c_alpha       alpha_i = c_alpha / R_i^2; <= 0 selects 2.41798793
+ *   offsets_host  [n_mol + 1] int32, offsets_host[0] = 0, non-decreasing,
+ *                 every count in 1..SHP_MAX_ATOMS
+ *   n_mol         >= 0
+ * Builds per molecule the mixture mass Z, the integer alias table of the
+ * component probabilities v_i / Z, and a largest-first order used to
+ * balance screens. Copies on `stream` and synchronises it before returning.
+ * On success *out owns all device memory of the set (free with
+ * shape_set_free). Errors: SHP_EINVAL (NULL, non-finite or non-positive
+ * values), SHP_ERANGE (atom counts), SHP_ENOMEM, SHP_ECUDA.
+ */
+int shape_set_load(const float* xyz_host, const float* radius_host, const float* height_host,
+                   double c_alpha, const int32_t* offsets_host, int32_t n_mol, void* stream,
+                   shp_set* out);
+
+/* Free a set (NULL is a no-op). Synchronises the device first. */
+int shape_set_free(shp_set s);
+
+/* Sizes of a set; any output may be NULL. */
+int shape_set_info(shp_set s, int32_t* n_mol, int64_t* n_atoms, int32_t* max_atoms);
+
+/*
+ * Host copies of the per-molecule mixture masses Z ([n_mol] double) and of
+ * the alias tables ([n_atoms] uint32 thresholds, [n_atoms] uint8 aliases,
+ * indices local to each molecule). Any output may be NULL.
+ */
+int shape_set_tables(shp_set s, double* Z_host, uint32_t* thr_host, uint8_t* alias_host);
+
+/* Monte-Carlo settings shared by the estimators. */
+typedef struct {
+  uint64_t seed;        /* Philox key                                        */
+  uint64_t stream_base; /* item k uses Philox stream stream_base + k          */
+  uint32_t n_samples;   /* per direction, >= 2 (even with SHP_ANTITHETIC)     */
+  uint32_t flags;       /* SHP_SYMMETRIC | SHP_ANTITHETIC                      */
+} shp_mc;
+
+/*
+ * Pair overlaps by importance sampling (Eq. expectation, Eq. var,
+ * Eq. union-is). For pair k, molecule A[ia[k]] and B[ib[k]] moved by
+ * poseB[k] (unit-normalised quaternion w,x,y,z then translation; NULL =
+ * identity): draws n_samples points from A's mixture (tag SHP_TAG_AB) and,
+ * with SHP_SYMMETRIC, n_samples from the posed B's mixture (tag
+ * SHP_TAG_BA), and writes
+ *   est[k][0], se[k][0]   first-order overlap  Z_A mean(m_B)
+ *   est[k][1], se[k][1]   union overlap        Z_A mean(u_A u_B / m_A)
+ * (symmetrised: mean of the two directions, SE 0.5 sqrt(se_AB^2 + se_BA^2)).
+ * SE = Z sqrt(s^2 / n) with the n-1 sample variance; with SHP_ANTITHETIC the
+ * unit is the mean of a reflected pair.
+ *   ia, ib   [n_pairs] int32 device;  poseB [n_pairs][7] float device or NULL
+ *   est, se  [n_pairs][2] double device
+ * Errors: SHP_EINVAL, SHP_ECUDA; out-of-range indices are not checked on
+ * the host (the kernel skips them and leaves their outputs as NaN).
+ */
+int overlap_estimate(shp_set A, const int32_t* ia, shp_set B, const int32_t* ib, int64_t n_pairs,
+                     const float* poseB, const shp_mc* mc, double* est, double* se, void* stream);
+
+/*
+ * Union volume and union self-overlap of molecules S[idx[k]] (Eq. union-is
+ * with f = u/m, and with B = A): samples from the molecule's own mixture
+ * (tag SHP_TAG_SELF, stream mc->stream_base + k) and writes
+ *   vol[k], vol_se[k]         V = Z mean(u/m)
+ *   self_ov[k], self_se[k]    O_AA = Z mean(u^2/m)   (both may be NULL)
+ *   idx   [n] int32 device or NULL (= 0..n-1); outputs [n] double device.
+ * mc->flags: SHP_ANTITHETIC only.
+ */
+int union_volume_estimate(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, double* vol,
+                          double* vol_se, double* self_ov, double* self_se, void* stream);
+
+/*
+ * Closed-form first-order overlap (Eq. fo with heights):
+ *   out[k] = sum_{i in A, j in B} p_i p_j (pi/(a_i+a_j))^{3/2}
+ *            exp(-a_i a_j / (a_i + a_j) |c_i - c'_j|^2)
+ * with c'_j the centres of B[ib[k]] moved by poseB[k] (NULL = identity).
+ *   ia, ib [n_pairs] int32 device; poseB [n_pairs][7] float or NULL;
+ *   out [n_pairs] double device.
+ */
+int fo_overlap(shp_set A, const int32_t* ia, shp_set B, const int32_t* ib, int64_t n_pairs,
+               const float* poseB, double* out, void* stream);
+
+/* Screening settings (Sec. confidence-bounded screening). */
+typedef struct {
+  uint64_t seed;        /* Philox key                                          */
+  uint64_t stream_base; /* pair (q, d) uses stream stream_base + q * n_db + d   */
+  uint32_t n_fixed;     /* samples per direction (fixed budget), >= 2          */
+  uint32_t flags;       /* SHP_ANTITHETIC (both directions are always used)     */
+} shp_screen;
+
+/*
+ * Fixed-budget Tanimoto screen of every query Q[q] against every database
+ * molecule D[d]. Both proposals, n_fixed samples each, give the symmetrised
+ * first-order and union overlaps O; with the self-overlaps S_Q, S_D supplied
+ * by the caller (slot 0 first order, slot 1 union, e.g. fo_overlap of a
+ * molecule with itself and union_volume_estimate's self_ov), writes for pair
+ * p = q * n_db + d and slot s:
+ *   T[p][s]   = O / (S_Q + S_D - O)
+ *   seT[p][s] = (S_Q + S_D) / (S_Q + S_D - O)^2 * SE(O)   (delta method)
+ *   O_out[p][s], seO_out[p][s] (double, may be NULL)
+ *   self_q [n_q][2], self_db [n_db][2] double device
+ *   T, seT [n_q * n_db][2] float device
+ * Work is balanced by a persistent kernel that takes pairs largest-first
+ * from a device queue (library-allocated, stream-ordered scratch).
+ */
+int tanimoto_screen(shp_set Q, shp_set D, const shp_screen* cfg, const double* self_q,
+                    const double* self_db, float* T, float* seT, double* O_out, double* seO_out,
+                    void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHAPE_H */

@@ -1,0 +1,14 @@
+"""Importance-sampling Gaussian shape overlap on B300 (sm_103a).
+
+Python face of the C ABI in ``include/shape.h`` (library ``libshape.so``):
+molecule sets live in device memory, the estimators of Eq. expectation /
+Eq. union-is run in hand-written CUDA kernels, and results come back as
+torch CUDA tensors. ``synth`` builds the seeded synthetic molecule sets.
+"""
+from ._binding import (ANTITHETIC, EXPORTS, LIB_PATH, MAX_ATOMS, SYMMETRIC, TAG_AB, TAG_BA, TAG_SELF,
+                       ShapeError, ShapeSet, fo_overlap, load_library, overlap_estimate, self_overlaps,
+                       shape_set_load, tanimoto_screen, union_volume_estimate)
+
+__all__ = ["ANTITHETIC", "EXPORTS", "LIB_PATH", "MAX_ATOMS", "SYMMETRIC", "TAG_AB", "TAG_BA", "TAG_SELF",
+           "ShapeError", "ShapeSet", "fo_overlap", "load_library", "overlap_estimate", "self_overlaps",
+           "shape_set_load", "tanimoto_screen", "union_volume_estimate"]

@@ -1,0 +1,234 @@
+"""ctypes binding of libshape.so (argument marshalling only).
+
+Every computation runs in the library's CUDA kernels; torch provides device
+memory and the current stream. There is no CPU fallback: without the built
+library or a CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libshape.so")
+
+SHP_OK = 0
+SYMMETRIC = 1
+ANTITHETIC = 2
+TAG_AB, TAG_BA, TAG_SELF = 0, 1, 2
+MAX_ATOMS = 64
+
+# Every entry point declared in include/shape.h.
+EXPORTS = ("shp_last_error", "shp_version", "shape_set_load", "shape_set_free", "shape_set_info",
+           "shape_set_tables", "overlap_estimate", "union_volume_estimate", "fo_overlap",
+           "tanimoto_screen")
+
+_P = ctypes.c_void_p
+
+
+class ShpMC(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("stream_base", ctypes.c_uint64), ("n_samples", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32)]
+
+
+class ShpScreen(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("stream_base", ctypes.c_uint64), ("n_fixed", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32)]
+
+
+_lib = None
+
+
+def load_library():
+    """Load libshape.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2607_20766_b300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    L.shp_last_error.restype = ctypes.c_char_p
+    L.shp_last_error.argtypes = []
+    L.shp_version.restype = ctypes.c_int
+    sig = {
+        "shape_set_load": [_P, _P, _P, ctypes.c_double, _P, ctypes.c_int32, _P, _P],
+        "shape_set_free": [_P],
+        "shape_set_info": [_P, _P, _P, _P],
+        "shape_set_tables": [_P, _P, _P, _P],
+        "overlap_estimate": [_P, _P, _P, _P, ctypes.c_int64, _P, _P, _P, _P, _P],
+        "union_volume_estimate": [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P],
+        "fo_overlap": [_P, _P, _P, _P, ctypes.c_int64, _P, _P, _P],
+        "tanimoto_screen": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class ShapeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libshape status {status}: {msg}")
+        self.status = status
+
+
+def _check(rc: int):
+    if rc != SHP_OK:
+        raise ShapeError(rc, load_library().shp_last_error().decode())
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _device_i32(x, device) -> torch.Tensor:
+    if isinstance(x, torch.Tensor):
+        t = x.to(device=device, dtype=torch.int32)
+    else:
+        t = torch.as_tensor(np.asarray(x, dtype=np.int32), device=device)
+    return t.contiguous()
+
+
+class ShapeSet:
+    """A molecule set resident in device memory (opaque shp_set handle)."""
+
+    def __init__(self, handle: int, n_mol: int, n_atoms: int, counts: np.ndarray, device: torch.device):
+        self.handle = ctypes.c_void_p(handle)
+        self.n_mol = n_mol
+        self.n_atoms = n_atoms
+        self.counts = counts
+        self.device = device
+
+    def tables(self):
+        """Host copies: (Z [n_mol] float64, thr [n_atoms] uint32, alias [n_atoms] uint8)."""
+        Z = np.empty(self.n_mol, np.float64)
+        thr = np.empty(self.n_atoms, np.uint32)
+        al = np.empty(self.n_atoms, np.uint8)
+        _check(load_library().shape_set_tables(self.handle, Z.ctypes.data, thr.ctypes.data, al.ctypes.data))
+        return Z, thr, al
+
+    def free(self):
+        if self.handle is not None and self.handle.value:
+            load_library().shape_set_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def shape_set_load(ms, c_alpha: float = 2.41798793, stream=None, device=None) -> ShapeSet:
+    """Upload a MolSet (host arrays) to the current CUDA device."""
+    if not torch.cuda.is_available():
+        raise RuntimeError("shape_set_load needs a CUDA device")
+    L = load_library()
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    xyz = np.ascontiguousarray(ms.xyz, dtype=np.float32)
+    rad = np.ascontiguousarray(ms.radius, dtype=np.float32)
+    hgt = None if ms.height is None else np.ascontiguousarray(ms.height, dtype=np.float32)
+    off = np.ascontiguousarray(ms.offsets, dtype=np.int32)
+    h = ctypes.c_void_p()
+    with torch.cuda.device(device):
+        _check(L.shape_set_load(xyz.ctypes.data, rad.ctypes.data, None if hgt is None else hgt.ctypes.data,
+                                c_alpha, off.ctypes.data, len(off) - 1, _stream(stream), ctypes.byref(h)))
+    return ShapeSet(h.value, len(off) - 1, int(off[-1]), np.diff(off).astype(np.int32), device)
+
+
+def overlap_estimate(A: ShapeSet, ia, B: ShapeSet, ib, seed: int, n_samples: int, flags: int = SYMMETRIC,
+                     stream_base: int = 0, pose=None, stream=None, out=None):
+    """(est, se): [n_pairs, 2] float64 device tensors; slot 0 first order, slot 1 union."""
+    dev = A.device
+    ia = _device_i32(ia, dev)
+    ib = _device_i32(ib, dev)
+    n = ia.numel()
+    if ib.numel() != n:
+        raise ValueError("ia and ib differ in length")
+    if pose is not None:
+        pose = torch.as_tensor(pose, dtype=torch.float32, device=dev).contiguous()
+        if pose.shape != (n, 7):
+            raise ValueError("pose must be [n_pairs, 7]")
+    est, se = out if out is not None else (torch.empty((n, 2), dtype=torch.float64, device=dev),
+                                           torch.empty((n, 2), dtype=torch.float64, device=dev))
+    mc = ShpMC(seed, stream_base, n_samples, flags)
+    _check(load_library().overlap_estimate(A.handle, _dptr(ia), B.handle, _dptr(ib), n, _dptr(pose),
+                                           ctypes.byref(mc), _dptr(est), _dptr(se), _stream(stream)))
+    return est, se
+
+
+def union_volume_estimate(S: ShapeSet, idx=None, seed: int = 0, n_samples: int = 4096, flags: int = 0,
+                          stream_base: int = 0, stream=None, out=None):
+    """(vol, vol_se, self_overlap, self_se): [n] float64 device tensors."""
+    dev = S.device
+    if idx is not None:
+        idx = _device_i32(idx, dev)
+        n = idx.numel()
+    else:
+        n = S.n_mol
+    outs = out if out is not None else tuple(torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4))
+    mc = ShpMC(seed, stream_base, n_samples, flags)
+    _check(load_library().union_volume_estimate(S.handle, _dptr(idx), n, ctypes.byref(mc), *(_dptr(t) for t in outs),
+                                                _stream(stream)))
+    return outs
+
+
+def fo_overlap(A: ShapeSet, ia, B: ShapeSet, ib, pose=None, stream=None, out=None):
+    """Closed-form first-order overlaps, [n_pairs] float64 device tensor."""
+    dev = A.device
+    ia = _device_i32(ia, dev)
+    ib = _device_i32(ib, dev)
+    n = ia.numel()
+    if pose is not None:
+        pose = torch.as_tensor(pose, dtype=torch.float32, device=dev).contiguous()
+    res = out if out is not None else torch.empty(n, dtype=torch.float64, device=dev)
+    _check(load_library().fo_overlap(A.handle, _dptr(ia), B.handle, _dptr(ib), n, _dptr(pose), _dptr(res),
+                                     _stream(stream)))
+    return res
+
+
+def tanimoto_screen(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: torch.Tensor, seed: int,
+                    n_fixed: int, flags: int = 0, stream_base: int = 0, stream=None, with_overlaps: bool = False,
+                    out=None):
+    """Fixed-budget screen. Returns dict T, seT ([n_q * n_db, 2] float32) and,
+    with with_overlaps, O, seO ([n_q * n_db, 2] float64)."""
+    dev = Q.device
+    npairs = Q.n_mol * D.n_mol
+    if out is None:
+        out = dict(T=torch.empty((npairs, 2), dtype=torch.float32, device=dev),
+                   seT=torch.empty((npairs, 2), dtype=torch.float32, device=dev))
+        if with_overlaps:
+            out["O"] = torch.empty((npairs, 2), dtype=torch.float64, device=dev)
+            out["seO"] = torch.empty((npairs, 2), dtype=torch.float64, device=dev)
+    cfg = ShpScreen(seed, stream_base, n_fixed, flags)
+    self_q = self_q.to(device=dev, dtype=torch.float64).contiguous()
+    self_db = self_db.to(device=dev, dtype=torch.float64).contiguous()
+    _check(load_library().tanimoto_screen(Q.handle, D.handle, ctypes.byref(cfg), _dptr(self_q), _dptr(self_db),
+                                          _dptr(out["T"]), _dptr(out["seT"]), _dptr(out.get("O")),
+                                          _dptr(out.get("seO")), _stream(stream)))
+    return out
+
+
+def self_overlaps(S: ShapeSet, seed: int, n_samples: int, stream_base: int = 0, stream=None):
+    """[n_mol, 2] float64 device tensor: slot 0 closed-form first-order
+    self-overlap, slot 1 union self-overlap estimate (n_samples draws)."""
+    dev = S.device
+    idx = torch.arange(S.n_mol, dtype=torch.int32, device=dev)
+    out = torch.empty((S.n_mol, 2), dtype=torch.float64, device=dev)
+    fo = fo_overlap(S, idx, S, idx, stream=stream)
+    vol, vse, so, sse = union_volume_estimate(S, idx, seed=seed, n_samples=n_samples, stream_base=stream_base,
+                                              stream=stream)
+    out[:, 0] = fo
+    out[:, 1] = so
+    return out

@@ -1,0 +1,60 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "shape.h"
+
+struct shp_set_s {
+  int device = 0;
+  int32_t n_mol = 0;
+  int64_t n_atoms = 0;
+  int32_t max_atoms = 0;
+  // device arrays (owned)
+  float4* atom = nullptr;    // [n_atoms] x, y, z, alpha
+  float2* aux = nullptr;     // [n_atoms] sigma = 1/sqrt(2 alpha), log2 p
+  uint32_t* thr = nullptr;   // [n_atoms] alias thresholds
+  uint8_t* alias = nullptr;  // [n_atoms] alias targets (local index)
+  int32_t* off = nullptr;    // [n_mol + 1]
+  double* Z = nullptr;       // [n_mol] mixture mass
+  int32_t* order = nullptr;  // [n_mol] molecule ids, atom count descending
+  // host mirrors
+  std::vector<int32_t> h_off;
+  std::vector<double> h_Z;
+  std::vector<uint32_t> h_thr;
+  std::vector<uint8_t> h_alias;
+};
+
+namespace shp {
+
+// Read-only device view of a set, passed to kernels by value.
+struct SetView {
+  const float4* atom;
+  const float2* aux;
+  const uint32_t* thr;
+  const uint8_t* alias;
+  const int32_t* off;
+  const double* Z;
+  int32_t n_mol;
+};
+
+inline SetView view(const shp_set_s* s) {
+  return SetView{s->atom, s->aux, s->thr, s->alias, s->off, s->Z, s->n_mol};
+}
+
+void set_error(const char* fmt, ...);
+void clear_error();
+int cuda_fail(cudaError_t e, const char* what);
+
+}  // namespace shp
+
+#define SHP_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return shp::cuda_fail(e_, #call); \
+  } while (0)

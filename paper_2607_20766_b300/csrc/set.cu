@@ -1,0 +1,208 @@
+// Molecule sets: validation, per-atom parameters, mixture masses and alias
+// tables (Eq. occ, Eq. expectation), device upload. Host code.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <numeric>
+
+#include "internal.h"
+
+namespace shp {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+void clear_error() { g_err.clear(); }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? SHP_ENOMEM : SHP_ECUDA;
+}
+
+// Integer alias table for weights v[0..n-1] (n <= 64). Column masses are in
+// units of 2^-32 of one column: M_i = floor((v_i / Z) * n 2^32), the
+// rounding remainder goes to the last atom; small (M < 2^32) and large
+// worklists are FIFO in atom order, and a large atom stays at the head of
+// its list until its residual mass turns small. Full columns get threshold
+// 2^32 - 1 and alias themselves.
+static void build_alias(int n, const double* v, uint32_t* thr, uint8_t* alias) {
+  const uint64_t kOne = 1ull << 32;
+  double Z = 0.0;
+  for (int i = 0; i < n; ++i) Z += v[i];
+  const double scale = (double)n * 4294967296.0;
+  uint64_t mass[SHP_MAX_ATOMS];
+  uint64_t sum = 0;
+  for (int i = 0; i < n; ++i) {
+    mass[i] = (uint64_t)std::floor((v[i] / Z) * scale);
+    sum += mass[i];
+  }
+  mass[n - 1] += (uint64_t)n * kOne - sum;
+  int sq[SHP_MAX_ATOMS], lq[SHP_MAX_ATOMS];
+  int sh = 0, st = 0, lh = 0, lt = 0;
+  for (int i = 0; i < n; ++i) (mass[i] < kOne ? sq[st++] : lq[lt++]) = i;
+  while (sh < st && lh < lt) {
+    const int s = sq[sh++];
+    const int l = lq[lh];
+    thr[s] = (uint32_t)mass[s];
+    alias[s] = (uint8_t)l;
+    mass[l] -= kOne - mass[s];
+    if (mass[l] < kOne) {
+      ++lh;
+      sq[st++] = l;
+    }
+  }
+  for (; sh < st; ++sh) { thr[sq[sh]] = 0xFFFFFFFFu; alias[sq[sh]] = (uint8_t)sq[sh]; }
+  for (; lh < lt; ++lh) { thr[lq[lh]] = 0xFFFFFFFFu; alias[lq[lh]] = (uint8_t)lq[lh]; }
+}
+
+template <class T>
+static int dev_upload(T** dst, const T* src, size_t count, cudaStream_t st) {
+  if (count == 0) { *dst = nullptr; return SHP_OK; }
+  SHP_CUDA(cudaMalloc((void**)dst, count * sizeof(T)));
+  SHP_CUDA(cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, st));
+  return SHP_OK;
+}
+
+static void free_set_memory(shp_set_s* s) {
+  cudaFree(s->atom); cudaFree(s->aux); cudaFree(s->thr); cudaFree(s->alias);
+  cudaFree(s->off); cudaFree(s->Z); cudaFree(s->order);
+  s->atom = nullptr; s->aux = nullptr; s->thr = nullptr; s->alias = nullptr;
+  s->off = nullptr; s->Z = nullptr; s->order = nullptr;
+}
+
+}  // namespace shp
+
+using namespace shp;
+
+extern "C" const char* shp_last_error(void) { return g_err.c_str(); }
+
+extern "C" int shp_version(void) { return 1; }
+
+extern "C" int shape_set_load(const float* xyz, const float* radius, const float* height,
+                              double c_alpha, const int32_t* offsets, int32_t n_mol, void* stream,
+                              shp_set* out) {
+  clear_error();
+  if (!out || !offsets || n_mol < 0) {
+    set_error("shape_set_load: NULL output/offsets or negative n_mol");
+    return SHP_EINVAL;
+  }
+  *out = nullptr;
+  if (offsets[0] != 0) { set_error("shape_set_load: offsets[0] must be 0"); return SHP_EINVAL; }
+  int32_t max_atoms = 0;
+  for (int32_t m = 0; m < n_mol; ++m) {
+    const int32_t c = offsets[m + 1] - offsets[m];
+    if (c < 1 || c > SHP_MAX_ATOMS) {
+      set_error("shape_set_load: molecule %d has %d atoms (allowed 1..%d)", m, c, SHP_MAX_ATOMS);
+      return SHP_ERANGE;
+    }
+    max_atoms = std::max(max_atoms, c);
+  }
+  const int64_t n_atoms = offsets[n_mol];
+  if (n_atoms > 0 && (!xyz || !radius)) { set_error("shape_set_load: NULL xyz/radius"); return SHP_EINVAL; }
+  const double ca = c_alpha > 0 ? c_alpha : 2.41798793;
+  const double kPi = 3.14159265358979323846;
+
+  auto* s = new (std::nothrow) shp_set_s;
+  if (!s) { set_error("shape_set_load: host allocation failed"); return SHP_ENOMEM; }
+  SHP_CUDA(cudaGetDevice(&s->device));
+  s->n_mol = n_mol;
+  s->n_atoms = n_atoms;
+  s->max_atoms = max_atoms;
+  s->h_off.assign(offsets, offsets + n_mol + 1);
+  s->h_Z.assign(n_mol, 0.0);
+  s->h_thr.assign(n_atoms, 0u);
+  s->h_alias.assign(n_atoms, 0);
+  std::vector<float4> atom(n_atoms);
+  std::vector<float2> aux(n_atoms);
+  std::vector<double> v(SHP_MAX_ATOMS);
+  for (int32_t m = 0; m < n_mol; ++m) {
+    const int32_t a0 = offsets[m], n = offsets[m + 1] - a0;
+    double Z = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const int64_t a = a0 + i;
+      const double x = xyz[3 * a], y = xyz[3 * a + 1], z = xyz[3 * a + 2];
+      const double R = radius[a];
+      const double p = height ? (double)height[a] : 2.0 * std::sqrt(2.0);
+      if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z) || !(R > 0) ||
+          !std::isfinite(R) || !(p > 0) || !std::isfinite(p)) {
+        set_error("shape_set_load: atom %lld of molecule %d has a non-finite or non-positive value",
+                  (long long)i, m);
+        delete s;
+        return SHP_EINVAL;
+      }
+      const double alpha = ca / (R * R);
+      const double t = kPi / alpha;
+      v[i] = p * t * std::sqrt(t);
+      Z += v[i];
+      atom[a] = make_float4((float)x, (float)y, (float)z, (float)alpha);
+      aux[a] = make_float2((float)(1.0 / std::sqrt(2.0 * alpha)), (float)std::log2(p));
+    }
+    s->h_Z[m] = Z;
+    build_alias(n, v.data(), &s->h_thr[a0], &s->h_alias[a0]);
+  }
+  std::vector<int32_t> order(n_mol);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
+  });
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = SHP_OK;
+  if (!rc) rc = dev_upload(&s->atom, atom.data(), atom.size(), st);
+  if (!rc) rc = dev_upload(&s->aux, aux.data(), aux.size(), st);
+  if (!rc) rc = dev_upload(&s->thr, s->h_thr.data(), s->h_thr.size(), st);
+  if (!rc) rc = dev_upload(&s->alias, s->h_alias.data(), s->h_alias.size(), st);
+  if (!rc) rc = dev_upload(&s->off, s->h_off.data(), s->h_off.size(), st);
+  if (!rc) rc = dev_upload(&s->Z, s->h_Z.data(), s->h_Z.size(), st);
+  if (!rc) rc = dev_upload(&s->order, order.data(), order.size(), st);
+  if (!rc) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "shape_set_load: cudaStreamSynchronize");
+  }
+  if (rc) {
+    free_set_memory(s);
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return SHP_OK;
+}
+
+extern "C" int shape_set_free(shp_set s) {
+  clear_error();
+  if (!s) return SHP_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != s->device) cudaSetDevice(s->device);
+  cudaDeviceSynchronize();
+  free_set_memory(s);
+  if (prev != s->device) cudaSetDevice(prev);
+  delete s;
+  return SHP_OK;
+}
+
+extern "C" int shape_set_info(shp_set s, int32_t* n_mol, int64_t* n_atoms, int32_t* max_atoms) {
+  clear_error();
+  if (!s) { set_error("shape_set_info: NULL set"); return SHP_EINVAL; }
+  if (n_mol) *n_mol = s->n_mol;
+  if (n_atoms) *n_atoms = s->n_atoms;
+  if (max_atoms) *max_atoms = s->max_atoms;
+  return SHP_OK;
+}
+
+extern "C" int shape_set_tables(shp_set s, double* Z, uint32_t* thr, uint8_t* alias) {
+  clear_error();
+  if (!s) { set_error("shape_set_tables: NULL set"); return SHP_EINVAL; }
+  if (Z && s->n_mol) std::memcpy(Z, s->h_Z.data(), sizeof(double) * s->n_mol);
+  if (thr && s->n_atoms) std::memcpy(thr, s->h_thr.data(), sizeof(uint32_t) * s->n_atoms);
+  if (alias && s->n_atoms) std::memcpy(alias, s->h_alias.data(), s->n_atoms);
+  return SHP_OK;
+}
