@@ -154,15 +154,28 @@ int fo_overlap(shp_set A, const int32_t* ia, shp_set B, const int32_t* ib, int64
 
 /* Screening settings (Sec. confidence-bounded screening). */
 typedef struct {
-  uint64_t seed;        /* Philox key                                          */
-  uint64_t stream_base; /* pair (q, d) uses stream stream_base + q * n_db + d   */
-  uint32_t n_fixed;     /* samples per direction (fixed budget), >= 2          */
-  uint32_t flags;       /* SHP_ANTITHETIC (both directions are always used)     */
+  uint64_t seed;        /* Philox key                                              */
+  uint64_t stream_base; /* pair (q, d) uses stream stream_base + q * n_db + d       */
+  uint32_t n_fixed;     /* > 0: fixed budget, samples per direction (>= 2);
+                           0: adaptive (fields below)                              */
+  uint32_t flags;       /* SHP_ANTITHETIC (fixed budget only; both directions are
+                           always used)                                            */
+  float tau;            /* adaptive: stop a pair once SE(T) <= tau                 */
+  uint32_t round;       /* adaptive: samples per direction per round, a multiple
+                           of 256                                                  */
+  uint32_t min_n;       /* adaptive: first check after min_n samples per direction
+                           (a multiple of round, >= round)                         */
+  uint32_t cap;         /* adaptive: at most cap samples per direction (a multiple
+                           of round, >= min_n)                                     */
+  uint32_t watch;       /* adaptive: which Tanimoto the rule watches, 1 = union,
+                           0 = first order                                         */
+  int32_t variant;      /* launch variant, -1 = the tuned (or built-in) default,
+                           else 0 .. shp_screen_variants()-1                      */
 } shp_screen;
 
 /*
- * Fixed-budget Tanimoto screen of every query Q[q] against every database
- * molecule D[d]. Both proposals, n_fixed samples each, give the symmetrised
+ * Tanimoto screen of every query Q[q] against every database molecule D[d]
+ * (Sec. confidence-bounded screening). Both proposals give the symmetrised
  * first-order and union overlaps O; with the self-overlaps S_Q, S_D supplied
  * by the caller (slot 0 first order, slot 1 union, e.g. fo_overlap of a
  * molecule with itself and union_volume_estimate's self_ov), writes for pair
@@ -170,6 +183,12 @@ typedef struct {
  *   T[p][s]   = O / (S_Q + S_D - O)
  *   seT[p][s] = (S_Q + S_D) / (S_Q + S_D - O)^2 * SE(O)   (delta method)
  *   O_out[p][s], seO_out[p][s] (double, may be NULL)
+ *   n_used[p] samples drawn per direction (may be NULL)
+ * Fixed budget: n_fixed samples per direction. Adaptive (n_fixed == 0):
+ * rounds of `round` samples per direction are drawn until, after at least
+ * min_n, the watched SE(T) (computed in FP32 from the running sums) is
+ * <= tau, or cap is reached; the samples are the first n_used of the same
+ * streams a fixed budget would draw.
  *   self_q [n_q][2], self_db [n_db][2] double device
  *   T, seT [n_q * n_db][2] float device
  * Work is balanced by a persistent kernel that takes pairs largest-first
@@ -177,7 +196,22 @@ typedef struct {
  */
 int tanimoto_screen(shp_set Q, shp_set D, const shp_screen* cfg, const double* self_q,
                     const double* self_db, float* T, float* seT, double* O_out, double* seO_out,
-                    void* stream);
+                    uint32_t* n_used, void* stream);
+
+/* Number of compiled launch variants of the screen kernel. */
+int shp_screen_variants(void);
+
+/*
+ * Autotuner: times every launch variant valid for cfg (fixed or adaptive) on
+ * n_sample pairs spread evenly over the screen (outputs go to the caller's
+ * T/seT/n_used buffers), makes the fastest the default of this device for
+ * that mode, and returns its id in *best. timings_ms [shp_screen_variants()]
+ * receives each variant's time (or -1 if not valid); may be NULL.
+ * Synchronises `stream`.
+ */
+int tanimoto_screen_tune(shp_set Q, shp_set D, const shp_screen* cfg, const double* self_q,
+                         const double* self_db, float* T, float* seT, uint32_t* n_used,
+                         int64_t n_sample, float* timings_ms, int32_t* best, void* stream);
 
 #ifdef __cplusplus
 }

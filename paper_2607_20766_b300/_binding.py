@@ -24,7 +24,7 @@ MAX_ATOMS = 64
 # Every entry point declared in include/shape.h.
 EXPORTS = ("shp_last_error", "shp_version", "shape_set_load", "shape_set_free", "shape_set_info",
            "shape_set_tables", "overlap_estimate", "union_volume_estimate", "fo_overlap",
-           "tanimoto_screen")
+           "tanimoto_screen", "shp_screen_variants", "tanimoto_screen_tune")
 
 _P = ctypes.c_void_p
 
@@ -36,7 +36,9 @@ class ShpMC(ctypes.Structure):
 
 class ShpScreen(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("stream_base", ctypes.c_uint64), ("n_fixed", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("tau", ctypes.c_float), ("round", ctypes.c_uint32),
+                ("min_n", ctypes.c_uint32), ("cap", ctypes.c_uint32), ("watch", ctypes.c_uint32),
+                ("variant", ctypes.c_int32)]
 
 
 _lib = None
@@ -61,7 +63,9 @@ def load_library():
         "overlap_estimate": [_P, _P, _P, _P, ctypes.c_int64, _P, _P, _P, _P, _P],
         "union_volume_estimate": [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P],
         "fo_overlap": [_P, _P, _P, _P, ctypes.c_int64, _P, _P, _P],
-        "tanimoto_screen": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+        "tanimoto_screen": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+        "shp_screen_variants": [],
+        "tanimoto_screen_tune": [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int64, _P, _P, _P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -198,26 +202,63 @@ def fo_overlap(A: ShapeSet, ia, B: ShapeSet, ib, pose=None, stream=None, out=Non
     return res
 
 
+def screen_config(seed: int, n_fixed: int = 0, tau: float = 0.005, round: int = 256, min_n: int = 1024,
+                  cap: int = 65536, watch: int = 1, flags: int = 0, stream_base: int = 0,
+                  variant: int = -1) -> ShpScreen:
+    """A shp_screen: fixed budget when n_fixed > 0, else adaptive (tau, round, min_n, cap, watch)."""
+    return ShpScreen(seed, stream_base, n_fixed, flags, tau, round, min_n, cap, watch, variant)
+
+
 def tanimoto_screen(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: torch.Tensor, seed: int,
-                    n_fixed: int, flags: int = 0, stream_base: int = 0, stream=None, with_overlaps: bool = False,
-                    out=None):
-    """Fixed-budget screen. Returns dict T, seT ([n_q * n_db, 2] float32) and,
-    with with_overlaps, O, seO ([n_q * n_db, 2] float64)."""
+                    n_fixed: int = 0, flags: int = 0, stream_base: int = 0, stream=None, with_overlaps: bool = False,
+                    out=None, tau: float = 0.005, round: int = 256, min_n: int = 1024, cap: int = 65536,
+                    watch: int = 1, variant: int = -1):
+    """Screen every query against every database molecule (fixed budget when
+    n_fixed > 0, else adaptive). Returns dict T, seT ([n_q * n_db, 2]
+    float32), n_used ([n_q * n_db] int32 view of uint32) and, with
+    with_overlaps, O, seO ([n_q * n_db, 2] float64)."""
     dev = Q.device
     npairs = Q.n_mol * D.n_mol
     if out is None:
         out = dict(T=torch.empty((npairs, 2), dtype=torch.float32, device=dev),
-                   seT=torch.empty((npairs, 2), dtype=torch.float32, device=dev))
+                   seT=torch.empty((npairs, 2), dtype=torch.float32, device=dev),
+                   n_used=torch.empty(npairs, dtype=torch.int32, device=dev))
         if with_overlaps:
             out["O"] = torch.empty((npairs, 2), dtype=torch.float64, device=dev)
             out["seO"] = torch.empty((npairs, 2), dtype=torch.float64, device=dev)
-    cfg = ShpScreen(seed, stream_base, n_fixed, flags)
+    cfg = screen_config(seed, n_fixed, tau, round, min_n, cap, watch, flags, stream_base, variant)
     self_q = self_q.to(device=dev, dtype=torch.float64).contiguous()
     self_db = self_db.to(device=dev, dtype=torch.float64).contiguous()
     _check(load_library().tanimoto_screen(Q.handle, D.handle, ctypes.byref(cfg), _dptr(self_q), _dptr(self_db),
                                           _dptr(out["T"]), _dptr(out["seT"]), _dptr(out.get("O")),
-                                          _dptr(out.get("seO")), _stream(stream)))
+                                          _dptr(out.get("seO")), _dptr(out.get("n_used")), _stream(stream)))
     return out
+
+
+def screen_variants() -> int:
+    return load_library().shp_screen_variants()
+
+
+def tanimoto_screen_tune(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: torch.Tensor, seed: int,
+                         n_fixed: int = 0, n_sample: int = 4096, stream=None, tau: float = 0.005, round: int = 256,
+                         min_n: int = 1024, cap: int = 65536, watch: int = 1):
+    """Autotune the screen's launch variant on n_sample pairs; returns
+    (best variant, per-variant milliseconds, -1 where not valid)."""
+    dev = Q.device
+    npairs = Q.n_mol * D.n_mol
+    T = torch.empty((npairs, 2), dtype=torch.float32, device=dev)
+    seT = torch.empty((npairs, 2), dtype=torch.float32, device=dev)
+    nu = torch.empty(npairs, dtype=torch.int32, device=dev)
+    cfg = screen_config(seed, n_fixed, tau, round, min_n, cap, watch)
+    nv = screen_variants()
+    times = np.empty(nv, np.float32)
+    best = ctypes.c_int32(-1)
+    self_q = self_q.to(device=dev, dtype=torch.float64).contiguous()
+    self_db = self_db.to(device=dev, dtype=torch.float64).contiguous()
+    _check(load_library().tanimoto_screen_tune(Q.handle, D.handle, ctypes.byref(cfg), _dptr(self_q), _dptr(self_db),
+                                               _dptr(T), _dptr(seT), _dptr(nu), n_sample, times.ctypes.data,
+                                               ctypes.byref(best), _stream(stream)))
+    return best.value, times
 
 
 def self_overlaps(S: ShapeSet, seed: int, n_samples: int, stream_base: int = 0, stream=None):

@@ -1,19 +1,25 @@
 // Importance-sampling estimators on sm_103a: pair overlaps (first order and
-// union), union volumes / self-overlaps, and the fixed-budget Tanimoto
-// screen (Eq. expectation, Eq. var, Eq. union-is, Sec. confidence-bounded
-// screening).
+// union), union volumes / self-overlaps, and the fixed-budget and adaptive
+// Tanimoto screens (Eq. expectation, Eq. var, Eq. union-is, Sec.
+// confidence-bounded screening).
 //
 // Work decomposition: one warp owns one work item (a molecule pair, or one
 // molecule for volumes) and runs all of its samples; warps take items from a
-// device queue (persistent kernel, items largest-first for screens). Per
+// device queue (persistent kernel; screens take pairs largest-first). Per
 // item and direction the warp stages, in shared memory, the sampled
 // molecule's component table (centre, sigma, alias) and both molecules'
 // Gaussian coefficients in the frame of the sampled molecule's centroid.
-// Each lane then draws 4 sample pairs per batch (256 samples per warp) and
-// evaluates every atom of both molecules with packed FP32x2 FMAs and one
-// SFU exp2 per Gaussian; FP32 batch partials are folded into a hi/lo pair
-// per lane and reduced over the warp in FP64.
+// Each lane then draws SP sample pairs per batch (64 SP samples per warp)
+// and evaluates every atom of both molecules: four FP32 FMAs for the
+// exponent, one SFU exp2, a packed FP32x2 add for the first-order sum and an
+// FMA for the union product. FP32 batch partials of values shifted by a
+// warp-uniform constant are folded into a hi/lo pair per lane and reduced
+// over the warp with compensated FP32 sums; the epilogue runs in FP64.
+//
+// Launch variants (SP, exponent form, warps per CTA) are template
+// instances; tanimoto_screen_tune times them and keeps the fastest.
 #include <cmath>
+#include <mutex>
 
 #include "device.cuh"
 #include "internal.h"
@@ -21,18 +27,28 @@
 namespace shp {
 namespace {
 
-constexpr int kSP = 4;     // sample pairs per lane per batch
-constexpr int kWarps = 8;  // warps per CTA
-constexpr int kThreads = kWarps * 32;
+// Gaussian coefficients of one atom (see Coef in device.cuh for the
+// meaning); a and c0 are also stored twice for the packed exponent form.
+struct __align__(16) CoefT {
+  float2 a2, c2;
+  float bx, by, bz, pad;
+};
+
+// Running per-lane sums of one proposal direction: shifted sums
+// {fa, fa^2, fb, fb^2} as hi + lo pairs, and the warp-uniform shifts.
+struct DirState {
+  float hi[4], lo[4];
+  float K[2];
+};
 
 struct __align__(16) WarpTables {
-  Coef x[SHP_MAX_ATOMS];       // sampled molecule
-  Coef y[SHP_MAX_ATOMS];       // other molecule
+  CoefT x[SHP_MAX_ATOMS];      // sampled molecule
+  CoefT y[SHP_MAX_ATOMS];      // other molecule
   float4 samp[SHP_MAX_ATOMS];  // sampled molecule: centre - origin, sigma
   uint32_t thr[SHP_MAX_ATOMS];
   uint8_t alias[SHP_MAX_ATOMS];
+  DirState st[2][32];          // per-lane running sums of both directions
 };
-constexpr size_t kSmemBytes = sizeof(WarpTables) * kWarps;
 
 struct MolRef {
   int32_t a0, n;
@@ -54,7 +70,8 @@ __device__ float3 centroid(const SetView& S, MolRef M, const Pose& P, int lane) 
   return make_float3(warp_sum(sx) * inv, warp_sum(sy) * inv, warp_sum(sz) * inv);
 }
 
-__device__ void stage_coef(Coef* dst, const SetView& S, MolRef M, const Pose& P, float3 o, int lane) {
+// log2 g(r) = a |r'|^2 + b . r' + c0 with r' = r - o (expanded form).
+__device__ void stage_coef(CoefT* dst, const SetView& S, MolRef M, const Pose& P, float3 o, int lane) {
   const float kLog2e = 1.4426950408889634f;
   for (int i = lane; i < M.n; i += 32) {
     const float4 a = S.atom[M.a0 + i];
@@ -63,15 +80,14 @@ __device__ void stage_coef(Coef* dst, const SetView& S, MolRef M, const Pose& P,
     const float dx = c.x - o.x, dy = c.y - o.y, dz = c.z - o.z;
     const float al = a.w * kLog2e;
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    Coef k;
-    k.a = make_float2(-al, -al);
-    const float bx = 2.f * al * dx, by = 2.f * al * dy, bz = 2.f * al * dz;
-    k.bx = make_float2(bx, bx);
-    k.by = make_float2(by, by);
-    k.bz = make_float2(bz, bz);
     const float c0 = fmaf(-al, d2, lp);
-    k.c0 = make_float2(c0, c0);
-    k.pad = make_float2(0.f, 0.f);
+    CoefT k;
+    k.a2 = make_float2(-al, -al);
+    k.c2 = make_float2(c0, c0);
+    k.bx = 2.f * al * dx;
+    k.by = 2.f * al * dy;
+    k.bz = 2.f * al * dz;
+    k.pad = 0.f;
     dst[i] = k;
   }
 }
@@ -86,6 +102,20 @@ __device__ void stage_samp(WarpTables& T, const SetView& S, MolRef M, const Pose
   }
 }
 
+// Stage one direction: X sampled (its coefficients, centres and alias
+// table), Y evaluated, in the frame of X's centroid. Poses (NULL =
+// identity) are rebuilt here so no pose is held in registers while sampling.
+__device__ __noinline__ void stage_direction(WarpTables& T, const SetView& SX, MolRef MX, const float* pose_x,
+                                             const SetView* SY, MolRef MY, const float* pose_y, int lane) {
+  const Pose PX = make_pose(pose_x), PY = make_pose(pose_y);
+  const float3 o = centroid(SX, MX, PX, lane);
+  __syncwarp();
+  stage_coef(T.x, SX, MX, PX, o, lane);
+  if (SY) stage_coef(T.y, *SY, MY, PY, o, lane);
+  stage_samp(T, SX, MX, PX, o, lane);
+  __syncwarp();
+}
+
 // Alias pick: column j = hi32(x n); keep j if lo32(x n) < thr_j.
 __device__ __forceinline__ int pick(const WarpTables& T, int n, uint32_t x) {
   const unsigned long long prod = (unsigned long long)x * (unsigned)n;
@@ -93,22 +123,30 @@ __device__ __forceinline__ int pick(const WarpTables& T, int n, uint32_t x) {
   return f < T.thr[j] ? (int)j : (int)T.alias[j];
 }
 
-// m = sum g and q = prod (1 - g) over one molecule's Gaussians, for kSP
-// sample pairs held as packed (even, odd) sample float2s.
-__device__ __forceinline__ void eval_table(const Coef* __restrict__ tab, int n,
-                                           const float2 (&rx)[kSP], const float2 (&ry)[kSP],
-                                           const float2 (&rz)[kSP], const float2 (&rr)[kSP],
-                                           float2 (&m)[kSP], float2 (&q)[kSP]) {
+// m = sum g and q = prod (1 - g) over one molecule's Gaussians for SP
+// sample pairs (even sample in .x, odd in .y). kForm 0: four scalar FMAs
+// for the exponent; kForm 1: a packed FMA for a|r|^2 + c0, then three
+// scalar FMAs.
+template <int SP, int kForm>
+__device__ __forceinline__ void eval_table(const CoefT* __restrict__ tab, int n, const float2 (&rx)[SP],
+                                           const float2 (&ry)[SP], const float2 (&rz)[SP],
+                                           const float2 (&rr)[SP], float2 (&m)[SP], float2 (&q)[SP]) {
 #pragma unroll 2
   for (int j = 0; j < n; ++j) {
-    const float2 ka = tab[j].a, kbx = tab[j].bx, kby = tab[j].by, kbz = tab[j].bz, kc = tab[j].c0;
+    const float4 k0 = *reinterpret_cast<const float4*>(&tab[j].a2);
+    const float4 k1 = *reinterpret_cast<const float4*>(&tab[j].bx);
 #pragma unroll
-    for (int p = 0; p < kSP; ++p) {
-      float2 e = __ffma2_rn(ka, rr[p], kc);
-      e = __ffma2_rn(kbx, rx[p], e);
-      e = __ffma2_rn(kby, ry[p], e);
-      e = __ffma2_rn(kbz, rz[p], e);
-      const float2 g = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+    for (int p = 0; p < SP; ++p) {
+      float ex, ey;
+      if (kForm == 0) {
+        ex = fmaf(k1.z, rz[p].x, fmaf(k1.y, ry[p].x, fmaf(k1.x, rx[p].x, fmaf(k0.x, rr[p].x, k0.z))));
+        ey = fmaf(k1.z, rz[p].y, fmaf(k1.y, ry[p].y, fmaf(k1.x, rx[p].y, fmaf(k0.x, rr[p].y, k0.z))));
+      } else {
+        const float2 e = __ffma2_rn(make_float2(k0.x, k0.y), rr[p], make_float2(k0.z, k0.w));
+        ex = fmaf(k1.z, rz[p].x, fmaf(k1.y, ry[p].x, fmaf(k1.x, rx[p].x, e.x)));
+        ey = fmaf(k1.z, rz[p].y, fmaf(k1.y, ry[p].y, fmaf(k1.x, rx[p].y, e.y)));
+      }
+      const float2 g = make_float2(ex2_approx(ex), ex2_approx(ey));
       m[p] = __fadd2_rn(m[p], g);
       q[p].x = fmaf(-g.x, q[p].x, q[p].x);
       q[p].y = fmaf(-g.y, q[p].y, q[p].y);
@@ -116,105 +154,118 @@ __device__ __forceinline__ void eval_table(const Coef* __restrict__ tab, int n,
   }
 }
 
-// One proposal direction: n samples from the staged molecule (T.x, T.samp)
-// evaluated against itself and, unless kSelf, against T.y. Returns the warp
-// totals of the shifted values, out = {sum (fa-Ka), sum (fa-Ka)^2,
-// sum (fb-Kb), sum (fb-Kb)^2} with shift = {Ka, Kb} the first unit's values
-// (a warp-uniform shift keeps the one-pass variance free of cancellation):
+__device__ __forceinline__ void dir_init(DirState& s) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) { s.hi[t] = 0.f; s.lo[t] = 0.f; }
+  s.K[0] = s.K[1] = 0.f;
+}
+
+// Sample pairs [b * 32 SP, (b + 1) * 32 SP) of one direction (P sample pairs
+// in total, n samples): draw, evaluate and accumulate. Values:
 //   cross: fa = m_Y (first order), fb = (u_X / m_X) u_Y (union)
 //   self:  fa = u_X / m_X (volume), fb = u_X^2 / m_X (self-overlap)
-// With antithetic pairs the unit is the mean of a sample and its reflection.
-template <bool kSelf>
-__device__ void run_direction(const WarpTables& T, int nx, int ny, uint32_t n, Key key, uint64_t stream,
-                              uint32_t tag, bool anti, int lane, double out[4], float shift[2]) {
+// With antithetic pairs the unit is the mean of a sample and its
+// reflection. The first batch sets the shifts from sample 0.
+template <bool kSelf, int SP, int kForm>
+__device__ __forceinline__ void run_batch(WarpTables& T, int nx, int ny, uint32_t b, uint32_t n, Key key,
+                                          uint32_t slo, uint32_t shi, uint32_t tag, bool anti, int lane,
+                                          DirState& st) {
   const uint32_t P = (n + 1u) >> 1;
-  const uint32_t slo = (uint32_t)stream, shi = (uint32_t)(stream >> 32);
-  float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-  for (uint32_t base = 0; base < P; base += 32u * kSP) {
-    float2 rx[kSP], ry[kSP], rz[kSP], rr[kSP], valid[kSP];
+  const uint32_t base = b * 32u * SP;
+  float2 rx[SP], ry[SP], rz[SP], rr[SP];
 #pragma unroll
-    for (int p = 0; p < kSP; ++p) {
-      const uint32_t s = base + (uint32_t)p * 32u + (uint32_t)lane;
-      const bool ok0 = s < P;
-      const bool ok1 = ok0 && (2u * s + 1u < n);
-      const uint4 w0 = philox10(make_uint4(2u * s, slo, shi, tag), key);
-      const uint4 w1 = philox10(make_uint4(2u * s + 1u, slo, shi, tag), key);
-      float n0, n1, n2, n3, n4, n5;
-      box_muller(w0.z, w0.w, n0, n1);
-      box_muller(w1.x, w1.y, n2, n3);
-      box_muller(w1.z, w1.w, n4, n5);
-      const float4 c0 = T.samp[pick(T, nx, w0.x)];
-      const float ax = fmaf(c0.w, n0, c0.x), ay = fmaf(c0.w, n1, c0.y), az = fmaf(c0.w, n4, c0.z);
-      float bx, by, bz;
-      if (anti) {
-        bx = fmaf(-c0.w, n0, c0.x); by = fmaf(-c0.w, n1, c0.y); bz = fmaf(-c0.w, n4, c0.z);
-      } else {
-        const float4 c1 = T.samp[pick(T, nx, w0.y)];
-        bx = fmaf(c1.w, n2, c1.x); by = fmaf(c1.w, n3, c1.y); bz = fmaf(c1.w, n5, c1.z);
-      }
-      rx[p] = make_float2(ax, bx);
-      ry[p] = make_float2(ay, by);
-      rz[p] = make_float2(az, bz);
-      rr[p] = make_float2(fmaf(ax, ax, fmaf(ay, ay, az * az)), fmaf(bx, bx, fmaf(by, by, bz * bz)));
-      valid[p] = make_float2(ok0 ? 1.f : 0.f, ok1 ? 1.f : 0.f);
-    }
-    float2 m[kSP], q[kSP], fa[kSP], fb[kSP];
-#pragma unroll
-    for (int p = 0; p < kSP; ++p) { m[p] = make_float2(0.f, 0.f); q[p] = make_float2(1.f, 1.f); }
-    eval_table(T.x, nx, rx, ry, rz, rr, m, q);
-    if (kSelf) {
-#pragma unroll
-      for (int p = 0; p < kSP; ++p) {
-        const float ux = 1.f - q[p].x, uy = 1.f - q[p].y;
-        const float wx = __fdividef(ux, m[p].x), wy = __fdividef(uy, m[p].y);
-        fa[p] = make_float2(wx, wy);
-        fb[p] = make_float2(wx * ux, wy * uy);
-      }
+  for (int p = 0; p < SP; ++p) {
+    const uint32_t s = base + (uint32_t)p * 32u + (uint32_t)lane;
+    const uint4 w0 = philox10(make_uint4(2u * s, slo, shi, tag), key);
+    const uint4 w1 = philox10(make_uint4(2u * s + 1u, slo, shi, tag), key);
+    float n0, n1, n2, n3, n4, n5;
+    box_muller(w0.z, w0.w, n0, n1);
+    box_muller(w1.x, w1.y, n2, n3);
+    box_muller(w1.z, w1.w, n4, n5);
+    const float4 c0 = T.samp[pick(T, nx, w0.x)];
+    const float ax = fmaf(c0.w, n0, c0.x), ay = fmaf(c0.w, n1, c0.y), az = fmaf(c0.w, n4, c0.z);
+    float bx, by, bz;
+    if (anti) {
+      bx = fmaf(-c0.w, n0, c0.x); by = fmaf(-c0.w, n1, c0.y); bz = fmaf(-c0.w, n4, c0.z);
     } else {
-      float2 w[kSP];
-#pragma unroll
-      for (int p = 0; p < kSP; ++p) {
-        w[p] = make_float2(__fdividef(1.f - q[p].x, m[p].x), __fdividef(1.f - q[p].y, m[p].y));
-        m[p] = make_float2(0.f, 0.f);
-        q[p] = make_float2(1.f, 1.f);
-      }
-      eval_table(T.y, ny, rx, ry, rz, rr, m, q);
-#pragma unroll
-      for (int p = 0; p < kSP; ++p) {
-        fa[p] = m[p];
-        fb[p] = make_float2(w[p].x * (1.f - q[p].x), w[p].y * (1.f - q[p].y));
-      }
+      const float4 c1 = T.samp[pick(T, nx, w0.y)];
+      bx = fmaf(c1.w, n2, c1.x); by = fmaf(c1.w, n3, c1.y); bz = fmaf(c1.w, n5, c1.z);
     }
-    if (base == 0) {
-      // sample 0 (lane 0, pair 0) always exists since n >= 2
-      shift[0] = __shfl_sync(0xffffffffu, anti ? 0.5f * (fa[0].x + fa[0].y) : fa[0].x, 0);
-      shift[1] = __shfl_sync(0xffffffffu, anti ? 0.5f * (fb[0].x + fb[0].y) : fb[0].x, 0);
-    }
-    float b[4] = {0.f, 0.f, 0.f, 0.f};
+    rx[p] = make_float2(ax, bx);
+    ry[p] = make_float2(ay, by);
+    rz[p] = make_float2(az, bz);
+    rr[p] = make_float2(fmaf(ax, ax, fmaf(ay, ay, az * az)), fmaf(bx, bx, fmaf(by, by, bz * bz)));
+  }
+  float2 m[SP], q[SP], fa[SP], fb[SP];
 #pragma unroll
-    for (int p = 0; p < kSP; ++p) {
-      if (anti) {
-        const float ga = 0.5f * (fa[p].x + fa[p].y) - shift[0], gb = 0.5f * (fb[p].x + fb[p].y) - shift[1];
-        const float v = valid[p].x;
-        b[0] = fmaf(v, ga, b[0]);
-        b[1] = fmaf(v * ga, ga, b[1]);
-        b[2] = fmaf(v, gb, b[2]);
-        b[3] = fmaf(v * gb, gb, b[3]);
-      } else {
-        const float2 v = valid[p];
-        const float a0 = fa[p].x - shift[0], a1 = fa[p].y - shift[0];
-        const float b0 = fb[p].x - shift[1], b1 = fb[p].y - shift[1];
-        b[0] += v.x * a0 + v.y * a1;
-        b[1] += v.x * a0 * a0 + v.y * a1 * a1;
-        b[2] += v.x * b0 + v.y * b1;
-        b[3] += v.x * b0 * b0 + v.y * b1 * b1;
-      }
-    }
+  for (int p = 0; p < SP; ++p) { m[p] = make_float2(0.f, 0.f); q[p] = make_float2(1.f, 1.f); }
+  eval_table<SP, kForm>(T.x, nx, rx, ry, rz, rr, m, q);
+  if (kSelf) {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) acc2(hi[t], lo[t], b[t]);
+    for (int p = 0; p < SP; ++p) {
+      const float ux = 1.f - q[p].x, uy = 1.f - q[p].y;
+      const float wx = __fdividef(ux, m[p].x), wy = __fdividef(uy, m[p].y);
+      fa[p] = make_float2(wx, wy);
+      fb[p] = make_float2(wx * ux, wy * uy);
+    }
+  } else {
+    float2 w[SP];
+#pragma unroll
+    for (int p = 0; p < SP; ++p) {
+      w[p] = make_float2(__fdividef(1.f - q[p].x, m[p].x), __fdividef(1.f - q[p].y, m[p].y));
+      m[p] = make_float2(0.f, 0.f);
+      q[p] = make_float2(1.f, 1.f);
+    }
+    eval_table<SP, kForm>(T.y, ny, rx, ry, rz, rr, m, q);
+#pragma unroll
+    for (int p = 0; p < SP; ++p) {
+      fa[p] = m[p];
+      fb[p] = make_float2(w[p].x * (1.f - q[p].x), w[p].y * (1.f - q[p].y));
+    }
+  }
+  if (b == 0) {
+    // sample 0 (lane 0, pair 0) always exists since n >= 2
+    st.K[0] = __shfl_sync(0xffffffffu, anti ? 0.5f * (fa[0].x + fa[0].y) : fa[0].x, 0);
+    st.K[1] = __shfl_sync(0xffffffffu, anti ? 0.5f * (fb[0].x + fb[0].y) : fb[0].x, 0);
+  }
+  const float Ka = st.K[0], Kb = st.K[1];
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int p = 0; p < SP; ++p) {
+    const uint32_t s = base + (uint32_t)p * 32u + (uint32_t)lane;
+    const float v0 = s < P ? 1.f : 0.f;
+    const float v1 = 2u * s + 1u < n ? 1.f : 0.f;  // implies s < P
+    if (anti) {
+      const float ga = 0.5f * (fa[p].x + fa[p].y) - Ka, gb = 0.5f * (fb[p].x + fb[p].y) - Kb;
+      acc[0] = fmaf(v0, ga, acc[0]);
+      acc[1] = fmaf(v0 * ga, ga, acc[1]);
+      acc[2] = fmaf(v0, gb, acc[2]);
+      acc[3] = fmaf(v0 * gb, gb, acc[3]);
+    } else {
+      const float a0 = fa[p].x - Ka, a1 = fa[p].y - Ka;
+      const float b0 = fb[p].x - Kb, b1 = fb[p].y - Kb;
+      acc[0] += v0 * a0 + v1 * a1;
+      acc[1] += v0 * a0 * a0 + v1 * a1 * a1;
+      acc[2] += v0 * b0 + v1 * b1;
+      acc[3] += v0 * b0 * b0 + v1 * b1 * b1;
+    }
   }
 #pragma unroll
-  for (int t = 0; t < 4; ++t) out[t] = warp_sum((double)hi[t] + (double)lo[t]);
+  for (int t = 0; t < 4; ++t) acc2(st.hi[t], st.lo[t], acc[t]);
+}
+
+// Compensated FP32 warp sum of hi + lo; lane 0's (hi, lo) carries the total.
+__device__ __forceinline__ void warp_sum2(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    const float s = hi + h2;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (h2 - bb);
+    hi = s;
+    lo = lo + l2 + e;
+  }
 }
 
 // est = Z mean, se = Z sqrt(s^2 / n) (n-1 sample variance, Eq. var) from
@@ -228,6 +279,18 @@ __device__ __forceinline__ void finish(double Z, double s, double s2, double K, 
   se = Z * sqrt(var / n);
 }
 
+// Warp totals of a direction (valid in lane 0): sums[4] in FP64.
+__device__ __forceinline__ void dir_totals(const DirState& st, double sums[4]) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    float h = st.hi[t], l = st.lo[t];
+    warp_sum2(h, l);
+    sums[t] = (double)h + (double)l;
+  }
+}
+
+enum Mode { kPairs = 0, kScreen = 1, kAdaptive = 2 };
+
 struct CrossArgs {
   SetView A, B;
   // pair mode
@@ -236,7 +299,7 @@ struct CrossArgs {
   const float* pose;
   double* est;
   double* se;
-  // screen mode
+  // screen modes
   const int32_t* order_b;
   int32_t n_q, n_db;
   const double* self_q;
@@ -245,8 +308,14 @@ struct CrossArgs {
   float* seT;
   double* O;
   double* seO;
+  uint32_t* n_used;
+  // adaptive
+  float tau;
+  uint32_t round_b, min_b, cap_b;  // in batches
+  int watch;
   // common
   int64_t n_items;
+  int64_t item_stride;
   Key key;
   uint64_t stream_base;
   uint32_t n;
@@ -254,12 +323,66 @@ struct CrossArgs {
   unsigned long long* queue;
 };
 
-template <bool kScreen>
-__global__ void __launch_bounds__(kThreads, 2) cross_kernel(const CrossArgs args) {
+// Pair epilogue: symmetrised estimates, Tanimoto and SEs; lane 0 only.
+template <int MODE>
+__device__ void pair_epilogue(const CrossArgs& args, int32_t xa, int32_t xb, int64_t out_idx, const double s0[4],
+                              const float k0[2], const double s1[4], const float k1[2], double n_eff) {
+  const double ZA = args.A.Z[xa], ZB = args.B.Z[xb];
+  double e[2], sd[2];
+  for (int slot = 0; slot < 2; ++slot) {
+    double e0, se0;
+    finish(ZA, s0[2 * slot], s0[2 * slot + 1], k0[slot], n_eff, e0, se0);
+    if (args.symmetric) {
+      double e1, se1;
+      finish(ZB, s1[2 * slot], s1[2 * slot + 1], k1[slot], n_eff, e1, se1);
+      e[slot] = 0.5 * (e0 + e1);
+      sd[slot] = 0.5 * sqrt(se0 * se0 + se1 * se1);
+    } else {
+      e[slot] = e0;
+      sd[slot] = se0;
+    }
+  }
+  if (MODE == kPairs) {
+    args.est[2 * out_idx] = e[0]; args.est[2 * out_idx + 1] = e[1];
+    args.se[2 * out_idx] = sd[0]; args.se[2 * out_idx + 1] = sd[1];
+  } else {
+    for (int slot = 0; slot < 2; ++slot) {
+      const double S = args.self_q[2 * (int64_t)xa + slot] + args.self_db[2 * (int64_t)xb + slot];
+      const double den = S - e[slot];
+      args.T[2 * out_idx + slot] = (float)(e[slot] / den);
+      args.seT[2 * out_idx + slot] = (float)(fabs(S / (den * den)) * sd[slot]);
+      if (args.O) args.O[2 * out_idx + slot] = e[slot];
+      if (args.seO) args.seO[2 * out_idx + slot] = sd[slot];
+    }
+  }
+}
+
+// FP32 SE(T) of the watched slot from the running sums (adaptive stop rule).
+__device__ __forceinline__ float watched_se_t(const CrossArgs& args, const DirState& sa, const DirState& sb, int32_t xa,
+                                              int32_t xb, float n) {
+  const int t = 2 * args.watch;
+  float h[4] = {sa.hi[t], sa.hi[t + 1], sb.hi[t], sb.hi[t + 1]};
+  float l[4] = {sa.lo[t], sa.lo[t + 1], sb.lo[t], sb.lo[t + 1]};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) warp_sum2(h[i], l[i]);
+  const float ZA = (float)args.A.Z[xa], ZB = (float)args.B.Z[xb];
+  const float s1a = h[0] + l[0], s2a = h[1] + l[1], s1b = h[2] + l[2], s2b = h[3] + l[3];
+  const float va = fmaxf((s2a - s1a * s1a / n) / (n - 1.f), 0.f);
+  const float vb = fmaxf((s2b - s1b * s1b / n) / (n - 1.f), 0.f);
+  const float ea = ZA * (sa.K[args.watch] + s1a / n), eb = ZB * (sb.K[args.watch] + s1b / n);
+  const float O = 0.5f * (ea + eb);
+  const float seO = 0.5f * sqrtf((ZA * ZA * va + ZB * ZB * vb) / n);
+  const float S = (float)(args.self_q[2 * (int64_t)xa + args.watch] + args.self_db[2 * (int64_t)xb + args.watch]);
+  const float den = S - O;
+  return fabsf(S / (den * den)) * seO;
+}
+
+template <int MODE, int SP, int kForm, int kWarps, int kMinBlocks>
+__global__ void __launch_bounds__(kWarps * 32, kMinBlocks) cross_kernel(const CrossArgs args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WarpTables& T = reinterpret_cast<WarpTables*>(smem_raw)[warp];
-  const double n_eff = args.anti ? (double)(args.n / 2u) : (double)args.n;
+  const uint32_t batch = 32u * SP;  // sample pairs per batch
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(args.queue, 1ull);
@@ -268,79 +391,77 @@ __global__ void __launch_bounds__(kThreads, 2) cross_kernel(const CrossArgs args
     int32_t xa, xb;
     int64_t out_idx;
     const float* pose = nullptr;
-    if (kScreen) {
-      const int64_t rank = (int64_t)item / args.n_q;
-      xa = (int32_t)((int64_t)item - rank * args.n_q);
-      xb = args.order_b[rank];
-      out_idx = (int64_t)xa * args.n_db + xb;
-    } else {
+    if (MODE == kPairs) {
       xa = args.ia[item];
       xb = args.ib[item];
       out_idx = (int64_t)item;
       if (args.pose) pose = args.pose + 7 * (int64_t)item;
+    } else {
+      const int64_t t = (int64_t)item * args.item_stride;
+      const int64_t rank = t / args.n_q;
+      xa = (int32_t)(t - rank * args.n_q);
+      xb = args.order_b[rank];
+      out_idx = (int64_t)xa * args.n_db + xb;
     }
     if (xa < 0 || xa >= args.A.n_mol || xb < 0 || xb >= args.B.n_mol) {
-      if (lane == 0 && !kScreen) {
+      if (lane == 0 && MODE == kPairs) {
         const double nan = __longlong_as_double(0x7ff8000000000000ll);
         args.est[2 * out_idx] = nan; args.est[2 * out_idx + 1] = nan;
         args.se[2 * out_idx] = nan; args.se[2 * out_idx + 1] = nan;
       }
       continue;
     }
-    const uint64_t stream = args.stream_base + (uint64_t)out_idx;
+    const uint32_t slo = (uint32_t)(args.stream_base + (uint64_t)out_idx);
+    const uint32_t shi = (uint32_t)((args.stream_base + (uint64_t)out_idx) >> 32);
     const MolRef MA = mol_ref(args.A, xa), MB = mol_ref(args.B, xb);
-    const Pose PA = make_pose(nullptr), PB = make_pose(pose);
-    double s0[4], s1[4] = {0.0, 0.0, 0.0, 0.0};
-    float k0[2], k1[2] = {0.f, 0.f};
-    {
-      const float3 o = centroid(args.A, MA, PA, lane);
-      __syncwarp();
-      stage_coef(T.x, args.A, MA, PA, o, lane);
-      stage_coef(T.y, args.B, MB, PB, o, lane);
-      stage_samp(T, args.A, MA, PA, o, lane);
-      __syncwarp();
-      run_direction<false>(T, MA.n, MB.n, args.n, args.key, stream, SHP_TAG_AB, args.anti, lane, s0, k0);
+    DirState& sa = T.st[0][lane];
+    DirState& sb = T.st[1][lane];
+    dir_init(sa);
+    dir_init(sb);
+    uint32_t n_dir;
+    if (MODE != kAdaptive) {
+      const uint32_t nb = ((args.n + 1u) / 2u + batch - 1u) / batch;
+      stage_direction(T, args.A, MA, nullptr, &args.B, MB, pose, lane);
+      for (uint32_t b = 0; b < nb; ++b)
+        run_batch<false, SP, kForm>(T, MA.n, MB.n, b, args.n, args.key, slo, shi, SHP_TAG_AB, args.anti, lane, sa);
+      if (args.symmetric) {
+        stage_direction(T, args.B, MB, pose, &args.A, MA, nullptr, lane);
+        for (uint32_t b = 0; b < nb; ++b)
+          run_batch<false, SP, kForm>(T, MB.n, MA.n, b, args.n, args.key, slo, shi, SHP_TAG_BA, args.anti, lane,
+                                      sb);
+      }
+      n_dir = args.n;
+    } else {
+      // rounds of round_b batches per direction until SE(T) <= tau or cap
+      uint32_t b = 0;
+      for (;;) {
+        const uint32_t nxt = b + args.round_b;
+        const uint32_t n_now = nxt * batch * 2u;
+        stage_direction(T, args.A, MA, nullptr, &args.B, MB, nullptr, lane);
+        for (uint32_t k = b; k < nxt; ++k)
+          run_batch<false, SP, kForm>(T, MA.n, MB.n, k, n_now, args.key, slo, shi, SHP_TAG_AB, false, lane, sa);
+        stage_direction(T, args.B, MB, nullptr, &args.A, MA, nullptr, lane);
+        for (uint32_t k = b; k < nxt; ++k)
+          run_batch<false, SP, kForm>(T, MB.n, MA.n, k, n_now, args.key, slo, shi, SHP_TAG_BA, false, lane, sb);
+        b = nxt;
+        if (b >= args.cap_b) break;
+        if (b >= args.min_b) {
+          const float se_t = watched_se_t(args, sa, sb, xa, xb, (float)n_now);
+          const int stop = __shfl_sync(0xffffffffu, (int)(se_t <= args.tau), 0);
+          if (stop) break;
+        }
+      }
+      n_dir = b * batch * 2u;
     }
-    if (args.symmetric) {
-      const float3 o = centroid(args.B, MB, PB, lane);
-      __syncwarp();
-      stage_coef(T.x, args.B, MB, PB, o, lane);
-      stage_coef(T.y, args.A, MA, PA, o, lane);
-      stage_samp(T, args.B, MB, PB, o, lane);
-      __syncwarp();
-      run_direction<false>(T, MB.n, MA.n, args.n, args.key, stream, SHP_TAG_BA, args.anti, lane, s1, k1);
+    double s0[4], s1[4] = {0.0, 0.0, 0.0, 0.0};
+    dir_totals(sa, s0);
+    if (args.symmetric) dir_totals(sb, s1);
+    if (lane == 0) {
+      const double n_eff = args.anti ? (double)(n_dir / 2u) : (double)n_dir;
+      pair_epilogue<MODE>(args, xa, xb, out_idx, s0, sa.K, s1, sb.K, n_eff);
+      if (MODE != kPairs && args.n_used) args.n_used[out_idx] = n_dir;
     }
     __syncwarp();
-    if (lane == 0) {
-      const double ZA = args.A.Z[xa], ZB = args.B.Z[xb];
-      double e[2], sd[2];
-      for (int slot = 0; slot < 2; ++slot) {
-        double e0, se0;
-        finish(ZA, s0[2 * slot], s0[2 * slot + 1], k0[slot], n_eff, e0, se0);
-        if (args.symmetric) {
-          double e1, se1;
-          finish(ZB, s1[2 * slot], s1[2 * slot + 1], k1[slot], n_eff, e1, se1);
-          e[slot] = 0.5 * (e0 + e1);
-          sd[slot] = 0.5 * sqrt(se0 * se0 + se1 * se1);
-        } else {
-          e[slot] = e0;
-          sd[slot] = se0;
-        }
-      }
-      if (kScreen) {
-        for (int slot = 0; slot < 2; ++slot) {
-          const double S = args.self_q[2 * (int64_t)xa + slot] + args.self_db[2 * (int64_t)xb + slot];
-          const double den = S - e[slot];
-          args.T[2 * out_idx + slot] = (float)(e[slot] / den);
-          args.seT[2 * out_idx + slot] = (float)(fabs(S / (den * den)) * sd[slot]);
-          if (args.O) args.O[2 * out_idx + slot] = e[slot];
-          if (args.seO) args.seO[2 * out_idx + slot] = sd[slot];
-        }
-      } else {
-        args.est[2 * out_idx] = e[0]; args.est[2 * out_idx + 1] = e[1];
-        args.se[2 * out_idx] = sd[0]; args.se[2 * out_idx + 1] = sd[1];
-      }
-    }
   }
 }
 
@@ -359,11 +480,12 @@ struct SelfArgs {
   unsigned long long* queue;
 };
 
-__global__ void __launch_bounds__(kThreads, 2) self_kernel(const SelfArgs args) {
+template <int SP, int kForm, int kWarps, int kMinBlocks>
+__global__ void __launch_bounds__(kWarps * 32, kMinBlocks) self_kernel(const SelfArgs args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WarpTables& T = reinterpret_cast<WarpTables*>(smem_raw)[warp];
-  const double n_eff = args.anti ? (double)(args.n / 2u) : (double)args.n;
+  const uint32_t batch = 32u * SP;
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(args.queue, 1ull);
@@ -381,45 +503,150 @@ __global__ void __launch_bounds__(kThreads, 2) self_kernel(const SelfArgs args) 
       continue;
     }
     const MolRef M = mol_ref(args.S, xm);
-    const Pose P = make_pose(nullptr);
-    const float3 o = centroid(args.S, M, P, lane);
-    __syncwarp();
-    stage_coef(T.x, args.S, M, P, o, lane);
-    stage_samp(T, args.S, M, P, o, lane);
-    __syncwarp();
+    const uint64_t stream = args.stream_base + item;
+    stage_direction(T, args.S, M, nullptr, nullptr, M, nullptr, lane);
+    DirState& st = T.st[0][lane];
+    dir_init(st);
+    const uint32_t nb = ((args.n + 1u) / 2u + batch - 1u) / batch;
+    for (uint32_t b = 0; b < nb; ++b)
+      run_batch<true, SP, kForm>(T, M.n, 0, b, args.n, args.key, (uint32_t)stream, (uint32_t)(stream >> 32),
+                                 SHP_TAG_SELF, args.anti, lane, st);
     double s[4];
-    float k[2];
-    run_direction<true>(T, M.n, 0, args.n, args.key, args.stream_base + item, SHP_TAG_SELF, args.anti, lane, s,
-                        k);
-    __syncwarp();
+    dir_totals(st, s);
     if (lane == 0) {
+      const double n_eff = args.anti ? (double)(args.n / 2u) : (double)args.n;
       const double Z = args.S.Z[xm];
       double e, sd;
-      finish(Z, s[0], s[1], k[0], n_eff, e, sd);
+      finish(Z, s[0], s[1], st.K[0], n_eff, e, sd);
       args.vol[item] = e;
       if (args.vol_se) args.vol_se[item] = sd;
-      finish(Z, s[2], s[3], k[1], n_eff, e, sd);
+      finish(Z, s[2], s[3], st.K[1], n_eff, e, sd);
       if (args.self_ov) args.self_ov[item] = e;
       if (args.self_se) args.self_se[item] = sd;
     }
+    __syncwarp();
   }
 }
 
-template <class Kernel>
-int persistent_grid(Kernel k, int64_t n_items, int* grid) {
-  static int sms = 0;
+// ------------------------------------------------------------ variants
+
+// sample pairs per lane, exponent form, warps per CTA, CTAs per SM (the
+// register budget follows: 3 x 8 warps -> 80, 5 x 4 -> 102, 2 x 8 -> 128)
+struct Variant {
+  int sp, form, warps, min_blocks;
+};
+constexpr Variant kVariants[] = {{4, 0, 8, 3}, {4, 1, 8, 3}, {4, 0, 8, 2}, {4, 1, 8, 2},
+                                 {4, 0, 4, 5}, {8, 0, 4, 4}, {8, 1, 4, 4}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+template <int V>
+struct VariantTraits {
+  static constexpr int sp = kVariants[V].sp, form = kVariants[V].form, warps = kVariants[V].warps;
+  static constexpr int min_blocks = kVariants[V].min_blocks;
+  static constexpr size_t smem = sizeof(WarpTables) * warps;
+};
+
+int sm_count(int* sms) {
   int dev = 0;
   SHP_CUDA(cudaGetDevice(&dev));
-  SHP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  SHP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+  SHP_CUDA(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev));
+  return SHP_OK;
+}
+
+template <class Kernel, class Args>
+int launch_persistent(Kernel k, Args args, int64_t n_items, int warps, size_t smem, cudaStream_t st,
+                      unsigned long long* queue_in = nullptr) {
+  int sms = 0;
+  int rc = sm_count(&sms);
+  if (rc) return rc;
+  SHP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  SHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, kSmemBytes));
+  SHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, warps * 32, smem));
   if (per_sm < 1) per_sm = 1;
-  const int64_t need = (n_items + kWarps - 1) / kWarps;
+  const int64_t need = (n_items + warps - 1) / warps;
   int64_t g = (int64_t)sms * per_sm;
   if (need < g) g = need;
-  *grid = (int)(g < 1 ? 1 : g);
+  const int grid = (int)(g < 1 ? 1 : g);
+  unsigned long long* q = queue_in;
+  if (!q) SHP_CUDA(cudaMallocAsync((void**)&q, sizeof(unsigned long long), st));
+  cudaError_t e = cudaMemsetAsync(q, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) {
+    args.queue = q;
+    k<<<grid, warps * 32, smem, st>>>(args);
+    e = cudaGetLastError();
+  }
+  cudaError_t e2 = queue_in ? cudaSuccess : cudaFreeAsync(q, st);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
   return SHP_OK;
+}
+
+template <int MODE, int V>
+int launch_cross_v(const CrossArgs& a, int64_t n_items, cudaStream_t st) {
+  using Tr = VariantTraits<V>;
+  return launch_persistent(cross_kernel<MODE, Tr::sp, Tr::form, Tr::warps, Tr::min_blocks>, a, n_items, Tr::warps,
+                           Tr::smem, st);
+}
+
+template <int MODE>
+int launch_cross(int v, const CrossArgs& a, int64_t n_items, cudaStream_t st) {
+  switch (v) {
+    case 0: return launch_cross_v<MODE, 0>(a, n_items, st);
+    case 1: return launch_cross_v<MODE, 1>(a, n_items, st);
+    case 2: return launch_cross_v<MODE, 2>(a, n_items, st);
+    case 3: return launch_cross_v<MODE, 3>(a, n_items, st);
+    case 4: return launch_cross_v<MODE, 4>(a, n_items, st);
+    case 5: return launch_cross_v<MODE, 5>(a, n_items, st);
+    default: return launch_cross_v<MODE, 6>(a, n_items, st);
+  }
+}
+
+// The adaptive mode needs rounds of whole batches: SP 4 only.
+template <>
+int launch_cross<kAdaptive>(int v, const CrossArgs& a, int64_t n_items, cudaStream_t st) {
+  switch (v) {
+    case 0: return launch_cross_v<kAdaptive, 0>(a, n_items, st);
+    case 1: return launch_cross_v<kAdaptive, 1>(a, n_items, st);
+    case 2: return launch_cross_v<kAdaptive, 2>(a, n_items, st);
+    case 3: return launch_cross_v<kAdaptive, 3>(a, n_items, st);
+    default: return launch_cross_v<kAdaptive, 4>(a, n_items, st);
+  }
+}
+
+int launch_self(const SelfArgs& a, int64_t n_items, cudaStream_t st) {
+  using Tr = VariantTraits<0>;
+  return launch_persistent(self_kernel<Tr::sp, Tr::form, Tr::warps, Tr::min_blocks>, a, n_items, Tr::warps,
+                           Tr::smem, st);
+}
+
+// Tuned defaults per (device, mode); -1 = not tuned.
+std::mutex g_tune_mu;
+int g_tuned[64][3];
+bool g_tuned_init = false;
+
+int default_variant(int mode) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (!g_tuned_init) {
+    for (auto& row : g_tuned) row[0] = row[1] = row[2] = -1;
+    g_tuned_init = true;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int v = (dev >= 0 && dev < 64) ? g_tuned[dev][mode] : -1;
+  return v >= 0 ? v : 0;
+}
+
+void set_default_variant(int mode, int v) {
+  default_variant(mode);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64) g_tuned[dev][mode] = v;
+}
+
+bool variant_valid(int mode, int v) {
+  if (v < 0 || v >= kNumVariants) return false;
+  return mode != kAdaptive || kVariants[v].sp == 4;
 }
 
 int check_mc(const shp_mc* mc, const char* who) {
@@ -433,24 +660,63 @@ int check_mc(const shp_mc* mc, const char* who) {
   return SHP_OK;
 }
 
-// Launch a persistent kernel with a stream-ordered queue counter.
-template <class Kernel, class Args>
-int launch_queued(Kernel k, Args args, int64_t n_items, cudaStream_t st) {
-  int grid = 0;
-  int rc = persistent_grid(k, n_items, &grid);
-  if (rc) return rc;
-  unsigned long long* q = nullptr;
-  SHP_CUDA(cudaMallocAsync((void**)&q, sizeof(unsigned long long), st));
-  cudaError_t e = cudaMemsetAsync(q, 0, sizeof(unsigned long long), st);
-  if (e == cudaSuccess) {
-    args.queue = q;
-    k<<<grid, kThreads, kSmemBytes, st>>>(args);
-    e = cudaGetLastError();
+// Validates a screen config and fills the mode-specific arguments.
+int screen_args(shp_set Q, shp_set D, const shp_screen* cfg, const double* self_q, const double* self_db, float* T,
+                float* seT, double* O, double* seO, uint32_t* n_used, CrossArgs& a, int& mode, const char* who) {
+  if (!Q || !D || !cfg) { set_error("%s: NULL set or config", who); return SHP_EINVAL; }
+  if (cfg->flags & ~SHP_ANTITHETIC) { set_error("%s: unknown flags", who); return SHP_EINVAL; }
+  a = CrossArgs{};
+  if (cfg->n_fixed > 0) {
+    mode = kScreen;
+    if (cfg->n_fixed < 2) { set_error("%s: n_fixed must be >= 2", who); return SHP_EINVAL; }
+    if ((cfg->flags & SHP_ANTITHETIC) && (cfg->n_fixed & 1u)) {
+      set_error("%s: antithetic sampling needs an even n_fixed", who);
+      return SHP_EINVAL;
+    }
+    a.n = cfg->n_fixed;
+  } else {
+    mode = kAdaptive;
+    if (cfg->flags & SHP_ANTITHETIC) { set_error("%s: adaptive screens do not take SHP_ANTITHETIC", who); return SHP_EINVAL; }
+    const uint32_t bs = 256;  // samples per direction per batch of the SP 4 variants
+    if (cfg->round == 0 || cfg->round % bs || cfg->min_n < cfg->round || cfg->min_n % cfg->round ||
+        cfg->cap < cfg->min_n || cfg->cap % cfg->round) {
+      set_error("%s: adaptive round/min_n/cap must be multiples of 256 with round <= min_n <= cap", who);
+      return SHP_EINVAL;
+    }
+    if (!(cfg->tau > 0.f) || cfg->watch > 1) { set_error("%s: tau must be > 0 and watch 0 or 1", who); return SHP_EINVAL; }
+    a.round_b = cfg->round / bs;
+    a.min_b = cfg->min_n / bs;
+    a.cap_b = cfg->cap / bs;
+    a.tau = cfg->tau;
+    a.watch = (int)cfg->watch;
   }
-  cudaError_t e2 = cudaFreeAsync(q, st);
-  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+  if (Q->n_mol > 0 && D->n_mol > 0 && (!self_q || !self_db || !T || !seT)) {
+    set_error("%s: NULL array", who);
+    return SHP_EINVAL;
+  }
+  a.A = view(Q);
+  a.B = view(D);
+  a.order_b = D->order;
+  a.n_q = Q->n_mol;
+  a.n_db = D->n_mol;
+  a.self_q = self_q;
+  a.self_db = self_db;
+  a.T = T;
+  a.seT = seT;
+  a.O = O;
+  a.seO = seO;
+  a.n_used = n_used;
+  a.n_items = (int64_t)Q->n_mol * D->n_mol;
+  a.item_stride = 1;
+  a.key = Key{(uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32)};
+  a.stream_base = cfg->stream_base;
+  a.anti = (cfg->flags & SHP_ANTITHETIC) != 0;
+  a.symmetric = true;
   return SHP_OK;
+}
+
+int launch_screen(int mode, int v, const CrossArgs& a, int64_t n_items, cudaStream_t st) {
+  return mode == kScreen ? launch_cross<kScreen>(v, a, n_items, st) : launch_cross<kAdaptive>(v, a, n_items, st);
 }
 
 }  // namespace
@@ -476,12 +742,13 @@ extern "C" int overlap_estimate(shp_set A, const int32_t* ia, shp_set B, const i
   a.est = est;
   a.se = se;
   a.n_items = n_pairs;
+  a.item_stride = 1;
   a.key = Key{(uint32_t)mc->seed, (uint32_t)(mc->seed >> 32)};
   a.stream_base = mc->stream_base;
   a.n = mc->n_samples;
   a.anti = (mc->flags & SHP_ANTITHETIC) != 0;
   a.symmetric = (mc->flags & SHP_SYMMETRIC) != 0;
-  return launch_queued(cross_kernel<false>, a, n_pairs, (cudaStream_t)stream);
+  return launch_cross<kPairs>(default_variant(kPairs), a, n_pairs, (cudaStream_t)stream);
 }
 
 extern "C" int union_volume_estimate(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, double* vol,
@@ -507,40 +774,64 @@ extern "C" int union_volume_estimate(shp_set S, const int32_t* idx, int64_t n, c
   a.vol_se = vol_se;
   a.self_ov = self_ov;
   a.self_se = self_se;
-  return launch_queued(self_kernel, a, n, (cudaStream_t)stream);
+  return launch_self(a, n, (cudaStream_t)stream);
 }
 
 extern "C" int tanimoto_screen(shp_set Q, shp_set D, const shp_screen* cfg, const double* self_q,
                                const double* self_db, float* T, float* seT, double* O_out, double* seO_out,
-                               void* stream) {
+                               uint32_t* n_used, void* stream) {
   clear_error();
-  if (!Q || !D || !cfg) { set_error("tanimoto_screen: NULL set or config"); return SHP_EINVAL; }
-  if (cfg->n_fixed < 2) { set_error("tanimoto_screen: n_fixed must be >= 2"); return SHP_EINVAL; }
-  if ((cfg->flags & SHP_ANTITHETIC) && (cfg->n_fixed & 1u)) {
-    set_error("tanimoto_screen: antithetic sampling needs an even n_fixed");
-    return SHP_EINVAL;
+  CrossArgs a;
+  int mode = 0;
+  int rc = screen_args(Q, D, cfg, self_q, self_db, T, seT, O_out, seO_out, n_used, a, mode, "tanimoto_screen");
+  if (rc) return rc;
+  if (a.n_items == 0) return SHP_OK;
+  int v = cfg->variant;
+  if (v < 0) v = default_variant(mode);
+  if (!variant_valid(mode, v)) { set_error("tanimoto_screen: variant %d not valid for this mode", v); return SHP_EINVAL; }
+  return launch_screen(mode, v, a, a.n_items, (cudaStream_t)stream);
+}
+
+extern "C" int shp_screen_variants(void) { return kNumVariants; }
+
+extern "C" int tanimoto_screen_tune(shp_set Q, shp_set D, const shp_screen* cfg, const double* self_q,
+                                    const double* self_db, float* T, float* seT, uint32_t* n_used, int64_t n_sample,
+                                    float* timings_ms, int32_t* best, void* stream) {
+  clear_error();
+  CrossArgs a;
+  int mode = 0;
+  int rc = screen_args(Q, D, cfg, self_q, self_db, T, seT, nullptr, nullptr, n_used, a, mode, "tanimoto_screen_tune");
+  if (rc) return rc;
+  if (a.n_items == 0 || n_sample <= 0) { set_error("tanimoto_screen_tune: nothing to time"); return SHP_EINVAL; }
+  if (n_sample > a.n_items) n_sample = a.n_items;
+  a.item_stride = a.n_items / n_sample;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  SHP_CUDA(cudaEventCreate(&e0));
+  SHP_CUDA(cudaEventCreate(&e1));
+  int best_v = -1;
+  float best_ms = 0.f;
+  for (int v = 0; v < kNumVariants; ++v) {
+    if (timings_ms) timings_ms[v] = -1.f;
+    if (!variant_valid(mode, v)) continue;
+    rc = launch_screen(mode, v, a, n_sample, st);  // warm-up (first launch pays set-up)
+    if (!rc) {
+      cudaEventRecord(e0, st);
+      rc = launch_screen(mode, v, a, n_sample, st);
+      cudaEventRecord(e1, st);
+    }
+    if (rc) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "tanimoto_screen_tune: cudaEventSynchronize"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (timings_ms) timings_ms[v] = ms;
+    if (best_v < 0 || ms < best_ms) { best_v = v; best_ms = ms; }
   }
-  if (cfg->flags & ~SHP_ANTITHETIC) { set_error("tanimoto_screen: unknown flags"); return SHP_EINVAL; }
-  const int64_t n_items = (int64_t)Q->n_mol * D->n_mol;
-  if (n_items == 0) return SHP_OK;
-  if (!self_q || !self_db || !T || !seT) { set_error("tanimoto_screen: NULL array"); return SHP_EINVAL; }
-  CrossArgs a{};
-  a.A = view(Q);
-  a.B = view(D);
-  a.order_b = D->order;
-  a.n_q = Q->n_mol;
-  a.n_db = D->n_mol;
-  a.self_q = self_q;
-  a.self_db = self_db;
-  a.T = T;
-  a.seT = seT;
-  a.O = O_out;
-  a.seO = seO_out;
-  a.n_items = n_items;
-  a.key = Key{(uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32)};
-  a.stream_base = cfg->stream_base;
-  a.n = cfg->n_fixed;
-  a.anti = (cfg->flags & SHP_ANTITHETIC) != 0;
-  a.symmetric = true;
-  return launch_queued(cross_kernel<true>, a, n_items, (cudaStream_t)stream);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  set_default_variant(mode, best_v);
+  if (best) *best = best_v;
+  return SHP_OK;
 }

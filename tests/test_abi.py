@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version_and_error_string(lib):
-    assert lib.shp_version() == 1
+    assert lib.shp_version() == 2
     assert isinstance(lib.shp_last_error(), bytes)
 
 
@@ -45,7 +45,8 @@ def test_null_and_bad_arguments_rejected(lib):
     assert b"NULL set" in lib.shp_last_error()
     assert lib.union_volume_estimate(None, None, 1, ctypes.byref(mc), None, None, None, None, None) == -1
     assert lib.fo_overlap(None, None, None, None, 1, None, None, None) == -1
-    assert lib.tanimoto_screen(None, None, None, None, None, None, None, None, None, None) == -1
+    assert lib.tanimoto_screen(None, None, None, None, None, None, None, None, None, None, None) == -1
+    assert lib.shp_screen_variants() >= 1
     out = ctypes.c_void_p()
     off = (ctypes.c_int32 * 2)(0, 1)
     assert lib.shape_set_load(None, None, None, 0.0, None, 1, None, ctypes.byref(out)) == -1

@@ -1,0 +1,158 @@
+"""Adaptive confidence-bounded screen (Sec. confidence-bounded screening) and
+the screen's launch variants, against the FP64 oracle.
+
+The stop decision is an integer (samples used) decided by floating point:
+the kernel takes it in FP32 from its running sums. The oracle reproduces
+the estimates at the kernel's n_used exactly (same streams: the first n_used
+samples of each direction) and checks that the decision is valid -- SE(T)
+at n_used is within tolerance of tau or the cap was hit, and SE(T) one round
+earlier was above tau or n_used is the minimum.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2607_20766_b300 as shp
+from paper_2607_20766_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+
+
+def assert_close(gpu, ref, rtol=RTOL, what=""):
+    gpu = np.asarray(gpu, np.float64)
+    e = np.abs(gpu - ref) / np.maximum(np.abs(ref), 1e-300)
+    assert np.all(np.isfinite(gpu)), what
+    assert e.max() <= rtol, f"{what}: max rel err {e.max():.3e}"
+
+
+def oracle_self(ms, seed, n, stream_base=0):
+    k = np.arange(ms.n_mol)
+    fo = O.fo_overlap(ms, k, ms, k)
+    so = O.union_volume_estimate(ms, k, seed=seed, n=n, stream_base=stream_base)[2]
+    return np.stack([fo, so], 1)
+
+
+@pytest.fixture(scope="module")
+def small_screen():
+    q = synth.principal_axes(synth.generate(21, [20, 36, 48]))
+    d = synth.principal_axes(synth.generate(22, synth.counts_heavy(22, 50)))
+    return q, d, shp.shape_set_load(q), shp.shape_set_load(d), oracle_self(q, 1, 8192), oracle_self(d, 2, 8192)
+
+
+def check_adaptive_against_oracle(q, d, res, sq, sd, seed, tau, rnd, min_n, cap, pairs, n_db, stream_base=0):
+    nu = res["n_used"].cpu().numpy().astype(np.int64)[pairs]
+    iq, idd = pairs // n_db, pairs % n_db
+    assert np.all(nu % rnd == 0) and np.all(nu >= min_n) and np.all(nu <= cap)
+    T = res["T"].cpu().numpy()[pairs]
+    seT = res["seT"].cpu().numpy()[pairs]
+    O_ = res["O"].cpu().numpy()[pairs]
+    seO = res["seO"].cpu().numpy()[pairs]
+    for n in np.unique(nu):
+        sel = nu == n
+        ref = O.tanimoto_pairs(q, iq[sel], d, idd[sel], (stream_base + pairs[sel]).astype(np.uint64), sq, sd,
+                               seed=seed, n=int(n))
+        assert_close(O_[sel], ref["O"], what=f"O at n={n}")
+        assert_close(seO[sel], ref["seO"], what=f"seO at n={n}")
+        assert_close(T[sel], ref["T"], what=f"T at n={n}")
+        assert_close(seT[sel], ref["seT"], what=f"seT at n={n}")
+        # stop rule validity (union slot watched)
+        if n < cap:
+            assert np.all(ref["seT"][:, 1] <= tau * (1 + 1e-4)), "stopped before SE(T) <= tau"
+        if n > min_n:
+            prev = O.tanimoto_pairs(q, iq[sel], d, idd[sel], (stream_base + pairs[sel]).astype(np.uint64), sq, sd,
+                                    seed=seed, n=int(n - rnd))
+            assert np.all(prev["seT"][:, 1] > tau * (1 - 1e-4)), "did not stop when SE(T) <= tau"
+    return nu
+
+
+def test_adaptive_parity_and_stop_rule(small_screen):
+    q, d, Sq, Sd, sq, sd = small_screen
+    tau, rnd, min_n, cap = 0.012, 256, 512, 6144
+    res = shp.tanimoto_screen(Sq, Sd, torch.tensor(sq), torch.tensor(sd), seed=5, tau=tau, round=rnd, min_n=min_n,
+                              cap=cap, with_overlaps=True, stream_base=3)
+    pairs = np.arange(q.n_mol * d.n_mol)
+    nu = check_adaptive_against_oracle(q, d, res, sq, sd, 5, tau, rnd, min_n, cap, pairs, d.n_mol, stream_base=3)
+    # the rule must actually adapt on this set: several distinct budgets
+    assert len(np.unique(nu)) >= 3
+
+
+def test_adaptive_first_order_watch(small_screen):
+    q, d, Sq, Sd, sq, sd = small_screen
+    res = shp.tanimoto_screen(Sq, Sd, torch.tensor(sq), torch.tensor(sd), seed=9, tau=0.02, round=512, min_n=512,
+                              cap=4096, watch=0, with_overlaps=True)
+    nu = res["n_used"].cpu().numpy().astype(np.int64)
+    pairs = np.arange(len(nu))
+    for n in np.unique(nu):
+        sel = pairs[nu == n]
+        ref = O.tanimoto_pairs(q, sel // d.n_mol, d, sel % d.n_mol, sel.astype(np.uint64), sq, sd, seed=9, n=int(n))
+        assert_close(res["T"].cpu().numpy()[sel], ref["T"], what="T")
+        if n < 4096:
+            assert np.all(ref["seT"][:, 0] <= 0.02 * (1 + 1e-4))
+
+
+def test_adaptive_rejects_bad_config(small_screen):
+    q, d, Sq, Sd, sq, sd = small_screen
+    with pytest.raises(shp.ShapeError):
+        shp.tanimoto_screen(Sq, Sd, torch.tensor(sq), torch.tensor(sd), seed=1, round=100)
+    with pytest.raises(shp.ShapeError):
+        shp.tanimoto_screen(Sq, Sd, torch.tensor(sq), torch.tensor(sd), seed=1, min_n=512, cap=256)
+    with pytest.raises(shp.ShapeError):
+        shp.tanimoto_screen(Sq, Sd, torch.tensor(sq), torch.tensor(sd), seed=1, tau=0.0)
+
+
+def test_variants_agree(small_screen):
+    """Every launch variant draws the same samples; only the summation order
+    differs between sample-per-lane widths."""
+    q, d, Sq, Sd, sq, sd = small_screen
+    tq, td = torch.tensor(sq), torch.tensor(sd)
+    nv = shp.screen_variants()
+    ref = shp.tanimoto_screen(Sq, Sd, tq, td, seed=4, n_fixed=1000, variant=0, with_overlaps=True)
+    for v in range(1, nv):
+        r = shp.tanimoto_screen(Sq, Sd, tq, td, seed=4, n_fixed=1000, variant=v, with_overlaps=True)
+        assert_close(r["O"].cpu().numpy(), ref["O"].cpu().numpy(), rtol=2e-6, what=f"variant {v}")
+    ada = [shp.tanimoto_screen(Sq, Sd, tq, td, seed=4, tau=0.015, min_n=512, cap=4096, variant=v, with_overlaps=True)
+           for v in range(5)]
+    for v in range(1, 5):
+        np.testing.assert_array_equal(ada[v]["n_used"].cpu().numpy(), ada[0]["n_used"].cpu().numpy())
+        assert_close(ada[v]["O"].cpu().numpy(), ada[0]["O"].cpu().numpy(), rtol=2e-6, what=f"adaptive variant {v}")
+    with pytest.raises(shp.ShapeError):
+        shp.tanimoto_screen(Sq, Sd, tq, td, seed=4, tau=0.015, variant=6)  # SP 8 cannot run rounds of 256
+
+
+def test_tuner_picks_a_valid_variant(small_screen):
+    q, d, Sq, Sd, sq, sd = small_screen
+    best, times = shp.tanimoto_screen_tune(Sq, Sd, torch.tensor(sq), torch.tensor(sd), seed=1, n_fixed=2048,
+                                           n_sample=64)
+    assert 0 <= best < shp.screen_variants()
+    assert times[best] > 0 and np.all(times[times > 0] >= times[best])
+    best_a, times_a = shp.tanimoto_screen_tune(Sq, Sd, torch.tensor(sq), torch.tensor(sd), seed=1, n_sample=64)
+    assert 0 <= best_a < 5 and np.all(times_a[5:] == -1)
+
+
+def test_adaptive_full_size_sampled():
+    """16 queries (20-48 atoms) x 1,000,000 molecules (18-60, heavy-tailed
+    toward 40), rounds of 256, SE(T) <= 0.005 or 65,536 per direction: the
+    launch the benchmark times; 24 sampled pairs checked by the oracle."""
+    q, d = synth.adaptive_screen()
+    Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
+    selfq = shp.self_overlaps(Sq, seed=11, n_samples=4096, stream_base=0)
+    selfd = shp.self_overlaps(Sd, seed=11, n_samples=4096, stream_base=16)
+    res = shp.tanimoto_screen(Sq, Sd, selfq, selfd, seed=77, tau=0.005, round=256, min_n=1024, cap=65536,
+                              with_overlaps=True)
+    torch.cuda.synchronize()
+    nu = res["n_used"].cpu().numpy()
+    assert np.all(nu % 256 == 0) and nu.min() >= 1024 and nu.max() <= 65536
+    rng = np.random.default_rng(3)
+    pairs = np.sort(rng.choice(len(nu), 24, replace=False))
+    # the oracle's self-overlaps for the sampled molecules (same streams as the library call)
+    sq = np.zeros((q.n_mol, 2))
+    sd = np.zeros((d.n_mol, 2))
+    qs, ds = np.unique(pairs // d.n_mol), np.unique(pairs % d.n_mol)
+    sq[qs, 0] = O.fo_overlap(q, qs, q, qs)
+    sq[qs, 1] = [O.union_volume_estimate(q, [k], seed=11, n=4096, stream_base=int(k))[2][0] for k in qs]
+    sd[ds, 0] = O.fo_overlap(d, ds, d, ds)
+    sd[ds, 1] = [O.union_volume_estimate(d, [k], seed=11, n=4096, stream_base=16 + int(k))[2][0] for k in ds]
+    check_adaptive_against_oracle(q, d, res, sq, sd, 77, 0.005, 256, 1024, 65536, pairs, d.n_mol)
