@@ -69,6 +69,11 @@ _SIGS = {
                  ctypes.c_int],
     "orc_tanimoto_pairs": [_P, _P, _P, _P, _P, ctypes.c_int64, _P, _P, ctypes.c_uint64,
                            ctypes.c_uint32, ctypes.c_uint32, _P, _P, _P, _P, ctypes.c_int],
+    "orc_crn_points": [_P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P],
+    "orc_pose_objective": [ctypes.c_double, _P, ctypes.c_uint32, _P, ctypes.c_int32, _P, ctypes.c_int, _P],
+    "orc_pose_grad_fd": [ctypes.c_double, _P, ctypes.c_uint32, _P, ctypes.c_int32, _P, ctypes.c_int,
+                         ctypes.c_double, _P, _P],
+    "orc_fo_pose_grad": [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _P],
 }
 
 
@@ -281,3 +286,50 @@ def tanimoto_pairs(Q, iq, D, idd, stream_ids, selfQ, selfD, seed, n, flags=0, n_
                                     sO.ctypes.data, T.ctypes.data, sT.ctypes.data, n_threads),
            "tanimoto_pairs")
     return dict(O=O, seO=sO, T=T, seT=sT)
+
+
+# ---------------------------------------------------------------- alignment
+
+TAG_CRN = 3
+OBJ_FO, OBJ_UNION = 0, 1
+
+
+def crn_points(Q, iq, seed, stream, n, c_alpha=2.41798793):
+    """[n, 4] float64: CRN points drawn from Q[iq] (tag 3) and their union weights u/m."""
+    s = _oset(Q, c_alpha)
+    pts = np.empty((n, 4))
+    _check(lib().orc_crn_points(s.ref, iq, seed, stream, n, pts.ctypes.data), "crn_points")
+    return pts
+
+
+def pose_objective(ZQ, points, B, ib, pose, objective=OBJ_UNION, c_alpha=2.41798793):
+    sb = _oset(B, c_alpha)
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    p = np.ascontiguousarray(pose, dtype=np.float32)
+    F = ctypes.c_double()
+    _check(lib().orc_pose_objective(ZQ, pts.ctypes.data, len(pts), sb.ref, ib, p.ctypes.data, objective,
+                                    ctypes.addressof(F)), "pose_objective")
+    return F.value
+
+
+def pose_grad_fd(ZQ, points, B, ib, pose, objective=OBJ_UNION, h=1e-3, c_alpha=2.41798793):
+    """(F, dF/dpose[7]) with central differences of step h in the raw pose."""
+    sb = _oset(B, c_alpha)
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    p = np.ascontiguousarray(pose, dtype=np.float64)
+    F = ctypes.c_double()
+    g = np.empty(7)
+    _check(lib().orc_pose_grad_fd(ZQ, pts.ctypes.data, len(pts), sb.ref, ib, p.ctypes.data, objective, h,
+                                  ctypes.addressof(F), g.ctypes.data), "pose_grad_fd")
+    return F.value, g
+
+
+def fo_pose_grad(A, ia, B, ib, pose, c_alpha=2.41798793):
+    """(O_fo, dO_fo/dpose[7]): closed form (Eq. fo) and its analytic gradient."""
+    sa, sb = _oset(A, c_alpha), _oset(B, c_alpha)
+    p = np.ascontiguousarray(pose, dtype=np.float64)
+    F = ctypes.c_double()
+    g = np.empty(7)
+    _check(lib().orc_fo_pose_grad(sa.ref, ia, sb.ref, ib, p.ctypes.data, ctypes.addressof(F), g.ctypes.data),
+           "fo_pose_grad")
+    return F.value, g

@@ -729,3 +729,152 @@ int orc_tanimoto_pairs(const orc_set* Q, const int32_t* iq, const orc_set* D, co
   }
   return err ? ORC_EINVAL : ORC_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Rigid alignment (Sec. differentiable alignment, Eq. pose, Eq. grad) */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Common random numbers: n points drawn once from the query's mixture
+ * (tag 3, the usual sample layout) with their union weights w = u/m.
+ * points[n][4] = (x, y, z, w).
+ */
+int orc_crn_points(const orc_set* S, int32_t idx, uint64_t seed, uint64_t stream, uint32_t n, double* points) {
+  orc_mol m;
+  int rc = load_mol(S, idx, NULL, &m);
+  if (rc) return rc;
+  for (uint32_t k = 0; k < n; k += 2) {
+    double r[2][3];
+    int i0, i1;
+    draw_pair(&m, seed, stream, 3u, k / 2, 0, r[0], r[1], &i0, &i1);
+    for (int j = 0; j < 2 && k + j < n; ++j) {
+      double ms, u;
+      occupancy(&m, r[j], &ms, &u);
+      double* p = points + 4 * (size_t)(k + j);
+      p[0] = r[j][0]; p[1] = r[j][1]; p[2] = r[j][2]; p[3] = u / ms;
+    }
+  }
+  return ORC_OK;
+}
+
+/*
+ * CRN objective of molecule B[ib] moved by pose (raw quaternion w,x,y,z,
+ * normalised inside, then translation): objective 0 = first order,
+ * F = (Z_Q / n) sum_k m_B(r_k); objective 1 = union (Eq. grad),
+ * F = (Z_Q / n) sum_k w_k u_B(r_k).
+ */
+static double crn_objective(const orc_mol* mb, const double* points, uint32_t n, double ZQ, int objective) {
+  double s = 0.0;
+  for (uint32_t k = 0; k < n; ++k) {
+    const double* p = points + 4 * (size_t)k;
+    double m, u;
+    occupancy(mb, p, &m, &u);
+    s += objective == 0 ? m : p[3] * u;
+  }
+  return ZQ * s / (double)n;
+}
+
+int orc_pose_objective(double ZQ, const double* points, uint32_t n, const orc_set* B, int32_t ib,
+                       const float* pose, int objective, double* F) {
+  orc_mol mb;
+  int rc = load_mol(B, ib, pose, &mb);
+  if (rc) return rc;
+  *F = crn_objective(&mb, points, n, ZQ, objective);
+  return ORC_OK;
+}
+
+/* Pose from doubles (the float pose of load_mol would round the FD step). */
+static int load_mol_posed_d(const orc_set* S, int32_t idx, const double pose[7], orc_mol* m) {
+  int rc = load_mol(S, idx, NULL, m);
+  if (rc) return rc;
+  double w = pose[0], x = pose[1], y = pose[2], z = pose[3];
+  double nq = sqrt(w * w + x * x + y * y + z * z);
+  if (!(nq > 0)) return ORC_EINVAL;
+  w /= nq; x /= nq; y /= nq; z /= nq;
+  double R[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
+                    {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
+                    {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+  for (int i = 0; i < m->n; ++i) {
+    double c[3] = {m->c[i][0], m->c[i][1], m->c[i][2]};
+    for (int k = 0; k < 3; ++k) m->c[i][k] = R[k][0] * c[0] + R[k][1] * c[1] + R[k][2] * c[2] + pose[4 + k];
+  }
+  return ORC_OK;
+}
+
+/* Central finite differences of the CRN objective in the 7 raw pose
+ * parameters, step h. */
+int orc_pose_grad_fd(double ZQ, const double* points, uint32_t n, const orc_set* B, int32_t ib,
+                     const double pose[7], int objective, double h, double* F, double grad[7]) {
+  orc_mol mb;
+  int rc = load_mol_posed_d(B, ib, pose, &mb);
+  if (rc) return rc;
+  *F = crn_objective(&mb, points, n, ZQ, objective);
+  for (int d = 0; d < 7; ++d) {
+    double pp[7], pm[7];
+    memcpy(pp, pose, sizeof pp);
+    memcpy(pm, pose, sizeof pm);
+    pp[d] += h;
+    pm[d] -= h;
+    orc_mol a, b;
+    if ((rc = load_mol_posed_d(B, ib, pp, &a)) || (rc = load_mol_posed_d(B, ib, pm, &b))) return rc;
+    grad[d] = (crn_objective(&a, points, n, ZQ, objective) - crn_objective(&b, points, n, ZQ, objective)) /
+              (2.0 * h);
+  }
+  return ORC_OK;
+}
+
+/*
+ * Analytic gradient of the closed-form first-order overlap (Eq. fo) with
+ * respect to the 7 raw pose parameters of B: with c'_j = R(q) c_j + t,
+ *   dO/dc'_j = sum_i K_ij 2 a_ij (c_i - c'_j),  a_ij = alpha_i alpha_j /
+ *   (alpha_i + alpha_j), K_ij the (i, j) term of Eq. fo;
+ *   dO/dt = sum_j dO/dc'_j,  dO/dR = sum_j dO/dc'_j c_j^T,
+ * then through R(q) and q = p / |p|.
+ */
+int orc_fo_pose_grad(const orc_set* A, int32_t ia, const orc_set* B, int32_t ib, const double pose[7],
+                     double* F, double grad[7]) {
+  orc_mol ma, mb, mb0;
+  int rc = load_mol(A, ia, NULL, &ma);
+  if (!rc) rc = load_mol(B, ib, NULL, &mb0);
+  if (!rc) rc = load_mol_posed_d(B, ib, pose, &mb);
+  if (rc) return rc;
+  double gt[3] = {0, 0, 0}, gR[3][3] = {{0}}, total = 0.0;
+  for (int j = 0; j < mb.n; ++j) {
+    double gc[3] = {0, 0, 0};
+    for (int i = 0; i < ma.n; ++i) {
+      double ai = ma.alpha[i], bj = mb.alpha[j], s = ai + bj, a = ai * bj / s;
+      double d[3] = {ma.c[i][0] - mb.c[j][0], ma.c[i][1] - mb.c[j][1], ma.c[i][2] - mb.c[j][2]};
+      double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      double t = ORC_PI / s;
+      double K = ma.p[i] * mb.p[j] * t * sqrt(t) * exp(-a * d2);
+      total += K;
+      for (int k = 0; k < 3; ++k) gc[k] += K * 2.0 * a * d[k];
+    }
+    for (int k = 0; k < 3; ++k) {
+      gt[k] += gc[k];
+      for (int l = 0; l < 3; ++l) gR[k][l] += gc[k] * mb0.c[j][l];
+    }
+  }
+  /* dR/dq for the unit quaternion q = (w, x, y, z) */
+  double p0 = pose[0], p1 = pose[1], p2 = pose[2], p3 = pose[3];
+  double nq = sqrt(p0 * p0 + p1 * p1 + p2 * p2 + p3 * p3);
+  double q[4] = {p0 / nq, p1 / nq, p2 / nq, p3 / nq};
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  double dR[4][3][3] = {
+      {{0, -2 * z, 2 * y}, {2 * z, 0, -2 * x}, {-2 * y, 2 * x, 0}},
+      {{0, 2 * y, 2 * z}, {2 * y, -4 * x, -2 * w}, {2 * z, 2 * w, -4 * x}},
+      {{-4 * y, 2 * x, 2 * w}, {2 * x, 0, 2 * z}, {-2 * w, 2 * z, -4 * y}},
+      {{-4 * z, -2 * w, 2 * x}, {2 * w, -4 * z, 2 * y}, {2 * x, 2 * y, 0}}};
+  double gq[4];
+  for (int a = 0; a < 4; ++a) {
+    gq[a] = 0.0;
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l) gq[a] += gR[k][l] * dR[a][k][l];
+  }
+  /* q = p / |p|: dF/dp = (gq - (gq . q) q) / |p| */
+  double dot = gq[0] * q[0] + gq[1] * q[1] + gq[2] * q[2] + gq[3] * q[3];
+  for (int a = 0; a < 4; ++a) grad[a] = (gq[a] - dot * q[a]) / nq;
+  for (int k = 0; k < 3; ++k) grad[4 + k] = gt[k];
+  *F = total;
+  return ORC_OK;
+}
