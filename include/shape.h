@@ -213,6 +213,79 @@ int tanimoto_screen_tune(shp_set Q, shp_set D, const shp_screen* cfg, const doub
                          const double* self_db, float* T, float* seT, uint32_t* n_used,
                          int64_t n_sample, float* timings_ms, int32_t* best, void* stream);
 
+/* ---------------------------------------------------------------------- */
+/* Rigid alignment (Sec. differentiable alignment, Eq. pose, Eq. grad)     */
+/* ---------------------------------------------------------------------- */
+
+#define SHP_TAG_CRN 3u   /* common-random-number points of a query      */
+#define SHP_TAG_START 4u /* random starting rotations of align_rigid     */
+#define SHP_OBJ_FO 0u    /* CRN objective (Z_Q/n) sum_k m_B(r_k)        */
+#define SHP_OBJ_UNION 1u /* CRN objective (Z_Q/n) sum_k w_k u_B(r_k)    */
+
+/*
+ * Common random numbers: mc->n_samples points drawn from Q[iq]'s mixture
+ * (tag SHP_TAG_CRN, stream mc->stream_base, the usual sample layout) with
+ * their union weights: points [n][4] float device = (x, y, z, u_Q/m_Q).
+ */
+int align_crn_points(shp_set Q, int32_t iq, const shp_mc* mc, float* points, void* stream);
+
+/*
+ * Fused forward/adjoint of the CRN overlap (Eq. grad) for items k: molecule
+ * B[ib[k]] moved by pose[k] = (raw quaternion w, x, y, z -- normalised
+ * inside --, translation), the n_points CRN points of Q[iq]:
+ *   value[k] = (Z_Q / n) sum_j f(r_j),  f = m_B (SHP_OBJ_FO) or w_j u_B
+ *              (SHP_OBJ_UNION)
+ *   grad[k][7] = d value[k] / d pose[k]  (through the normalisation)
+ * The union derivative uses prefix and suffix products of (1 - g_l), never
+ * a division by (1 - g_j).
+ *   points [n_points][4] float, ib [n_items] int32, pose [n_items][7] float,
+ *   value [n_items] double, grad [n_items][7] float; all device.
+ */
+int overlap_pose_grad(shp_set Q, int32_t iq, const float* points, uint32_t n_points, shp_set B,
+                      const int32_t* ib, int64_t n_items, const float* pose, uint32_t objective,
+                      double* value, float* grad, void* stream);
+
+/* Multi-start alignment settings. */
+typedef struct {
+  uint64_t seed;      /* Philox key for CRN points, random starts and scoring      */
+  uint64_t stream;    /* Philox stream of the CRN points and scoring base           */
+  uint32_t starts;    /* starts per pair, 1..64: 4 principal-axis sign patterns,
+                         then uniform random rotations                              */
+  uint32_t steps;     /* Adam steps                                                 */
+  uint32_t n_crn;     /* CRN points per step                                        */
+  uint32_t objective; /* SHP_OBJ_FO or SHP_OBJ_UNION                                */
+  float lr, lr_t;     /* Adam step sizes of the quaternion and of the translation   */
+  float beta1, beta2, eps;
+  uint32_t n_score;   /* samples per direction for the final union Tanimoto          */
+} shp_align;
+
+/*
+ * Multi-start rigid alignment of database molecules B[ib[k]] onto the query
+ * Q[iq] (Sec. differentiable alignment): per pair, `starts` poses (B's
+ * principal frame mapped onto Q's with the four proper sign patterns, then
+ * random rotations between the frames, centroids matched), `steps` Adam
+ * ascent steps on the CRN objective, then each final pose is scored by the
+ * symmetrised union Tanimoto (overlap_estimate with n_score samples and the
+ * union self-overlaps self_q[iq][1], self_db[ib[k]][1]) and the best start
+ * is kept.
+ *   self_q [n_q][2], self_db [n_db][2] double device (slot 1 = union)
+ *   pose_out [n_pairs][7], T_out [n_pairs], T_starts [n_pairs][starts]
+ *   (may be NULL) float device.
+ * Scratch (CRN points, per-start poses, scores) is stream-ordered library
+ * memory.
+ */
+int align_rigid(shp_set Q, int32_t iq, shp_set B, const int32_t* ib, int64_t n_pairs,
+                const shp_align* cfg, const double* self_q, const double* self_db, float* pose_out,
+                float* T_out, float* T_starts, void* stream);
+
+/*
+ * Host copy of each molecule's principal frame ([n_mol][12] float: the
+ * Gaussian-volume-weighted centroid, then the 3x3 axis matrix row-major with
+ * the axes as columns, sorted by decreasing second moment, the first two
+ * oriented to a non-negative third moment, det +1).
+ */
+int shape_set_frames(shp_set s, float* frames_host);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,9 @@ MAX_ATOMS = 64
 # Every entry point declared in include/shape.h.
 EXPORTS = ("shp_last_error", "shp_version", "shape_set_load", "shape_set_free", "shape_set_info",
            "shape_set_tables", "overlap_estimate", "union_volume_estimate", "fo_overlap",
-           "tanimoto_screen", "shp_screen_variants", "tanimoto_screen_tune")
+           "tanimoto_screen", "shp_screen_variants", "tanimoto_screen_tune", "align_crn_points",
+           "overlap_pose_grad", "align_rigid", "shape_set_frames")
+OBJ_FO, OBJ_UNION = 0, 1
 
 _P = ctypes.c_void_p
 
@@ -39,6 +41,13 @@ class ShpScreen(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("tau", ctypes.c_float), ("round", ctypes.c_uint32),
                 ("min_n", ctypes.c_uint32), ("cap", ctypes.c_uint32), ("watch", ctypes.c_uint32),
                 ("variant", ctypes.c_int32)]
+
+
+class ShpAlign(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("stream", ctypes.c_uint64), ("starts", ctypes.c_uint32),
+                ("steps", ctypes.c_uint32), ("n_crn", ctypes.c_uint32), ("objective", ctypes.c_uint32),
+                ("lr", ctypes.c_float), ("lr_t", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("n_score", ctypes.c_uint32)]
 
 
 _lib = None
@@ -66,6 +75,11 @@ def load_library():
         "tanimoto_screen": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
         "shp_screen_variants": [],
         "tanimoto_screen_tune": [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int64, _P, _P, _P],
+        "align_crn_points": [_P, ctypes.c_int32, _P, _P, _P],
+        "overlap_pose_grad": [_P, ctypes.c_int32, _P, ctypes.c_uint32, _P, _P, ctypes.c_int64, _P, ctypes.c_uint32,
+                              _P, _P, _P],
+        "align_rigid": [_P, ctypes.c_int32, _P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P],
+        "shape_set_frames": [_P, _P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -121,6 +135,12 @@ class ShapeSet:
         al = np.empty(self.n_atoms, np.uint8)
         _check(load_library().shape_set_tables(self.handle, Z.ctypes.data, thr.ctypes.data, al.ctypes.data))
         return Z, thr, al
+
+    def frames(self):
+        """Host copy of the principal frames, [n_mol, 12] float32 (centroid, axes row-major)."""
+        out = np.empty((self.n_mol, 12), np.float32)
+        _check(load_library().shape_set_frames(self.handle, out.ctypes.data))
+        return out
 
     def free(self):
         if self.handle is not None and self.handle.value:
@@ -272,4 +292,75 @@ def self_overlaps(S: ShapeSet, seed: int, n_samples: int, stream_base: int = 0, 
                                               stream=stream)
     out[:, 0] = fo
     out[:, 1] = so
+    return out
+
+
+# ---------------------------------------------------------------- alignment
+
+def align_crn_points(Q: ShapeSet, iq: int, seed: int, n: int, stream_base: int = 0, stream=None):
+    """[n, 4] float32 device tensor: CRN points of Q[iq] and their union weights."""
+    pts = torch.empty((n, 4), dtype=torch.float32, device=Q.device)
+    mc = ShpMC(seed, stream_base, n, 0)
+    _check(load_library().align_crn_points(Q.handle, iq, ctypes.byref(mc), _dptr(pts), _stream(stream)))
+    return pts
+
+
+def overlap_pose_grad(Q: ShapeSet, iq: int, points: torch.Tensor, B: ShapeSet, ib, pose, objective: int = OBJ_UNION,
+                      stream=None):
+    """(value [n] float64, grad [n, 7] float32): CRN overlap of B[ib[k]] posed by
+    pose[k] and its gradient with respect to the raw pose."""
+    dev = Q.device
+    ib = _device_i32(ib, dev)
+    n = ib.numel()
+    pose = torch.as_tensor(pose, dtype=torch.float32, device=dev).contiguous()
+    if pose.shape != (n, 7):
+        raise ValueError("pose must be [n, 7]")
+    points = points.contiguous()
+    value = torch.empty(n, dtype=torch.float64, device=dev)
+    grad = torch.empty((n, 7), dtype=torch.float32, device=dev)
+    _check(load_library().overlap_pose_grad(Q.handle, iq, _dptr(points), points.shape[0], B.handle, _dptr(ib), n,
+                                            _dptr(pose), objective, _dptr(value), _dptr(grad), _stream(stream)))
+    return value, grad
+
+
+class PoseOverlap(torch.autograd.Function):
+    """Differentiable CRN overlap (Eq. grad): forward and adjoint come from
+    one fused kernel launch; backward scales the saved pose gradient."""
+
+    @staticmethod
+    def forward(ctx, pose, Q, iq, points, B, ib, objective):
+        value, grad = overlap_pose_grad(Q, iq, points, B, ib, pose.detach(), objective)
+        ctx.save_for_backward(grad)
+        return value.to(pose.dtype)
+
+    @staticmethod
+    def backward(ctx, g_out):
+        (grad,) = ctx.saved_tensors
+        return (g_out[:, None] * grad).to(g_out.dtype), None, None, None, None, None, None
+
+
+def pose_overlap(pose, Q: ShapeSet, iq: int, points: torch.Tensor, B: ShapeSet, ib, objective: int = OBJ_UNION):
+    """Autograd-enabled CRN overlap of B[ib[k]] under pose[k] ([n, 7])."""
+    return PoseOverlap.apply(pose, Q, iq, points, B, ib, objective)
+
+
+def align_rigid(Q: ShapeSet, iq: int, B: ShapeSet, ib, self_q: torch.Tensor, self_db: torch.Tensor, seed: int = 0,
+                starts: int = 8, steps: int = 100, n_crn: int = 1024, objective: int = OBJ_UNION, lr: float = 0.05,
+                lr_t: float = 0.1, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, n_score: int = 4096,
+                stream_base: int = 0, with_starts: bool = False, stream=None):
+    """Multi-start Adam alignment of B[ib[k]] onto Q[iq]. Returns dict pose
+    ([n, 7]), T ([n]) and, with with_starts, T_starts ([n, starts])."""
+    dev = Q.device
+    ib = _device_i32(ib, dev)
+    n = ib.numel()
+    cfg = ShpAlign(seed, stream_base, starts, steps, n_crn, objective, lr, lr_t, beta1, beta2, eps, n_score)
+    out = dict(pose=torch.empty((n, 7), dtype=torch.float32, device=dev),
+               T=torch.empty(n, dtype=torch.float32, device=dev))
+    if with_starts:
+        out["T_starts"] = torch.empty((n, starts), dtype=torch.float32, device=dev)
+    self_q = self_q.to(device=dev, dtype=torch.float64).contiguous()
+    self_db = self_db.to(device=dev, dtype=torch.float64).contiguous()
+    _check(load_library().align_rigid(Q.handle, iq, B.handle, _dptr(ib), n, ctypes.byref(cfg), _dptr(self_q),
+                                      _dptr(self_db), _dptr(out["pose"]), _dptr(out["T"]), _dptr(out.get("T_starts")),
+                                      _stream(stream)))
     return out

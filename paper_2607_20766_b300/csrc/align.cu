@@ -1,0 +1,537 @@
+// Differentiable rigid alignment (Sec. differentiable alignment, Eq. pose,
+// Eq. grad): common-random-number (CRN) points from the query, a fused
+// forward/adjoint kernel for the CRN overlap and its gradient with respect
+// to B's pose (raw quaternion w,x,y,z normalised inside, translation), and a
+// persistent multi-start Adam optimiser built on the same device routine.
+//
+// Objective with points r_k drawn once from the query's mixture:
+//   first order  F = (Z_Q / n) sum_k m_B(r_k)
+//   union        F = (Z_Q / n) sum_k w_k u_B(r_k),   w_k = u_Q(r_k) / m_Q(r_k)
+// dF/dc'_j = (Z_Q / n) sum_k c_jk 2 alpha_j g_j(r_k) (r_k - c'_j) with
+// c_jk = 1 (first order) or w_k prod_{l != j} (1 - g_l(r_k)) (union); the
+// product over l != j is formed from prefix and suffix products kept in
+// per-lane shared-memory columns, never by dividing by (1 - g_j) (g_j
+// reaches 1 when p > 1). dF/dt = sum_j dF/dc'_j, dF/dR = sum_j dF/dc'_j c_j^T,
+// then through R(q) and q = p / |p|.
+#include <cmath>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace shp {
+namespace {
+
+constexpr int kAlignWarps = 4;
+constexpr int kAlignThreads = kAlignWarps * 32;
+
+struct __align__(16) AlignTables {
+  float4 body[SHP_MAX_ATOMS];   // B's centres (own frame), alpha
+  float4 posed[SHP_MAX_ATOMS];  // R c + t, -alpha log2(e)
+  float lp[SHP_MAX_ATOMS];      // log2 p
+  float g[SHP_MAX_ATOMS][32];   // per-lane Gaussian values of the current point
+  float pre[SHP_MAX_ATOMS][32]; // per-lane prefix products prod_{l<j} (1 - g_l)
+};
+constexpr size_t kAlignSmem = sizeof(AlignTables) * kAlignWarps;
+
+__device__ __forceinline__ void quat_to_rot(const float q[4], float R[9]) {
+  const float w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Rotation matrix (row-major) to a unit quaternion (w, x, y, z), w >= 0
+// branch chosen by the largest diagonal combination.
+__device__ void rot_to_quat(const float R[9], float q[4]) {
+  const float tr = R[0] + R[4] + R[8];
+  if (tr > 0.f) {
+    const float s = 2.f * sqrtf(tr + 1.f);
+    q[0] = 0.25f * s; q[1] = (R[7] - R[5]) / s; q[2] = (R[2] - R[6]) / s; q[3] = (R[3] - R[1]) / s;
+  } else if (R[0] > R[4] && R[0] > R[8]) {
+    const float s = 2.f * sqrtf(1.f + R[0] - R[4] - R[8]);
+    q[0] = (R[7] - R[5]) / s; q[1] = 0.25f * s; q[2] = (R[1] + R[3]) / s; q[3] = (R[2] + R[6]) / s;
+  } else if (R[4] > R[8]) {
+    const float s = 2.f * sqrtf(1.f + R[4] - R[0] - R[8]);
+    q[0] = (R[2] - R[6]) / s; q[1] = (R[1] + R[3]) / s; q[2] = 0.25f * s; q[3] = (R[5] + R[7]) / s;
+  } else {
+    const float s = 2.f * sqrtf(1.f + R[8] - R[0] - R[4]);
+    q[0] = (R[3] - R[1]) / s; q[1] = (R[2] + R[6]) / s; q[2] = (R[5] + R[7]) / s; q[3] = 0.25f * s;
+  }
+}
+
+__device__ void stage_body(AlignTables& T, const SetView& B, int32_t a0, int nb, int lane) {
+  for (int i = lane; i < nb; i += 32) {
+    T.body[i] = B.atom[a0 + i];
+    T.lp[i] = B.aux[a0 + i].y;
+  }
+  __syncwarp();
+}
+
+__device__ void stage_posed(AlignTables& T, int nb, const float pose[7], int lane) {
+  const float kLog2e = 1.4426950408889634f;
+  float q[4] = {pose[0], pose[1], pose[2], pose[3]};
+  const float inv = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  for (int k = 0; k < 4; ++k) q[k] *= inv;
+  float R[9];
+  quat_to_rot(q, R);
+  __syncwarp();
+  for (int i = lane; i < nb; i += 32) {
+    const float4 c = T.body[i];
+    T.posed[i] = make_float4(fmaf(R[0], c.x, fmaf(R[1], c.y, fmaf(R[2], c.z, pose[4]))),
+                             fmaf(R[3], c.x, fmaf(R[4], c.y, fmaf(R[5], c.z, pose[5]))),
+                             fmaf(R[6], c.x, fmaf(R[7], c.y, fmaf(R[8], c.z, pose[6]))), -c.w * kLog2e);
+  }
+  __syncwarp();
+}
+
+// CRN objective and its gradient at the staged pose. acc = {sum f, dF/dt (3),
+// dF/dR (9)} before the Z_Q / n factor, reduced over the warp (every lane
+// gets lane 0's totals).
+__device__ void value_grad(AlignTables& T, int nb, const float4* __restrict__ pts, int n, int objective, int lane,
+                           float acc[13]) {
+#pragma unroll
+  for (int i = 0; i < 13; ++i) acc[i] = 0.f;
+  for (int k = lane; k < n; k += 32) {
+    const float4 r = pts[k];
+    if (objective == SHP_OBJ_FO) {
+      float m = 0.f;
+      for (int j = 0; j < nb; ++j) {
+        const float4 c = T.posed[j];
+        const float dx = r.x - c.x, dy = r.y - c.y, dz = r.z - c.z;
+        const float g = ex2_approx(fmaf(c.w, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), T.lp[j]));
+        m += g;
+        const float h = -2.f * c.w * 0.6931471805599453f * g;  // 2 alpha g
+        const float4 b = T.body[j];
+        const float gx = h * dx, gy = h * dy, gz = h * dz;
+        acc[1] += gx; acc[2] += gy; acc[3] += gz;
+        acc[4] = fmaf(gx, b.x, acc[4]); acc[5] = fmaf(gx, b.y, acc[5]); acc[6] = fmaf(gx, b.z, acc[6]);
+        acc[7] = fmaf(gy, b.x, acc[7]); acc[8] = fmaf(gy, b.y, acc[8]); acc[9] = fmaf(gy, b.z, acc[9]);
+        acc[10] = fmaf(gz, b.x, acc[10]); acc[11] = fmaf(gz, b.y, acc[11]); acc[12] = fmaf(gz, b.z, acc[12]);
+      }
+      acc[0] += m;
+    } else {
+      float q = 1.f;
+      for (int j = 0; j < nb; ++j) {
+        const float4 c = T.posed[j];
+        const float dx = r.x - c.x, dy = r.y - c.y, dz = r.z - c.z;
+        const float g = ex2_approx(fmaf(c.w, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), T.lp[j]));
+        T.pre[j][lane] = q;
+        T.g[j][lane] = g;
+        q = fmaf(-g, q, q);
+      }
+      acc[0] = fmaf(r.w, 1.f - q, acc[0]);
+      float S = r.w;  // w_k times the suffix product
+      for (int j = nb - 1; j >= 0; --j) {
+        const float g = T.g[j][lane];
+        const float4 c = T.posed[j];
+        const float h = -2.f * c.w * 0.6931471805599453f * g * T.pre[j][lane] * S;
+        S = fmaf(-g, S, S);
+        const float dx = r.x - c.x, dy = r.y - c.y, dz = r.z - c.z;
+        const float4 b = T.body[j];
+        const float gx = h * dx, gy = h * dy, gz = h * dz;
+        acc[1] += gx; acc[2] += gy; acc[3] += gz;
+        acc[4] = fmaf(gx, b.x, acc[4]); acc[5] = fmaf(gx, b.y, acc[5]); acc[6] = fmaf(gx, b.z, acc[6]);
+        acc[7] = fmaf(gy, b.x, acc[7]); acc[8] = fmaf(gy, b.y, acc[8]); acc[9] = fmaf(gy, b.z, acc[9]);
+        acc[10] = fmaf(gz, b.x, acc[10]); acc[11] = fmaf(gz, b.y, acc[11]); acc[12] = fmaf(gz, b.z, acc[12]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 13; ++i) acc[i] = __shfl_sync(0xffffffffu, warp_sum(acc[i]), 0);
+}
+
+// dF/d(raw pose) from dF/dt, dF/dR and the raw quaternion p (q = p/|p|).
+__device__ void pose_gradient(const float pose[7], const float acc[13], float scale, float grad[7]) {
+  const float nq = sqrtf(pose[0] * pose[0] + pose[1] * pose[1] + pose[2] * pose[2] + pose[3] * pose[3]);
+  const float w = pose[0] / nq, x = pose[1] / nq, y = pose[2] / nq, z = pose[3] / nq;
+  const float* G = acc + 4;  // dF/dR, row-major
+  // dR/dw, dR/dx, dR/dy, dR/dz contracted with G
+  const float gw = 2.f * (-z * G[1] + y * G[2] + z * G[3] - x * G[5] - y * G[6] + x * G[7]);
+  const float gx = 2.f * (y * G[1] + z * G[2] + y * G[3] - 2.f * x * G[4] - w * G[5] + z * G[6] + w * G[7] -
+                          2.f * x * G[8]);
+  const float gy = 2.f * (-2.f * y * G[0] + x * G[1] + w * G[2] + x * G[3] + z * G[5] - w * G[6] + z * G[7] -
+                          2.f * y * G[8]);
+  const float gz = 2.f * (-2.f * z * G[0] - w * G[1] + x * G[2] + w * G[3] - 2.f * z * G[4] + y * G[5] +
+                          x * G[6] + y * G[7]);
+  const float dot = gw * w + gx * x + gy * y + gz * z;
+  grad[0] = scale * (gw - dot * w) / nq;
+  grad[1] = scale * (gx - dot * x) / nq;
+  grad[2] = scale * (gy - dot * y) / nq;
+  grad[3] = scale * (gz - dot * z) / nq;
+  grad[4] = scale * acc[1];
+  grad[5] = scale * acc[2];
+  grad[6] = scale * acc[3];
+}
+
+__global__ void crn_points_kernel(SetView Q, int32_t iq, Key key, uint64_t stream, uint32_t n, float4* out) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;  // sample pair
+  if (2u * s >= n) return;
+  const int32_t a0 = Q.off[iq], na = Q.off[iq + 1] - a0;
+  const uint32_t slo = (uint32_t)stream, shi = (uint32_t)(stream >> 32);
+  const uint4 w0 = philox10(make_uint4(2u * s, slo, shi, SHP_TAG_CRN), key);
+  const uint4 w1 = philox10(make_uint4(2u * s + 1u, slo, shi, SHP_TAG_CRN), key);
+  float z[6];
+  box_muller(w0.z, w0.w, z[0], z[1]);
+  box_muller(w1.x, w1.y, z[2], z[3]);
+  box_muller(w1.z, w1.w, z[4], z[5]);
+  const uint32_t words[2] = {w0.x, w0.y};
+  const float zz[2][3] = {{z[0], z[1], z[4]}, {z[2], z[3], z[5]}};
+  const float kLog2e = 1.4426950408889634f;
+  for (int t = 0; t < 2; ++t) {
+    if (2u * s + t >= n) break;
+    const unsigned long long prod = (unsigned long long)words[t] * (unsigned)na;
+    const uint32_t j = (uint32_t)(prod >> 32), f = (uint32_t)prod;
+    const int i = f < Q.thr[a0 + j] ? (int)j : (int)Q.alias[a0 + j];
+    const float4 c = Q.atom[a0 + i];
+    const float sg = Q.aux[a0 + i].x;
+    const float rx = fmaf(sg, zz[t][0], c.x), ry = fmaf(sg, zz[t][1], c.y), rz = fmaf(sg, zz[t][2], c.z);
+    float m = 0.f, q = 1.f;
+    for (int l = 0; l < na; ++l) {
+      const float4 a = Q.atom[a0 + l];
+      const float dx = rx - a.x, dy = ry - a.y, dz = rz - a.z;
+      const float g = ex2_approx(fmaf(-a.w * kLog2e, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), Q.aux[a0 + l].y));
+      m += g;
+      q = fmaf(-g, q, q);
+    }
+    out[2u * s + t] = make_float4(rx, ry, rz, __fdividef(1.f - q, m));
+  }
+}
+
+struct GradArgs {
+  SetView B;
+  const int32_t* ib;
+  const float* pose;
+  const float4* pts;
+  int n_pts;
+  int objective;
+  double scale;  // Z_Q / n
+  int64_t n_items;
+  double* value;
+  float* grad;
+};
+
+__global__ void __launch_bounds__(kAlignThreads) pose_grad_kernel(const GradArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  AlignTables& T = reinterpret_cast<AlignTables*>(smem_raw)[warp];
+  const int64_t item = (int64_t)blockIdx.x * kAlignWarps + warp;
+  if (item >= a.n_items) return;
+  const int32_t xb = a.ib[item];
+  if (xb < 0 || xb >= a.B.n_mol) {
+    if (lane == 0) {
+      a.value[item] = __longlong_as_double(0x7ff8000000000000ll);
+      for (int d = 0; d < 7; ++d) a.grad[7 * item + d] = __int_as_float(0x7fc00000);
+    }
+    return;
+  }
+  const int32_t b0 = a.B.off[xb], nb = a.B.off[xb + 1] - b0;
+  float pose[7];
+  for (int d = 0; d < 7; ++d) pose[d] = a.pose[7 * item + d];
+  stage_body(T, a.B, b0, nb, lane);
+  stage_posed(T, nb, pose, lane);
+  float acc[13];
+  value_grad(T, nb, a.pts, a.n_pts, a.objective, lane, acc);
+  if (lane == 0) {
+    float g[7];
+    pose_gradient(pose, acc, (float)a.scale, g);
+    a.value[item] = a.scale * (double)acc[0];
+    for (int d = 0; d < 7; ++d) a.grad[7 * item + d] = g[d];
+  }
+}
+
+struct AdamArgs {
+  SetView Q, B;
+  int32_t iq;
+  const int32_t* ib;
+  int64_t n_pairs;
+  int starts, steps, objective;
+  const float4* pts;
+  int n_pts;
+  float scale;
+  float lr, lr_t, beta1, beta2, eps;
+  Key key;
+  uint64_t stream;
+  float* pose_out;   // [n_pairs * starts][7]
+  float* value_out;  // [n_pairs * starts]
+  unsigned long long* queue;
+};
+
+// Start s of pair (Q, B): s < 4 maps B's principal frame onto Q's with one
+// of the four proper axis sign patterns; s >= 4 uses a uniform random
+// rotation (Shoemake, from Philox words, tag SHP_TAG_START) between the two
+// frames. The translation matches the frame centroids.
+__device__ void start_pose(const AdamArgs& a, int32_t xb, int64_t pair, int s, float pose[7]) {
+  const float* FA = a.Q.frame + 12 * (int64_t)a.iq;
+  const float* FB = a.B.frame + 12 * (int64_t)xb;
+  float M[9];  // middle rotation in principal coordinates
+  if (s < 4) {
+    const float sx = (s == 2 || s == 3) ? -1.f : 1.f, sy = (s == 1 || s == 3) ? -1.f : 1.f;
+    const float sz = sx * sy;
+    M[0] = sx; M[1] = 0.f; M[2] = 0.f; M[3] = 0.f; M[4] = sy; M[5] = 0.f; M[6] = 0.f; M[7] = 0.f; M[8] = sz;
+  } else {
+    const uint4 w = philox10(make_uint4((uint32_t)s, (uint32_t)pair, (uint32_t)((uint64_t)pair >> 32), SHP_TAG_START),
+                             a.key);
+    const float u1 = (float)(w.x >> 8) * 5.9604644775390625e-08f;
+    const float u2 = (float)(w.y >> 8) * 5.9604644775390625e-08f;
+    const float u3 = (float)(w.z >> 8) * 5.9604644775390625e-08f;
+    const float r1 = sqrtf(1.f - u1), r2 = sqrtf(u1);
+    float s2, c2, s3, c3;
+    sincospif(2.f * u2, &s2, &c2);
+    sincospif(2.f * u3, &s3, &c3);
+    const float q[4] = {r2 * c3, r1 * s2, r1 * c2, r2 * s3};
+    quat_to_rot(q, M);
+  }
+  // R = E_A M E_B^T
+  float T1[9], R[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      float t = 0.f;
+      for (int k = 0; k < 3; ++k) t = fmaf(FA[3 + 3 * i + k], M[3 * k + j], t);
+      T1[3 * i + j] = t;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      float t = 0.f;
+      for (int k = 0; k < 3; ++k) t = fmaf(T1[3 * i + k], FB[3 + 3 * j + k], t);
+      R[3 * i + j] = t;
+    }
+  float q[4];
+  rot_to_quat(R, q);
+  for (int k = 0; k < 4; ++k) pose[k] = q[k];
+  for (int i = 0; i < 3; ++i)
+    pose[4 + i] = FA[i] - (R[3 * i] * FB[0] + R[3 * i + 1] * FB[1] + R[3 * i + 2] * FB[2]);
+}
+
+__global__ void __launch_bounds__(kAlignThreads) align_adam_kernel(const AdamArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  AlignTables& T = reinterpret_cast<AlignTables*>(smem_raw)[warp];
+  const int64_t n_items = a.n_pairs * a.starts;
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(a.queue, 1ull);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= (unsigned long long)n_items) break;
+    const int64_t pair = (int64_t)item / a.starts;
+    const int s = (int)((int64_t)item - pair * a.starts);
+    const int32_t xb = a.ib[pair];
+    if (xb < 0 || xb >= a.B.n_mol) {
+      if (lane == 0) {
+        for (int d = 0; d < 7; ++d) a.pose_out[7 * item + d] = __int_as_float(0x7fc00000);
+        a.value_out[item] = __int_as_float(0x7fc00000);
+      }
+      continue;
+    }
+    const int32_t b0 = a.B.off[xb], nb = a.B.off[xb + 1] - b0;
+    float pose[7], m1[7], m2[7];
+    start_pose(a, xb, pair, s, pose);
+    for (int d = 0; d < 7; ++d) { m1[d] = 0.f; m2[d] = 0.f; }
+    stage_body(T, a.B, b0, nb, lane);
+    float b1t = 1.f, b2t = 1.f, value = 0.f;
+    for (int step = 0; step < a.steps; ++step) {
+      stage_posed(T, nb, pose, lane);
+      float acc[13];
+      value_grad(T, nb, a.pts, a.n_pts, a.objective, lane, acc);
+      float g[7];
+      pose_gradient(pose, acc, a.scale, g);
+      value = a.scale * acc[0];
+      b1t *= a.beta1;
+      b2t *= a.beta2;
+      for (int d = 0; d < 7; ++d) {  // Adam ascent (maximise the overlap)
+        m1[d] = fmaf(a.beta1, m1[d], (1.f - a.beta1) * g[d]);
+        m2[d] = fmaf(a.beta2, m2[d], (1.f - a.beta2) * g[d] * g[d]);
+        const float mh = m1[d] / (1.f - b1t), vh = m2[d] / (1.f - b2t);
+        pose[d] += (d < 4 ? a.lr : a.lr_t) * mh / (sqrtf(vh) + a.eps);
+      }
+      // keep the raw quaternion near unit length (the objective ignores its scale)
+      const float inv = rsqrtf(pose[0] * pose[0] + pose[1] * pose[1] + pose[2] * pose[2] + pose[3] * pose[3]);
+      for (int d = 0; d < 4; ++d) pose[d] *= inv;
+    }
+    if (lane == 0) {
+      for (int d = 0; d < 7; ++d) a.pose_out[7 * item + d] = pose[d];
+      a.value_out[item] = value;
+    }
+    __syncwarp();
+  }
+}
+
+// Best start per pair by the union Tanimoto of the scored poses.
+__global__ void select_best_kernel(int64_t n_pairs, int starts, const double* est, const double* self_q,
+                                   int32_t iq, const double* self_db, int32_t n_db, const int32_t* ib,
+                                   const float* poses, float* pose_out, float* T_out, float* T_starts) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pairs) return;
+  const int32_t xb = ib[p];
+  if (xb < 0 || xb >= n_db) {
+    const float nan = __int_as_float(0x7fc00000);
+    T_out[p] = nan;
+    for (int d = 0; d < 7; ++d) pose_out[7 * p + d] = nan;
+    if (T_starts)
+      for (int s = 0; s < starts; ++s) T_starts[p * starts + s] = nan;
+    return;
+  }
+  float best = -1.f;
+  int bs = 0;
+  for (int s = 0; s < starts; ++s) {
+    const int64_t it = p * starts + s;
+    const double O = est[2 * it + 1];
+    const double S = self_q[2 * (int64_t)iq + 1] + self_db[2 * (int64_t)xb + 1];
+    const float T = (float)(O / (S - O));
+    if (T_starts) T_starts[it] = T;
+    if (T > best) { best = T; bs = s; }
+  }
+  T_out[p] = best;
+  for (int d = 0; d < 7; ++d) pose_out[7 * p + d] = poses[7 * (p * starts + bs) + d];
+}
+
+__global__ void pair_index_kernel(int64_t n_pairs, int starts, int32_t iq, const int32_t* ib, int32_t* ia_out,
+                                  int32_t* ib_out) {
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= n_pairs * starts) return;
+  ia_out[it] = iq;
+  ib_out[it] = ib[it / starts];
+}
+
+int check_points_args(shp_set Q, int32_t iq, const char* who) {
+  if (!Q) { set_error("%s: NULL set", who); return SHP_EINVAL; }
+  if (iq < 0 || iq >= Q->n_mol) { set_error("%s: query index %d out of range", who, iq); return SHP_ERANGE; }
+  return SHP_OK;
+}
+
+}  // namespace
+}  // namespace shp
+
+using namespace shp;
+
+extern "C" int align_crn_points(shp_set Q, int32_t iq, const shp_mc* mc, float* points, void* stream) {
+  clear_error();
+  int rc = check_points_args(Q, iq, "align_crn_points");
+  if (rc) return rc;
+  if (!mc || mc->n_samples < 1 || !points) { set_error("align_crn_points: bad arguments"); return SHP_EINVAL; }
+  const uint32_t pairs = (mc->n_samples + 1u) / 2u;
+  crn_points_kernel<<<(pairs + 127u) / 128u, 128, 0, (cudaStream_t)stream>>>(
+      view(Q), iq, Key{(uint32_t)mc->seed, (uint32_t)(mc->seed >> 32)}, mc->stream_base, mc->n_samples,
+      reinterpret_cast<float4*>(points));
+  SHP_CUDA(cudaGetLastError());
+  return SHP_OK;
+}
+
+extern "C" int overlap_pose_grad(shp_set Q, int32_t iq, const float* points, uint32_t n_points, shp_set B,
+                                 const int32_t* ib, int64_t n_items, const float* pose, uint32_t objective,
+                                 double* value, float* grad, void* stream) {
+  clear_error();
+  int rc = check_points_args(Q, iq, "overlap_pose_grad");
+  if (rc) return rc;
+  if (!B || objective > SHP_OBJ_UNION || n_items < 0 || n_points < 1) {
+    set_error("overlap_pose_grad: bad arguments");
+    return SHP_EINVAL;
+  }
+  if (n_items == 0) return SHP_OK;
+  if (!points || !ib || !pose || !value || !grad) { set_error("overlap_pose_grad: NULL array"); return SHP_EINVAL; }
+  GradArgs a{};
+  a.B = view(B);
+  a.ib = ib;
+  a.pose = pose;
+  a.pts = reinterpret_cast<const float4*>(points);
+  a.n_pts = (int)n_points;
+  a.objective = (int)objective;
+  a.scale = Q->h_Z[iq] / (double)n_points;
+  a.n_items = n_items;
+  a.value = value;
+  a.grad = grad;
+  SHP_CUDA(cudaFuncSetAttribute(pose_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAlignSmem));
+  const int64_t blocks = (n_items + kAlignWarps - 1) / kAlignWarps;
+  pose_grad_kernel<<<(unsigned)blocks, kAlignThreads, kAlignSmem, (cudaStream_t)stream>>>(a);
+  SHP_CUDA(cudaGetLastError());
+  return SHP_OK;
+}
+
+extern "C" int align_rigid(shp_set Q, int32_t iq, shp_set B, const int32_t* ib, int64_t n_pairs,
+                           const shp_align* cfg, const double* self_q, const double* self_db, float* pose_out,
+                           float* T_out, float* T_starts, void* stream) {
+  clear_error();
+  int rc = check_points_args(Q, iq, "align_rigid");
+  if (rc) return rc;
+  if (!B || !cfg || n_pairs < 0) { set_error("align_rigid: bad arguments"); return SHP_EINVAL; }
+  if (cfg->starts < 1 || cfg->starts > 64 || cfg->n_crn < 2 || cfg->n_score < 2 || cfg->objective > SHP_OBJ_UNION ||
+      !(cfg->lr > 0.f) || !(cfg->lr_t > 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
+      !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) || !(cfg->eps > 0.f)) {
+    set_error("align_rigid: invalid configuration");
+    return SHP_EINVAL;
+  }
+  if (n_pairs == 0) return SHP_OK;
+  if (!ib || !self_q || !self_db || !pose_out || !T_out) { set_error("align_rigid: NULL array"); return SHP_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n_items = n_pairs * cfg->starts;
+  float4* pts = nullptr;
+  float* poses = nullptr;
+  float* values = nullptr;
+  int32_t* ia2 = nullptr;
+  int32_t* ib2 = nullptr;
+  double* est = nullptr;
+  double* se = nullptr;
+  unsigned long long* queue = nullptr;
+  auto release = [&]() {
+    cudaFreeAsync(pts, st); cudaFreeAsync(poses, st); cudaFreeAsync(values, st); cudaFreeAsync(ia2, st);
+    cudaFreeAsync(ib2, st); cudaFreeAsync(est, st); cudaFreeAsync(se, st); cudaFreeAsync(queue, st);
+  };
+  cudaError_t e = cudaMallocAsync((void**)&pts, sizeof(float4) * cfg->n_crn, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&poses, sizeof(float) * 7 * n_items, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&values, sizeof(float) * n_items, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&ia2, sizeof(int32_t) * n_items, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&ib2, sizeof(int32_t) * n_items, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&est, sizeof(double) * 2 * n_items, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&se, sizeof(double) * 2 * n_items, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&queue, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) { release(); return cuda_fail(e, "align_rigid: scratch"); }
+  shp_mc mc{cfg->seed, cfg->stream, cfg->n_crn, 0u};
+  rc = align_crn_points(Q, iq, &mc, reinterpret_cast<float*>(pts), stream);
+  if (rc) { release(); return rc; }
+  AdamArgs a{};
+  a.Q = view(Q);
+  a.B = view(B);
+  a.iq = iq;
+  a.ib = ib;
+  a.n_pairs = n_pairs;
+  a.starts = (int)cfg->starts;
+  a.steps = (int)cfg->steps;
+  a.objective = (int)cfg->objective;
+  a.pts = pts;
+  a.n_pts = (int)cfg->n_crn;
+  a.scale = (float)(Q->h_Z[iq] / (double)cfg->n_crn);
+  a.lr = cfg->lr;
+  a.lr_t = cfg->lr_t;
+  a.beta1 = cfg->beta1;
+  a.beta2 = cfg->beta2;
+  a.eps = cfg->eps;
+  a.key = Key{(uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32)};
+  a.stream = cfg->stream;
+  a.pose_out = poses;
+  a.value_out = values;
+  a.queue = queue;
+  e = cudaFuncSetAttribute(align_adam_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAlignSmem);
+  int sms = 0, dev = 0, per_sm = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, align_adam_kernel, kAlignThreads, kAlignSmem);
+  if (e != cudaSuccess) { release(); return cuda_fail(e, "align_rigid: launch set-up"); }
+  int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  const int64_t need = (n_items + kAlignWarps - 1) / kAlignWarps;
+  if (need < grid) grid = need;
+  align_adam_kernel<<<(unsigned)grid, kAlignThreads, kAlignSmem, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) { release(); return cuda_fail(e, "align_rigid: optimiser launch"); }
+  pair_index_kernel<<<(unsigned)((n_items + 255) / 256), 256, 0, st>>>(n_pairs, (int)cfg->starts, iq, ib, ia2, ib2);
+  shp_mc score{cfg->seed ^ 0x5DEECE66Dull, cfg->stream, cfg->n_score, SHP_SYMMETRIC};
+  rc = overlap_estimate(Q, ia2, B, ib2, n_items, poses, &score, est, se, stream);
+  if (rc) { release(); return rc; }
+  select_best_kernel<<<(unsigned)((n_pairs + 255) / 256), 256, 0, st>>>(n_pairs, (int)cfg->starts, est, self_q, iq,
+                                                                         self_db, B->n_mol, ib, poses, pose_out,
+                                                                         T_out, T_starts);
+  e = cudaGetLastError();
+  release();
+  if (e != cudaSuccess) return cuda_fail(e, "align_rigid: selection launch");
+  return SHP_OK;
+}

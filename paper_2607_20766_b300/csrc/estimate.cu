@@ -399,6 +399,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) cross_kernel(const Cr
     } else {
       const int64_t t = (int64_t)item * args.item_stride;
       const int64_t rank = t / args.n_q;
+      if (rank >= args.n_db) continue;
       xa = (int32_t)(t - rank * args.n_q);
       xb = args.order_b[rank];
       out_idx = (int64_t)xa * args.n_db + xb;
@@ -805,6 +806,7 @@ extern "C" int tanimoto_screen_tune(shp_set Q, shp_set D, const shp_screen* cfg,
   if (a.n_items == 0 || n_sample <= 0) { set_error("tanimoto_screen_tune: nothing to time"); return SHP_EINVAL; }
   if (n_sample > a.n_items) n_sample = a.n_items;
   a.item_stride = a.n_items / n_sample;
+  a.n_items = n_sample;  // the kernel visits items 0 .. n_sample-1, pair = item * stride
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   SHP_CUDA(cudaEventCreate(&e0));

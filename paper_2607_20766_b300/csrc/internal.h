@@ -23,11 +23,14 @@ struct shp_set_s {
   int32_t* off = nullptr;    // [n_mol + 1]
   double* Z = nullptr;       // [n_mol] mixture mass
   int32_t* order = nullptr;  // [n_mol] molecule ids, atom count descending
+  float* frame = nullptr;    // [n_mol][12] principal frame: centroid (3), axes E (3x3 row-major,
+                             // columns = axes, det +1)
   // host mirrors
   std::vector<int32_t> h_off;
   std::vector<double> h_Z;
   std::vector<uint32_t> h_thr;
   std::vector<uint8_t> h_alias;
+  std::vector<float> h_frame;
 };
 
 namespace shp {
@@ -40,11 +43,12 @@ struct SetView {
   const uint8_t* alias;
   const int32_t* off;
   const double* Z;
+  const float* frame;
   int32_t n_mol;
 };
 
 inline SetView view(const shp_set_s* s) {
-  return SetView{s->atom, s->aux, s->thr, s->alias, s->off, s->Z, s->n_mol};
+  return SetView{s->atom, s->aux, s->thr, s->alias, s->off, s->Z, s->frame, s->n_mol};
 }
 
 void set_error(const char* fmt, ...);

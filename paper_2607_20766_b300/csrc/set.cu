@@ -64,6 +64,72 @@ static void build_alias(int n, const double* v, uint32_t* thr, uint8_t* alias) {
   for (; lh < lt; ++lh) { thr[lq[lh]] = 0xFFFFFFFFu; alias[lq[lh]] = (uint8_t)lq[lh]; }
 }
 
+// Principal frame of one molecule: centroid weighted by the Gaussian
+// volumes v_i, and the eigenvectors of the weighted second-moment matrix
+// (cyclic Jacobi rotations, FP64) sorted by decreasing eigenvalue; the first
+// two axes point so the weighted third moment of the projection is >= 0, the
+// third completes a proper rotation. out = centroid (3), E row-major (9)
+// with the axes as columns.
+static void principal_frame(int n, const double (*c)[3], const double* v, float* out) {
+  double W = 0.0, cen[3] = {0, 0, 0};
+  for (int i = 0; i < n; ++i) {
+    W += v[i];
+    for (int k = 0; k < 3; ++k) cen[k] += v[i] * c[i][k];
+  }
+  for (int k = 0; k < 3; ++k) cen[k] /= W;
+  double A[3][3] = {{0}};
+  for (int i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) A[a][b] += v[i] * (c[i][a] - cen[a]) * (c[i][b] - cen[b]);
+  double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    const double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    const double diag = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+    if (off <= 1e-30 * (diag + 1e-300)) break;
+    for (int p = 0; p < 2; ++p)
+      for (int q = p + 1; q < 3; ++q) {
+        if (A[p][q] == 0.0) continue;
+        const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < 3; ++k) {  // A <- A J
+          const double akp = A[k][p], akq = A[k][q];
+          A[k][p] = cs * akp - sn * akq;
+          A[k][q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < 3; ++k) {  // A <- J^T A
+          const double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = cs * apk - sn * aqk;
+          A[q][k] = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < 3; ++k) {  // V <- V J
+          const double vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = cs * vkp - sn * vkq;
+          V[k][q] = sn * vkp + cs * vkq;
+        }
+      }
+  }
+  int ord[3] = {0, 1, 2};
+  std::sort(ord, ord + 3, [&](int a, int b) { return A[a][a] > A[b][b]; });
+  double E[3][3];
+  for (int a = 0; a < 2; ++a) {
+    double skew = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double pr = 0.0;
+      for (int k = 0; k < 3; ++k) pr += (c[i][k] - cen[k]) * V[k][ord[a]];
+      skew += v[i] * pr * pr * pr;
+    }
+    const double sg = skew < 0 ? -1.0 : 1.0;
+    for (int k = 0; k < 3; ++k) E[k][a] = sg * V[k][ord[a]];
+  }
+  E[0][2] = E[1][0] * E[2][1] - E[2][0] * E[1][1];
+  E[1][2] = E[2][0] * E[0][1] - E[0][0] * E[2][1];
+  E[2][2] = E[0][0] * E[1][1] - E[1][0] * E[0][1];
+  for (int k = 0; k < 3; ++k) out[k] = (float)cen[k];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) out[3 + 3 * a + b] = (float)E[a][b];
+}
+
 template <class T>
 static int dev_upload(T** dst, const T* src, size_t count, cudaStream_t st) {
   if (count == 0) { *dst = nullptr; return SHP_OK; }
@@ -74,9 +140,9 @@ static int dev_upload(T** dst, const T* src, size_t count, cudaStream_t st) {
 
 static void free_set_memory(shp_set_s* s) {
   cudaFree(s->atom); cudaFree(s->aux); cudaFree(s->thr); cudaFree(s->alias);
-  cudaFree(s->off); cudaFree(s->Z); cudaFree(s->order);
+  cudaFree(s->off); cudaFree(s->Z); cudaFree(s->order); cudaFree(s->frame);
   s->atom = nullptr; s->aux = nullptr; s->thr = nullptr; s->alias = nullptr;
-  s->off = nullptr; s->Z = nullptr; s->order = nullptr;
+  s->off = nullptr; s->Z = nullptr; s->order = nullptr; s->frame = nullptr;
 }
 
 }  // namespace shp
@@ -121,9 +187,11 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
   s->h_Z.assign(n_mol, 0.0);
   s->h_thr.assign(n_atoms, 0u);
   s->h_alias.assign(n_atoms, 0);
+  s->h_frame.assign(12 * (size_t)n_mol, 0.f);
   std::vector<float4> atom(n_atoms);
   std::vector<float2> aux(n_atoms);
   std::vector<double> v(SHP_MAX_ATOMS);
+  double cd[SHP_MAX_ATOMS][3];
   for (int32_t m = 0; m < n_mol; ++m) {
     const int32_t a0 = offsets[m], n = offsets[m + 1] - a0;
     double Z = 0.0;
@@ -144,10 +212,12 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
       v[i] = p * t * std::sqrt(t);
       Z += v[i];
       atom[a] = make_float4((float)x, (float)y, (float)z, (float)alpha);
+      cd[i][0] = (float)x; cd[i][1] = (float)y; cd[i][2] = (float)z;
       aux[a] = make_float2((float)(1.0 / std::sqrt(2.0 * alpha)), (float)std::log2(p));
     }
     s->h_Z[m] = Z;
     build_alias(n, v.data(), &s->h_thr[a0], &s->h_alias[a0]);
+    principal_frame(n, cd, v.data(), &s->h_frame[12 * (size_t)m]);
   }
   std::vector<int32_t> order(n_mol);
   std::iota(order.begin(), order.end(), 0);
@@ -163,6 +233,7 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
   if (!rc) rc = dev_upload(&s->off, s->h_off.data(), s->h_off.size(), st);
   if (!rc) rc = dev_upload(&s->Z, s->h_Z.data(), s->h_Z.size(), st);
   if (!rc) rc = dev_upload(&s->order, order.data(), order.size(), st);
+  if (!rc) rc = dev_upload(&s->frame, s->h_frame.data(), s->h_frame.size(), st);
   if (!rc) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = cuda_fail(e, "shape_set_load: cudaStreamSynchronize");
@@ -204,5 +275,12 @@ extern "C" int shape_set_tables(shp_set s, double* Z, uint32_t* thr, uint8_t* al
   if (Z && s->n_mol) std::memcpy(Z, s->h_Z.data(), sizeof(double) * s->n_mol);
   if (thr && s->n_atoms) std::memcpy(thr, s->h_thr.data(), sizeof(uint32_t) * s->n_atoms);
   if (alias && s->n_atoms) std::memcpy(alias, s->h_alias.data(), s->n_atoms);
+  return SHP_OK;
+}
+
+extern "C" int shape_set_frames(shp_set s, float* frames) {
+  clear_error();
+  if (!s || !frames) { set_error("shape_set_frames: NULL argument"); return SHP_EINVAL; }
+  if (s->n_mol) std::memcpy(frames, s->h_frame.data(), sizeof(float) * 12 * (size_t)s->n_mol);
   return SHP_OK;
 }

@@ -1,0 +1,173 @@
+"""Alignment on the GPU (Sec. differentiable alignment, Eq. pose, Eq. grad)
+against the FP64 oracle: CRN points, the fused forward/adjoint kernel's
+value and gradient (central differences h = 1e-3 of the oracle's CRN
+objective, and the analytic first-order gradient), the autograd wrapper,
+the multi-start optimiser's starts and first Adam step, and recovery of
+known superpositions."""
+import numpy as np
+import pytest
+import torch
+from scipy.spatial.transform import Rotation
+
+import oracle as O
+import paper_2607_20766_b300 as shp
+from paper_2607_20766_b300 import synth
+from paper_2607_20766_b300.synth import MolSet
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mols():
+    q = synth.centre(synth.generate(41, [30]))
+    b = synth.centre(synth.generate(42, [1, 7, 24, 45, 64]))
+    return q, b, shp.shape_set_load(q), shp.shape_set_load(b)
+
+
+def test_principal_frames(mols):
+    q, b, Sq, Sb = mols
+    fr = Sb.frames()
+    for i in range(b.n_mol):
+        x = b.mol(i).astype(np.float64)
+        w = b.radius[b.offsets[i]:b.offsets[i + 1]].astype(np.float64) ** 3
+        c = (w[:, None] * x).sum(0) / w.sum()
+        np.testing.assert_allclose(fr[i, :3], c, atol=2e-5)
+        E = fr[i, 3:].reshape(3, 3)
+        np.testing.assert_allclose(E.T @ E, np.eye(3), atol=1e-5)
+        assert np.linalg.det(E) == pytest.approx(1.0, abs=1e-5)
+        if len(x) >= 4:
+            d = x - c
+            C = (w[:, None, None] * d[:, :, None] * d[:, None, :]).sum(0)
+            ev, V = np.linalg.eigh(C)
+            for k in range(2):  # same axis, same third-moment sign convention
+                v = V[:, 2 - k]
+                v = v if (w * (d @ v) ** 3).sum() >= 0 else -v
+                np.testing.assert_allclose(E[:, k], v, atol=1e-4)
+
+
+def test_crn_points_match_oracle(mols):
+    q, b, Sq, Sb = mols
+    pts = shp.align_crn_points(Sq, 0, seed=9, n=1001, stream_base=4).cpu().numpy()
+    ref = O.crn_points(q, 0, seed=9, stream=4, n=1001)
+    np.testing.assert_allclose(pts[:, :3], ref[:, :3], rtol=1e-5, atol=2e-5)
+    np.testing.assert_allclose(pts[:, 3], ref[:, 3], rtol=2e-5, atol=1e-6)
+
+
+def _poses(k, rng):
+    return np.concatenate([rng.normal(size=(k, 4)), rng.normal(scale=0.8, size=(k, 3))], 1).astype(np.float32)
+
+
+@pytest.mark.parametrize("objective", [shp.OBJ_FO, shp.OBJ_UNION])
+def test_pose_value_and_gradient(mols, objective):
+    q, b, Sq, Sb = mols
+    n = 1024
+    pts_gpu = shp.align_crn_points(Sq, 0, seed=3, n=n, stream_base=7)
+    pts_ref = O.crn_points(q, 0, seed=3, stream=7, n=n)
+    ZQ = O.mixture_mass(q)[0]
+    rng = np.random.default_rng(objective)
+    ib = np.repeat(np.arange(b.n_mol), 3).astype(np.int32)
+    pose = _poses(len(ib), rng)
+    value, grad = shp.overlap_pose_grad(Sq, 0, pts_gpu, Sb, ib, pose, objective=objective)
+    value, grad = value.cpu().numpy(), grad.cpu().numpy()
+    for k in range(len(ib)):
+        F, g = O.pose_grad_fd(ZQ, pts_ref, b, int(ib[k]), pose[k].astype(np.float64), objective=objective, h=1e-3)
+        assert value[k] == pytest.approx(F, rel=1e-5, abs=1e-7 * ZQ)
+        assert np.linalg.norm(grad[k] - g) <= 2e-4 * np.linalg.norm(g) + 1e-6 * ZQ, (k, grad[k], g)
+
+
+def test_crn_first_order_gradient_estimates_analytic(mols):
+    """The IS first-order gradient is an unbiased estimate of the gradient
+    of the closed form (Eq. fo)."""
+    q, b, Sq, Sb = mols
+    pts = shp.align_crn_points(Sq, 0, seed=5, n=1 << 16, stream_base=1)
+    rng = np.random.default_rng(5)
+    ib = np.array([2, 3, 4], np.int32)
+    pose = _poses(3, rng)
+    pose[:, 4:] *= 0.3
+    _, grad = shp.overlap_pose_grad(Sq, 0, pts, Sb, ib, pose, objective=shp.OBJ_FO)
+    grad = grad.cpu().numpy()
+    for k in range(3):
+        _, g_an = O.fo_pose_grad(q, 0, b, int(ib[k]), pose[k].astype(np.float64))
+        assert np.linalg.norm(grad[k] - g_an) < 0.03 * np.linalg.norm(g_an)
+
+
+def test_autograd_wrapper(mols):
+    q, b, Sq, Sb = mols
+    pts = shp.align_crn_points(Sq, 0, seed=1, n=512)
+    rng = np.random.default_rng(1)
+    ib = np.array([1, 2, 3], np.int32)
+    pose = torch.tensor(_poses(3, rng), device="cuda", requires_grad=True)
+    val = shp.pose_overlap(pose, Sq, 0, pts, Sb, ib)
+    (val * torch.tensor([1.0, 2.0, -1.0], device="cuda")).sum().backward()
+    _, g = shp.overlap_pose_grad(Sq, 0, pts, Sb, ib, pose.detach())
+    expect = g * torch.tensor([1.0, 2.0, -1.0], device="cuda")[:, None]
+    torch.testing.assert_close(pose.grad, expect)
+
+
+def _self(S):
+    return shp.self_overlaps(S, seed=2, n_samples=8192)
+
+
+def test_align_starts_and_first_adam_step(mols):
+    q, b, Sq, Sb = mols
+    ib = np.array([2, 3], np.int32)
+    sq, sb = _self(Sq), _self(Sb)
+    r0 = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=4, starts=4, steps=0, n_score=256, with_starts=True)
+    # starts 0..3 are B's principal frame mapped onto Q's (identity / axis flips)
+    FA, FB = Sq.frames()[0], Sb.frames()
+    signs = [(1, 1, 1), (1, -1, -1), (-1, 1, -1), (-1, -1, 1)]
+    # the best of the four is returned; check it is one of them
+    pose0 = r0["pose"].cpu().numpy()
+    for k, i in enumerate(ib):
+        EA, EB = FA[3:].reshape(3, 3).astype(np.float64), FB[i, 3:].reshape(3, 3).astype(np.float64)
+        cands = []
+        for sg in signs:
+            R = EA @ np.diag(sg) @ EB.T
+            t = FA[:3] - R @ FB[i, :3]
+            cands.append((R, t))
+        Rp = Rotation.from_quat([pose0[k, 1], pose0[k, 2], pose0[k, 3], pose0[k, 0]]).as_matrix()
+        assert min(np.abs(Rp - R).max() + np.abs(pose0[k, 4:] - t).max() for R, t in cands) < 1e-4
+    # one Adam step from start 0 moves each raw parameter by lr * sign(grad) (then the quaternion is renormalised)
+    r1 = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=4, starts=1, steps=1, n_crn=1024, lr=1e-3, lr_t=2e-3,
+                         n_score=256)
+    r0s = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=4, starts=1, steps=0, n_score=256)
+    p0 = r0s["pose"].cpu().numpy()
+    pts = shp.align_crn_points(Sq, 0, seed=4, n=1024, stream_base=0)
+    _, g = shp.overlap_pose_grad(Sq, 0, pts, Sb, ib, p0)
+    g = g.cpu().numpy()
+    p1 = r1["pose"].cpu().numpy()
+    np.testing.assert_allclose(p1[:, 4:] - p0[:, 4:], 2e-3 * np.sign(g[:, 4:]), atol=2e-6)
+    qraw = p0[:, :4] + 1e-3 * np.sign(g[:, :4])
+    np.testing.assert_allclose(p1[:, :4], qraw / np.linalg.norm(qraw, axis=1, keepdims=True), atol=2e-6)
+
+
+def test_recovers_known_superpositions():
+    """Rigidly displaced copies (15 A away, random rotation: disjoint, T = 0)
+    are superposed back to a Tanimoto of at least 0.99."""
+    q = synth.principal_axes(synth.generate(51, [30]))
+    rng = np.random.default_rng(8)
+    copies = []
+    for k in range(6):
+        R = Rotation.random(random_state=k).as_matrix()
+        t = rng.normal(size=3)
+        t = 15.0 * t / np.linalg.norm(t)
+        copies.append((q.xyz.astype(np.float64) @ R.T + t).astype(np.float32))
+    others = synth.principal_axes(synth.generate(52, [24, 36]))
+    b = MolSet(np.concatenate(copies + [others.xyz]), np.concatenate([q.radius] * 6 + [others.radius]),
+               np.concatenate([np.arange(7) * 30, 180 + others.offsets[1:]]).astype(np.int32),
+               np.concatenate([q.elem] * 6 + [others.elem]))
+    Sq, Sb = shp.shape_set_load(q), shp.shape_set_load(b)
+    sq, sb = _self(Sq), _self(Sb)
+    ib = np.arange(b.n_mol, dtype=np.int32)
+    res = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=12, starts=8, steps=100, n_crn=1024, n_score=8192)
+    T = res["T"].cpu().numpy()
+    assert np.all(T[:6] >= 0.99), T
+    # the unaligned copies do not overlap at all
+    est, _ = shp.overlap_estimate(Sq, np.zeros(6), Sb, ib[:6], seed=1, n_samples=1024)
+    assert np.all(est.cpu().numpy()[:, 1] < 1e-3)
+    # distinct molecules: alignment does not lower the score of the pre-aligned pose
+    pose_id = np.tile(np.array([1, 0, 0, 0, 0, 0, 0], np.float32), (2, 1))
+    est, _ = shp.overlap_estimate(Sq, np.zeros(2), Sb, ib[6:], seed=1, n_samples=8192, pose=pose_id)
+    S = sq.cpu().numpy()[0, 1] + sb.cpu().numpy()[6:, 1]
+    O_ = est.cpu().numpy()[:, 1]
+    assert np.all(T[6:] >= O_ / (S - O_) - 0.01)
