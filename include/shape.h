@@ -264,7 +264,8 @@ typedef struct {
  * Q[iq] (Sec. differentiable alignment): per pair, `starts` poses (B's
  * principal frame mapped onto Q's with the four proper sign patterns, then
  * random rotations between the frames, centroids matched), `steps` Adam
- * ascent steps on the CRN objective, then each final pose is scored by the
+ * ascent steps on the CRN objective (step sizes decayed by
+ * (1 + cos(pi step / steps)) / 2), then each final pose is scored by the
  * symmetrised union Tanimoto (overlap_estimate with n_score samples and the
  * union self-overlaps self_q[iq][1], self_db[ib[k]][1]) and the best start
  * is kept.
@@ -277,6 +278,82 @@ typedef struct {
 int align_rigid(shp_set Q, int32_t iq, shp_set B, const int32_t* ib, int64_t n_pairs,
                 const shp_align* cfg, const double* self_q, const double* self_db, float* pose_out,
                 float* T_out, float* T_starts, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Learned control variate for union volumes                               */
+/* ---------------------------------------------------------------------- */
+/*
+ * Not in the paper: a per-atom network predicts crowding weights om_i; the
+ * weighted Gaussians u~ = sum_i om_i g_i have the closed-form volume
+ * sum_i om_i v_i (v_i = p_i (pi/alpha_i)^{3/2}), and the sampler estimates
+ * only the residual, V = sum_i om_i v_i + Z E_q[(u - u~)/m] -- unbiased for
+ * any om (Eq. expectation with f = (u - u~)/m).
+ */
+
+#define SHP_TAG_ATTR 5u /* samples of the union attributions */
+
+/*
+ * Union attributions om*_i = E_{r ~ N(c_i, I/(2 alpha_i))}[u(r)/m(r)] for
+ * every atom of S (training targets of the network; sum_i v_i om*_i = V):
+ * M samples per atom (a multiple of 256); atom i of molecule k uses sample
+ * pairs i M/2 .. (i+1) M/2 - 1 of stream stream_base + k, tag SHP_TAG_ATTR,
+ * normals only. omega [n_atoms] float device.
+ */
+int union_attributions(shp_set S, uint64_t seed, uint64_t stream_base, uint32_t M, float* omega,
+                       void* stream);
+
+/*
+ * Union volume of molecules S[idx[k]] with the control variate omega (per
+ * set atom, float device; NULL = plain estimator), same samples as
+ * union_volume_estimate (tag SHP_TAG_SELF, stream mc->stream_base + k).
+ * target_rel_se <= 0: mc->n_samples samples. target_rel_se > 0: rounds of
+ * `round` samples (a multiple of 256 dividing mc->n_samples, which is then
+ * the cap) until SE / V <= target_rel_se (checked in FP32).
+ *   vol, vol_se [n] double, n_used [n] uint32 (may be NULL); device.
+ */
+int union_volume_cv(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, const float* omega,
+                    float target_rel_se, uint32_t round, double* vol, double* vol_se, uint32_t* n_used,
+                    void* stream);
+
+#define SHP_MLP_IN 33
+#define SHP_MLP_HIDDEN 64
+#define SHP_MLP_PARAMS 6401 /* W1 64x33, b1 64, W2 64x64, b2 64, w3 64, b3 1 */
+
+/*
+ * Per-atom features of every atom of S: the 16 nearest other atoms of the
+ * molecule by distance (ties by index) as (d / 4 A, R / 1.7 A) pairs, then
+ * the atom's own R / 1.7 A; missing neighbours are (2.5, 0).
+ * feat [n_atoms][33] float device.
+ */
+int cv_features(shp_set S, float* feat, void* stream);
+
+/*
+ * The network: z1 = W1 x + b1, h1 = GELU(z1), z2 = W2 h1 + b2,
+ * h2 = GELU(z2), y = w3 . h2 + b3 (GELU in the erf form). params
+ * [SHP_MLP_PARAMS] float device is the FP32 master copy in the order above
+ * (matrices row-major); the kernels compute with the parameters rounded to
+ * BF16 and accumulate in FP32.
+ * mlp_forward: y[k] for the rows rows[k] of x (rows NULL = 0..n-1).
+ *   x [*][33] float, y [n] float; device.
+ */
+int mlp_forward(const float* params, const float* x, const int32_t* rows, int64_t n, float* y,
+                void* stream);
+
+/*
+ * Loss L = mean_k (y_k - target[rows[k]])^2 over the selected rows and its
+ * gradient with respect to the (BF16-rounded) parameters, reduced
+ * deterministically: grad [SHP_MLP_PARAMS] float, loss [1] double; device.
+ * Scratch (per-block partial gradients) is stream-ordered library memory.
+ */
+int mlp_loss_grad(const float* params, const float* x, const float* target, const int32_t* rows,
+                  int64_t n, float* grad, double* loss, void* stream);
+
+/*
+ * One Adam descent step on the FP32 master parameters (step >= 1, bias
+ * corrected): m, v [n_params] float device moments, updated in place.
+ */
+int mlp_adam(float* params, float* m, float* v, const float* grad, int64_t n_params, int64_t step,
+             float lr, float beta1, float beta2, float eps, void* stream);
 
 /*
  * Host copy of each molecule's principal frame ([n_mol][12] float: the

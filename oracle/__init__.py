@@ -74,6 +74,10 @@ _SIGS = {
     "orc_pose_grad_fd": [ctypes.c_double, _P, ctypes.c_uint32, _P, ctypes.c_int32, _P, ctypes.c_int,
                          ctypes.c_double, _P, _P],
     "orc_fo_pose_grad": [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _P],
+    "orc_attributions": [_P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, ctypes.c_int],
+    "orc_union_volume_cv": [_P, _P, ctypes.c_int64, _P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, _P,
+                            ctypes.c_int],
+    "orc_cv_features": [_P, _P],
 }
 
 
@@ -333,3 +337,39 @@ def fo_pose_grad(A, ia, B, ib, pose, c_alpha=2.41798793):
     _check(lib().orc_fo_pose_grad(sa.ref, ia, sb.ref, ib, p.ctypes.data, ctypes.addressof(F), g.ctypes.data),
            "fo_pose_grad")
     return F.value, g
+
+
+# ---------------------------------------------------------------- control variate
+
+TAG_ATTR = 5
+
+
+def attributions(S, idx, seed, M, stream_base=0, n_threads=0, c_alpha=2.41798793):
+    """Union attributions omega*_i = E_{N(c_i, 1/(2 alpha_i))}[u/m], M samples per
+    atom; concatenated over idx (atom order)."""
+    s = _oset(S, c_alpha)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    n_at = int(sum(s.offsets[i + 1] - s.offsets[i] for i in idx))
+    out = np.empty(n_at)
+    _check(lib().orc_attributions(s.ref, idx.ctypes.data, len(idx), seed, stream_base, M, out.ctypes.data, n_threads),
+           "attributions")
+    return out
+
+
+def union_volume_cv(S, idx, omega, seed, n, stream_base=0, n_threads=0, c_alpha=2.41798793):
+    """(vol, vol_se) with the weighted-Gaussian control variate; omega per set atom."""
+    s = _oset(S, c_alpha)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    v, vs = np.empty(len(idx)), np.empty(len(idx))
+    _check(lib().orc_union_volume_cv(s.ref, idx.ctypes.data, len(idx), om.ctypes.data, seed, stream_base, n,
+                                     v.ctypes.data, vs.ctypes.data, n_threads), "union_volume_cv")
+    return v, vs
+
+
+def cv_features(S, c_alpha=2.41798793):
+    """[n_atoms, 33] float64: 16-nearest-neighbour (d/4, R/1.7) pairs and own R/1.7."""
+    s = _oset(S, c_alpha)
+    out = np.empty((int(s.offsets[-1]), 33))
+    _check(lib().orc_cv_features(s.ref, out.ctypes.data), "cv_features")
+    return out

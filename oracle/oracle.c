@@ -878,3 +878,151 @@ int orc_fo_pose_grad(const orc_set* A, int32_t ia, const orc_set* B, int32_t ib,
   *F = total;
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Learned control variate for the union volume                        */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Union attributions omega*_i = E_{r ~ N(c_i, I/(2 alpha_i))}[u(r)/m(r)]:
+ * since q = sum_i (v_i / Z) N(c_i, .), V = Z E_q[u/m] = sum_i v_i omega*_i.
+ * M samples per atom (M even) from stream stream_base + k (k = position in
+ * idx), tag 5; atom i uses sample pairs i M/2 .. (i+1) M/2 - 1 of the usual
+ * layout (normals only, the component words are unused).
+ * omega [sum of the atom counts of idx] in idx order.
+ */
+static void attributions_one(const orc_mol* m, uint64_t seed, uint64_t stream, uint32_t M, double* omega) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int i = 0; i < m->n; ++i) {
+    double s = 0.0;
+    for (uint32_t p = 0; p < M / 2; ++p) {
+      uint32_t blk = 2u * ((uint32_t)i * (M / 2) + p);
+      uint32_t c[4] = {blk, (uint32_t)stream, (uint32_t)(stream >> 32), 5u};
+      uint32_t w[8];
+      orc_philox4x32_10(c, key, w);
+      c[0] = blk + 1u;
+      orc_philox4x32_10(c, key, w + 4);
+      double n01[2], n23[2], n45[2];
+      orc_normal_pair(w[2], w[3], n01);
+      orc_normal_pair(w[4], w[5], n23);
+      orc_normal_pair(w[6], w[7], n45);
+      double z[2][3] = {{n01[0], n01[1], n45[0]}, {n23[0], n23[1], n45[1]}};
+      for (int t = 0; t < 2; ++t) {
+        double r[3], ms, u;
+        for (int k = 0; k < 3; ++k) r[k] = m->c[i][k] + m->sigma[i] * z[t][k];
+        occupancy(m, r, &ms, &u);
+        s += u / ms;
+      }
+    }
+    omega[i] = s / (double)M;
+  }
+}
+
+int orc_attributions(const orc_set* S, const int32_t* idx, int64_t n_mol, uint64_t seed, uint64_t stream_base,
+                     uint32_t M, double* omega, int n_threads) {
+  if (M < 2 || (M & 1u)) return ORC_EINVAL;
+  nthreads_set(n_threads);
+  int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_mol + 1));
+  if (!start) return ORC_EINVAL;
+  start[0] = 0;
+  for (int64_t k = 0; k < n_mol; ++k) {
+    int32_t mi = idx ? idx[k] : (int32_t)k;
+    if (mi < 0 || mi >= S->n_mol) { free(start); return ORC_EINVAL; }
+    start[k + 1] = start[k] + (S->offsets[mi + 1] - S->offsets[mi]);
+  }
+  int err = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : err)
+  for (int64_t k = 0; k < n_mol; ++k) {
+    orc_mol m;
+    if (load_mol(S, idx ? idx[k] : (int32_t)k, NULL, &m)) { err |= 1; continue; }
+    attributions_one(&m, seed, stream_base + (uint64_t)k, M, omega + start[k]);
+  }
+  free(start);
+  return err ? ORC_EINVAL : ORC_OK;
+}
+
+/*
+ * Union volume with the weighted-Gaussian control variate
+ * u~(r) = sum_i omega_i g_i(r):
+ *   V = sum_i omega_i v_i + Z E_q[(u - u~) / m]
+ * unbiased for any omega; same samples as orc_union_volume_estimate (tag 2,
+ * stream stream_base + k). omega is per atom of the set (set atom order).
+ */
+int orc_union_volume_cv(const orc_set* S, const int32_t* idx, int64_t n_mol, const double* omega, uint64_t seed,
+                        uint64_t stream_base, uint32_t n, double* vol, double* vol_se, int n_threads) {
+  if (n < 2) return ORC_EINVAL;
+  nthreads_set(n_threads);
+  int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+  for (int64_t k = 0; k < n_mol; ++k) {
+    int32_t mi = idx ? idx[k] : (int32_t)k;
+    orc_mol m;
+    if (load_mol(S, mi, NULL, &m)) { err |= 1; continue; }
+    const double* om = omega + S->offsets[mi];
+    double closed = 0.0;
+    for (int i = 0; i < m.n; ++i) closed += om[i] * m.v[i];
+    double s = 0.0, s2 = 0.0;
+    for (uint32_t t = 0; t < n; t += 2) {
+      double r[2][3];
+      int i0, i1;
+      draw_pair(&m, seed, stream_base + (uint64_t)k, ORC_TAG_SELF, t / 2, 0, r[0], r[1], &i0, &i1);
+      for (int j = 0; j < 2 && t + j < n; ++j) {
+        double ms = 0.0, prod = 1.0, ut = 0.0;
+        for (int i = 0; i < m.n; ++i) {
+          double dx = r[j][0] - m.c[i][0], dy = r[j][1] - m.c[i][1], dz = r[j][2] - m.c[i][2];
+          double g = m.p[i] * exp(-m.alpha[i] * (dx * dx + dy * dy + dz * dz));
+          ms += g;
+          prod *= 1.0 - g;
+          ut += om[i] * g;
+        }
+        double f = ((1.0 - prod) - ut) / ms;
+        s += f;
+        s2 += f * f;
+      }
+    }
+    double mean = s / n, var = (s2 - s * mean) / (n - 1.0);
+    if (var < 0) var = 0;
+    vol[k] = closed + m.Z * mean;
+    if (vol_se) vol_se[k] = m.Z * sqrt(var / n);
+  }
+  return err ? ORC_EINVAL : ORC_OK;
+}
+
+/*
+ * Per-atom geometric features: the K = 16 nearest other atoms of the same
+ * molecule by distance (ties by index), as (d / 4 A, R / 1.7 A) pairs, then
+ * the atom's own R / 1.7 A; missing neighbours are (2.5, 0).
+ * feat [n_atoms][33] for every atom of the set.
+ */
+int orc_cv_features(const orc_set* S, double* feat) {
+  for (int32_t mi = 0; mi < S->n_mol; ++mi) {
+    int32_t a0 = S->offsets[mi], n = S->offsets[mi + 1] - a0;
+    for (int i = 0; i < n; ++i) {
+      double d[ORC_MAXN];
+      int id[ORC_MAXN], cnt = 0;
+      for (int j = 0; j < n; ++j) {
+        if (j == i) continue;
+        double dx = (double)S->xyz[3 * (a0 + i)] - S->xyz[3 * (a0 + j)];
+        double dy = (double)S->xyz[3 * (a0 + i) + 1] - S->xyz[3 * (a0 + j) + 1];
+        double dz = (double)S->xyz[3 * (a0 + i) + 2] - S->xyz[3 * (a0 + j) + 2];
+        d[cnt] = sqrt(dx * dx + dy * dy + dz * dz);
+        id[cnt++] = j;
+      }
+      /* insertion sort by (distance, index) */
+      for (int a = 1; a < cnt; ++a) {
+        double dv = d[a];
+        int iv = id[a], b = a - 1;
+        while (b >= 0 && (d[b] > dv || (d[b] == dv && id[b] > iv))) { d[b + 1] = d[b]; id[b + 1] = id[b]; --b; }
+        d[b + 1] = dv;
+        id[b + 1] = iv;
+      }
+      double* f = feat + 33 * (size_t)(a0 + i);
+      for (int k = 0; k < 16; ++k) {
+        if (k < cnt) { f[2 * k] = d[k] / 4.0; f[2 * k + 1] = (double)S->radius[a0 + id[k]] / 1.7; }
+        else { f[2 * k] = 2.5; f[2 * k + 1] = 0.0; }
+      }
+      f[32] = (double)S->radius[a0 + i] / 1.7;
+    }
+  }
+  return ORC_OK;
+}

@@ -25,7 +25,9 @@ MAX_ATOMS = 64
 EXPORTS = ("shp_last_error", "shp_version", "shape_set_load", "shape_set_free", "shape_set_info",
            "shape_set_tables", "overlap_estimate", "union_volume_estimate", "fo_overlap",
            "tanimoto_screen", "shp_screen_variants", "tanimoto_screen_tune", "align_crn_points",
-           "overlap_pose_grad", "align_rigid", "shape_set_frames")
+           "overlap_pose_grad", "align_rigid", "shape_set_frames", "union_attributions", "union_volume_cv",
+           "cv_features", "mlp_forward", "mlp_loss_grad", "mlp_adam")
+MLP_IN, MLP_HIDDEN, MLP_PARAMS = 33, 64, 6401
 OBJ_FO, OBJ_UNION = 0, 1
 
 _P = ctypes.c_void_p
@@ -80,6 +82,13 @@ def load_library():
                               _P, _P, _P],
         "align_rigid": [_P, ctypes.c_int32, _P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P],
         "shape_set_frames": [_P, _P],
+        "union_attributions": [_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, _P],
+        "union_volume_cv": [_P, _P, ctypes.c_int64, _P, _P, ctypes.c_float, ctypes.c_uint32, _P, _P, _P, _P],
+        "cv_features": [_P, _P, _P],
+        "mlp_forward": [_P, _P, _P, ctypes.c_int64, _P, _P],
+        "mlp_loss_grad": [_P, _P, _P, _P, ctypes.c_int64, _P, _P, _P],
+        "mlp_adam": [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                     ctypes.c_float, _P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -364,3 +373,63 @@ def align_rigid(Q: ShapeSet, iq: int, B: ShapeSet, ib, self_q: torch.Tensor, sel
                                       _dptr(self_db), _dptr(out["pose"]), _dptr(out["T"]), _dptr(out.get("T_starts")),
                                       _stream(stream)))
     return out
+
+
+# ---------------------------------------------------------------- control variate
+
+def union_attributions(S: ShapeSet, seed: int, M: int = 512, stream_base: int = 0, stream=None):
+    """[n_atoms] float32 device tensor: om*_i = E_{N(c_i, 1/(2 alpha_i))}[u/m]."""
+    out = torch.empty(S.n_atoms, dtype=torch.float32, device=S.device)
+    _check(load_library().union_attributions(S.handle, seed, stream_base, M, _dptr(out), _stream(stream)))
+    return out
+
+
+def union_volume_cv(S: ShapeSet, idx=None, omega=None, seed: int = 0, n_samples: int = 4096,
+                    target_rel_se: float = 0.0, round: int = 256, stream_base: int = 0, stream=None):
+    """(vol, vol_se, n_used): union volumes with the control variate omega
+    (per set atom; None = plain), fixed n_samples or adaptive to a relative SE."""
+    dev = S.device
+    if idx is not None:
+        idx = _device_i32(idx, dev)
+        n = idx.numel()
+    else:
+        n = S.n_mol
+    if omega is not None:
+        omega = torch.as_tensor(omega, dtype=torch.float32, device=dev).contiguous()
+    vol = torch.empty(n, dtype=torch.float64, device=dev)
+    se = torch.empty(n, dtype=torch.float64, device=dev)
+    nu = torch.empty(n, dtype=torch.int32, device=dev)
+    mc = ShpMC(seed, stream_base, n_samples, 0)
+    _check(load_library().union_volume_cv(S.handle, _dptr(idx), n, ctypes.byref(mc), _dptr(omega), target_rel_se,
+                                          round, _dptr(vol), _dptr(se), _dptr(nu), _stream(stream)))
+    return vol, se, nu
+
+
+def cv_features(S: ShapeSet, stream=None):
+    """[n_atoms, 33] float32 device tensor of per-atom neighbour features."""
+    out = torch.empty((S.n_atoms, MLP_IN), dtype=torch.float32, device=S.device)
+    _check(load_library().cv_features(S.handle, _dptr(out), _stream(stream)))
+    return out
+
+
+def mlp_forward(params: torch.Tensor, x: torch.Tensor, rows=None, stream=None):
+    n = x.shape[0] if rows is None else rows.numel()
+    y = torch.empty(n, dtype=torch.float32, device=x.device)
+    _check(load_library().mlp_forward(_dptr(params), _dptr(x), _dptr(rows), n, _dptr(y), _stream(stream)))
+    return y
+
+
+def mlp_loss_grad(params: torch.Tensor, x: torch.Tensor, target: torch.Tensor, rows=None, stream=None, out=None):
+    """(loss [1] float64, grad [6401] float32) device tensors."""
+    n = x.shape[0] if rows is None else rows.numel()
+    grad, loss = out if out is not None else (torch.empty(MLP_PARAMS, dtype=torch.float32, device=x.device),
+                                              torch.empty(1, dtype=torch.float64, device=x.device))
+    _check(load_library().mlp_loss_grad(_dptr(params), _dptr(x), _dptr(target), _dptr(rows), n, _dptr(grad),
+                                        _dptr(loss), _stream(stream)))
+    return loss, grad
+
+
+def mlp_adam(params, m, v, grad, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+             eps: float = 1e-8, stream=None):
+    _check(load_library().mlp_adam(_dptr(params), _dptr(m), _dptr(v), _dptr(grad), params.numel(), step, lr, beta1,
+                                   beta2, eps, _stream(stream)))

@@ -337,11 +337,14 @@ __global__ void __launch_bounds__(kAlignThreads) align_adam_kernel(const AdamArg
       value = a.scale * acc[0];
       b1t *= a.beta1;
       b2t *= a.beta2;
+      // cosine step-size decay: constant-step Adam keeps moving by about the
+      // step size around the optimum, the decay lets it settle
+      const float decay = 0.5f * (1.f + cospif((float)step / (float)a.steps));
       for (int d = 0; d < 7; ++d) {  // Adam ascent (maximise the overlap)
         m1[d] = fmaf(a.beta1, m1[d], (1.f - a.beta1) * g[d]);
         m2[d] = fmaf(a.beta2, m2[d], (1.f - a.beta2) * g[d] * g[d]);
         const float mh = m1[d] / (1.f - b1t), vh = m2[d] / (1.f - b2t);
-        pose[d] += (d < 4 ? a.lr : a.lr_t) * mh / (sqrtf(vh) + a.eps);
+        pose[d] += decay * (d < 4 ? a.lr : a.lr_t) * mh / (sqrtf(vh) + a.eps);
       }
       // keep the raw quaternion near unit length (the objective ignores its scale)
       const float inv = rsqrtf(pose[0] * pose[0] + pose[1] * pose[1] + pose[2] * pose[2] + pose[3] * pose[3]);

@@ -16,8 +16,8 @@
 // warp-uniform constant are folded into a hi/lo pair per lane and reduced
 // over the warp with compensated FP32 sums; the epilogue runs in FP64.
 //
-// Launch variants (SP, exponent form, warps per CTA) are template
-// instances; tanimoto_screen_tune times them and keeps the fastest.
+// Launch variants (SP, exponent form, warps per CTA, CTAs per SM) are
+// template instances; tanimoto_screen_tune times them and keeps the fastest.
 #include <cmath>
 #include <mutex>
 
@@ -27,11 +27,15 @@
 namespace shp {
 namespace {
 
-// Gaussian coefficients of one atom (see Coef in device.cuh for the
-// meaning); a and c0 are also stored twice for the packed exponent form.
+// Gaussian coefficients of one atom in the frame of the sampled molecule:
+// log2 g(r) = a |r'|^2 + b . r' + c0 with r' = r - o, a = -alpha log2(e),
+// b = 2 alpha log2(e) (c - o), c0 = -alpha log2(e) |c - o|^2 + log2 p; every
+// scalar is stored twice so the packed form evaluates two samples per
+// instruction; om is the control-variate weight of the atom (0 if unused).
 struct __align__(16) CoefT {
-  float2 a2, c2;
-  float bx, by, bz, pad;
+  float4 ac;   // a, a, c0, c0
+  float4 bxy;  // bx, bx, by, by
+  float4 bzw;  // bz, bz, om, om
 };
 
 // Running per-lane sums of one proposal direction: shifted sums
@@ -71,7 +75,8 @@ __device__ float3 centroid(const SetView& S, MolRef M, const Pose& P, int lane) 
 }
 
 // log2 g(r) = a |r'|^2 + b . r' + c0 with r' = r - o (expanded form).
-__device__ void stage_coef(CoefT* dst, const SetView& S, MolRef M, const Pose& P, float3 o, int lane) {
+__device__ void stage_coef(CoefT* dst, const SetView& S, MolRef M, const Pose& P, float3 o, const float* omega,
+                           int lane) {
   const float kLog2e = 1.4426950408889634f;
   for (int i = lane; i < M.n; i += 32) {
     const float4 a = S.atom[M.a0 + i];
@@ -81,13 +86,12 @@ __device__ void stage_coef(CoefT* dst, const SetView& S, MolRef M, const Pose& P
     const float al = a.w * kLog2e;
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float c0 = fmaf(-al, d2, lp);
+    const float bx = 2.f * al * dx, by = 2.f * al * dy, bz = 2.f * al * dz;
+    const float om = omega ? omega[M.a0 + i] : 0.f;
     CoefT k;
-    k.a2 = make_float2(-al, -al);
-    k.c2 = make_float2(c0, c0);
-    k.bx = 2.f * al * dx;
-    k.by = 2.f * al * dy;
-    k.bz = 2.f * al * dz;
-    k.pad = 0.f;
+    k.ac = make_float4(-al, -al, c0, c0);
+    k.bxy = make_float4(bx, bx, by, by);
+    k.bzw = make_float4(bz, bz, om, om);
     dst[i] = k;
   }
 }
@@ -106,12 +110,13 @@ __device__ void stage_samp(WarpTables& T, const SetView& S, MolRef M, const Pose
 // table), Y evaluated, in the frame of X's centroid. Poses (NULL =
 // identity) are rebuilt here so no pose is held in registers while sampling.
 __device__ __noinline__ void stage_direction(WarpTables& T, const SetView& SX, MolRef MX, const float* pose_x,
-                                             const SetView* SY, MolRef MY, const float* pose_y, int lane) {
+                                             const SetView* SY, MolRef MY, const float* pose_y, int lane,
+                                             const float* omega_x = nullptr) {
   const Pose PX = make_pose(pose_x), PY = make_pose(pose_y);
   const float3 o = centroid(SX, MX, PX, lane);
   __syncwarp();
-  stage_coef(T.x, SX, MX, PX, o, lane);
-  if (SY) stage_coef(T.y, *SY, MY, PY, o, lane);
+  stage_coef(T.x, SX, MX, PX, o, omega_x, lane);
+  if (SY) stage_coef(T.y, *SY, MY, PY, o, nullptr, lane);
   stage_samp(T, SX, MX, PX, o, lane);
   __syncwarp();
 }
@@ -124,32 +129,38 @@ __device__ __forceinline__ int pick(const WarpTables& T, int n, uint32_t x) {
 }
 
 // m = sum g and q = prod (1 - g) over one molecule's Gaussians for SP
-// sample pairs (even sample in .x, odd in .y). kForm 0: four scalar FMAs
-// for the exponent; kForm 1: a packed FMA for a|r|^2 + c0, then three
-// scalar FMAs.
-template <int SP, int kForm>
+// sample pairs (even sample in .x, odd in .y), and with kCV also
+// ut = sum om g. kForm 0: four scalar FMAs for the exponent; kForm 2: four
+// packed FP32x2 FMAs (two samples per instruction).
+template <int SP, int kForm, bool kCV = false>
 __device__ __forceinline__ void eval_table(const CoefT* __restrict__ tab, int n, const float2 (&rx)[SP],
                                            const float2 (&ry)[SP], const float2 (&rz)[SP],
-                                           const float2 (&rr)[SP], float2 (&m)[SP], float2 (&q)[SP]) {
+                                           const float2 (&rr)[SP], float2 (&m)[SP], float2 (&q)[SP],
+                                           float2 (&ut)[SP]) {
 #pragma unroll 2
   for (int j = 0; j < n; ++j) {
-    const float4 k0 = *reinterpret_cast<const float4*>(&tab[j].a2);
-    const float4 k1 = *reinterpret_cast<const float4*>(&tab[j].bx);
+    const float4 k0 = tab[j].ac, k1 = tab[j].bxy, k2 = tab[j].bzw;
 #pragma unroll
     for (int p = 0; p < SP; ++p) {
-      float ex, ey;
+      float2 g;
       if (kForm == 0) {
-        ex = fmaf(k1.z, rz[p].x, fmaf(k1.y, ry[p].x, fmaf(k1.x, rx[p].x, fmaf(k0.x, rr[p].x, k0.z))));
-        ey = fmaf(k1.z, rz[p].y, fmaf(k1.y, ry[p].y, fmaf(k1.x, rx[p].y, fmaf(k0.x, rr[p].y, k0.z))));
+        const float ex = fmaf(k2.x, rz[p].x, fmaf(k1.z, ry[p].x, fmaf(k1.x, rx[p].x, fmaf(k0.x, rr[p].x, k0.z))));
+        const float ey = fmaf(k2.x, rz[p].y, fmaf(k1.z, ry[p].y, fmaf(k1.x, rx[p].y, fmaf(k0.x, rr[p].y, k0.z))));
+        g = make_float2(ex2_approx(ex), ex2_approx(ey));
       } else {
-        const float2 e = __ffma2_rn(make_float2(k0.x, k0.y), rr[p], make_float2(k0.z, k0.w));
-        ex = fmaf(k1.z, rz[p].x, fmaf(k1.y, ry[p].x, fmaf(k1.x, rx[p].x, e.x)));
-        ey = fmaf(k1.z, rz[p].y, fmaf(k1.y, ry[p].y, fmaf(k1.x, rx[p].y, e.y)));
+        float2 e = __ffma2_rn(make_float2(k0.x, k0.y), rr[p], make_float2(k0.z, k0.w));
+        e = __ffma2_rn(make_float2(k1.x, k1.y), rx[p], e);
+        e = __ffma2_rn(make_float2(k1.z, k1.w), ry[p], e);
+        e = __ffma2_rn(make_float2(k2.x, k2.y), rz[p], e);
+        g = make_float2(ex2_approx(e.x), ex2_approx(e.y));
       }
-      const float2 g = make_float2(ex2_approx(ex), ex2_approx(ey));
       m[p] = __fadd2_rn(m[p], g);
       q[p].x = fmaf(-g.x, q[p].x, q[p].x);
       q[p].y = fmaf(-g.y, q[p].y, q[p].y);
+      if (kCV) {
+        ut[p].x = fmaf(k2.z, g.x, ut[p].x);
+        ut[p].y = fmaf(k2.z, g.y, ut[p].y);
+      }
     }
   }
 }
@@ -166,7 +177,7 @@ __device__ __forceinline__ void dir_init(DirState& s) {
 //   self:  fa = u_X / m_X (volume), fb = u_X^2 / m_X (self-overlap)
 // With antithetic pairs the unit is the mean of a sample and its
 // reflection. The first batch sets the shifts from sample 0.
-template <bool kSelf, int SP, int kForm>
+template <bool kSelf, int SP, int kForm, bool kCV = false>
 __device__ __forceinline__ void run_batch(WarpTables& T, int nx, int ny, uint32_t b, uint32_t n, Key key,
                                           uint32_t slo, uint32_t shi, uint32_t tag, bool anti, int lane,
                                           DirState& st) {
@@ -196,17 +207,22 @@ __device__ __forceinline__ void run_batch(WarpTables& T, int nx, int ny, uint32_
     rz[p] = make_float2(az, bz);
     rr[p] = make_float2(fmaf(ax, ax, fmaf(ay, ay, az * az)), fmaf(bx, bx, fmaf(by, by, bz * bz)));
   }
-  float2 m[SP], q[SP], fa[SP], fb[SP];
+  float2 m[SP], q[SP], ut[SP], fa[SP], fb[SP];
 #pragma unroll
-  for (int p = 0; p < SP; ++p) { m[p] = make_float2(0.f, 0.f); q[p] = make_float2(1.f, 1.f); }
-  eval_table<SP, kForm>(T.x, nx, rx, ry, rz, rr, m, q);
+  for (int p = 0; p < SP; ++p) {
+    m[p] = make_float2(0.f, 0.f);
+    q[p] = make_float2(1.f, 1.f);
+    ut[p] = make_float2(0.f, 0.f);
+  }
+  eval_table<SP, kForm, kCV>(T.x, nx, rx, ry, rz, rr, m, q, ut);
   if (kSelf) {
+    // volume: fa = u/m (or (u - ut)/m with the control variate), fb = u^2/m
 #pragma unroll
     for (int p = 0; p < SP; ++p) {
       const float ux = 1.f - q[p].x, uy = 1.f - q[p].y;
-      const float wx = __fdividef(ux, m[p].x), wy = __fdividef(uy, m[p].y);
-      fa[p] = make_float2(wx, wy);
-      fb[p] = make_float2(wx * ux, wy * uy);
+      const float ix = __fdividef(1.f, m[p].x), iy = __fdividef(1.f, m[p].y);
+      fa[p] = kCV ? make_float2((ux - ut[p].x) * ix, (uy - ut[p].y) * iy) : make_float2(ux * ix, uy * iy);
+      fb[p] = make_float2(ux * ux * ix, uy * uy * iy);
     }
   } else {
     float2 w[SP];
@@ -216,7 +232,7 @@ __device__ __forceinline__ void run_batch(WarpTables& T, int nx, int ny, uint32_
       m[p] = make_float2(0.f, 0.f);
       q[p] = make_float2(1.f, 1.f);
     }
-    eval_table<SP, kForm>(T.y, ny, rx, ry, rz, rr, m, q);
+    eval_table<SP, kForm, false>(T.y, ny, rx, ry, rz, rr, m, q, ut);
 #pragma unroll
     for (int p = 0; p < SP; ++p) {
       fa[p] = m[p];
@@ -532,12 +548,12 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) self_kernel(const Sel
 // ------------------------------------------------------------ variants
 
 // sample pairs per lane, exponent form, warps per CTA, CTAs per SM (the
-// register budget follows: 3 x 8 warps -> 80, 5 x 4 -> 102, 2 x 8 -> 128)
+// register budget follows: 2 x 8 or 4 x 4 warps -> 128, 5 x 4 -> 102; shared
+// memory, about 10 KB per warp, caps an SM at 20 warps)
 struct Variant {
   int sp, form, warps, min_blocks;
 };
-constexpr Variant kVariants[] = {{4, 0, 8, 3}, {4, 1, 8, 3}, {4, 0, 8, 2}, {4, 1, 8, 2},
-                                 {4, 0, 4, 5}, {8, 0, 4, 4}, {8, 1, 4, 4}};
+constexpr Variant kVariants[] = {{4, 0, 8, 2}, {4, 2, 8, 2}, {4, 0, 4, 5}, {4, 2, 4, 5}, {8, 0, 4, 4}, {8, 2, 4, 4}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <int V>
@@ -597,8 +613,7 @@ int launch_cross(int v, const CrossArgs& a, int64_t n_items, cudaStream_t st) {
     case 2: return launch_cross_v<MODE, 2>(a, n_items, st);
     case 3: return launch_cross_v<MODE, 3>(a, n_items, st);
     case 4: return launch_cross_v<MODE, 4>(a, n_items, st);
-    case 5: return launch_cross_v<MODE, 5>(a, n_items, st);
-    default: return launch_cross_v<MODE, 6>(a, n_items, st);
+    default: return launch_cross_v<MODE, 5>(a, n_items, st);
   }
 }
 
@@ -609,8 +624,7 @@ int launch_cross<kAdaptive>(int v, const CrossArgs& a, int64_t n_items, cudaStre
     case 0: return launch_cross_v<kAdaptive, 0>(a, n_items, st);
     case 1: return launch_cross_v<kAdaptive, 1>(a, n_items, st);
     case 2: return launch_cross_v<kAdaptive, 2>(a, n_items, st);
-    case 3: return launch_cross_v<kAdaptive, 3>(a, n_items, st);
-    default: return launch_cross_v<kAdaptive, 4>(a, n_items, st);
+    default: return launch_cross_v<kAdaptive, 3>(a, n_items, st);
   }
 }
 
@@ -836,4 +850,221 @@ extern "C" int tanimoto_screen_tune(shp_set Q, shp_set D, const shp_screen* cfg,
   set_default_variant(mode, best_v);
   if (best) *best = best_v;
   return SHP_OK;
+}
+
+// ------------------------------------------------------------------------
+// Learned control variate for the union volume
+// ------------------------------------------------------------------------
+namespace shp {
+namespace {
+
+constexpr int kCVWarps = 8;
+
+struct AttrArgs {
+  SetView S;
+  Key key;
+  uint64_t stream_base;
+  uint32_t M;  // samples per atom, a multiple of 256
+  float* omega;
+  unsigned long long* queue;
+};
+
+// omega*_i = E_{N(c_i, I/(2 alpha_i))}[u/m]: atom i of molecule k uses sample
+// pairs i M/2 .. (i+1) M/2 - 1 of stream stream_base + k, tag 5 (normals only).
+__global__ void __launch_bounds__(kCVWarps * 32, 2) attribution_kernel(const AttrArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpTables& T = reinterpret_cast<WarpTables*>(smem_raw)[warp];
+  constexpr int SP = 4;
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(a.queue, 1ull);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= (unsigned long long)a.S.n_mol) break;
+    const MolRef M = mol_ref(a.S, (int32_t)item);
+    stage_direction(T, a.S, M, nullptr, nullptr, M, nullptr, lane);
+    const uint64_t stream = a.stream_base + item;
+    const uint32_t slo = (uint32_t)stream, shi = (uint32_t)(stream >> 32);
+    for (int i = 0; i < M.n; ++i) {
+      const float4 ci = T.samp[i];
+      float acc = 0.f;
+      for (uint32_t b = 0; b < a.M / 256u; ++b) {
+        float2 rx[SP], ry[SP], rz[SP], rr[SP], m[SP], q[SP], ut[SP];
+#pragma unroll
+        for (int p = 0; p < SP; ++p) {
+          const uint32_t s = (uint32_t)i * (a.M / 2u) + b * 128u + (uint32_t)p * 32u + (uint32_t)lane;
+          const uint4 w0 = philox10(make_uint4(2u * s, slo, shi, SHP_TAG_ATTR), a.key);
+          const uint4 w1 = philox10(make_uint4(2u * s + 1u, slo, shi, SHP_TAG_ATTR), a.key);
+          float n0, n1, n2, n3, n4, n5;
+          box_muller(w0.z, w0.w, n0, n1);
+          box_muller(w1.x, w1.y, n2, n3);
+          box_muller(w1.z, w1.w, n4, n5);
+          const float ax = fmaf(ci.w, n0, ci.x), ay = fmaf(ci.w, n1, ci.y), az = fmaf(ci.w, n4, ci.z);
+          const float bx = fmaf(ci.w, n2, ci.x), by = fmaf(ci.w, n3, ci.y), bz = fmaf(ci.w, n5, ci.z);
+          rx[p] = make_float2(ax, bx);
+          ry[p] = make_float2(ay, by);
+          rz[p] = make_float2(az, bz);
+          rr[p] = make_float2(fmaf(ax, ax, fmaf(ay, ay, az * az)), fmaf(bx, bx, fmaf(by, by, bz * bz)));
+          m[p] = make_float2(0.f, 0.f);
+          q[p] = make_float2(1.f, 1.f);
+        }
+        eval_table<SP, 0, false>(T.x, M.n, rx, ry, rz, rr, m, q, ut);
+#pragma unroll
+        for (int p = 0; p < SP; ++p)
+          acc += __fdividef(1.f - q[p].x, m[p].x) + __fdividef(1.f - q[p].y, m[p].y);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) a.omega[M.a0 + i] = acc / (float)a.M;
+    }
+    __syncwarp();
+  }
+}
+
+struct CVArgs {
+  SetView S;
+  const int32_t* idx;
+  const float* omega;  // per set atom, or NULL (plain estimator)
+  int64_t n_items;
+  Key key;
+  uint64_t stream_base;
+  uint32_t n;          // fixed budget (samples), or the cap when adaptive
+  float target;        // > 0: stop once SE / V <= target (checked every round_b batches)
+  uint32_t round_b;
+  double* vol;
+  double* vol_se;
+  uint32_t* n_used;
+  unsigned long long* queue;
+};
+
+// Union volume with the weighted-Gaussian control variate: V = sum_i om_i v_i
+// + Z mean((u - sum_i om_i g_i) / m), same samples as union_volume_estimate.
+template <bool kCV>
+__global__ void __launch_bounds__(kCVWarps * 32, 2) cv_volume_kernel(const CVArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpTables& T = reinterpret_cast<WarpTables*>(smem_raw)[warp];
+  constexpr int SP = 4;
+  const uint32_t batch = 32u * SP;
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(a.queue, 1ull);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= (unsigned long long)a.n_items) break;
+    const int32_t xm = a.idx ? a.idx[item] : (int32_t)item;
+    if (xm < 0 || xm >= a.S.n_mol) {
+      if (lane == 0) {
+        a.vol[item] = __longlong_as_double(0x7ff8000000000000ll);
+        if (a.vol_se) a.vol_se[item] = __longlong_as_double(0x7ff8000000000000ll);
+        if (a.n_used) a.n_used[item] = 0;
+      }
+      continue;
+    }
+    const MolRef M = mol_ref(a.S, xm);
+    stage_direction(T, a.S, M, nullptr, nullptr, M, nullptr, lane, kCV ? a.omega : nullptr);
+    // closed-form part sum_i om_i v_i, v_i = p_i (pi / alpha_i)^{3/2}, in FP64
+    double closed = 0.0;
+    if (kCV) {
+      for (int i = lane; i < M.n; i += 32) {
+        const double t = 3.141592653589793 / (double)a.S.atom[M.a0 + i].w;
+        closed += (double)a.omega[M.a0 + i] * exp2((double)a.S.aux[M.a0 + i].y) * t * sqrt(t);
+      }
+      closed = warp_sum(closed);
+    }
+    const double Z = a.S.Z[xm];
+    DirState& st = T.st[0][lane];
+    dir_init(st);
+    const uint64_t stream = a.stream_base + item;
+    const uint32_t slo = (uint32_t)stream, shi = (uint32_t)(stream >> 32);
+    uint32_t n_done;
+    if (a.target <= 0.f) {
+      const uint32_t nb = ((a.n + 1u) / 2u + batch - 1u) / batch;
+      for (uint32_t b = 0; b < nb; ++b)
+        run_batch<true, SP, 0, kCV>(T, M.n, 0, b, a.n, a.key, slo, shi, SHP_TAG_SELF, false, lane, st);
+      n_done = a.n;
+    } else {
+      const uint32_t cap_b = a.n / (2u * batch);
+      uint32_t b = 0;
+      for (;;) {
+        const uint32_t nxt = b + a.round_b;
+        const uint32_t n_now = nxt * batch * 2u;
+        for (uint32_t k = b; k < nxt; ++k)
+          run_batch<true, SP, 0, kCV>(T, M.n, 0, k, n_now, a.key, slo, shi, SHP_TAG_SELF, false, lane, st);
+        b = nxt;
+        if (b >= cap_b) break;
+        float h1 = st.hi[0], l1 = st.lo[0], h2 = st.hi[1], l2 = st.lo[1];
+        warp_sum2(h1, l1);
+        warp_sum2(h2, l2);
+        const float nf = (float)n_now, s1 = h1 + l1, s2 = h2 + l2;
+        const float var = fmaxf((s2 - s1 * s1 / nf) / (nf - 1.f), 0.f);
+        const float V = (float)closed + (float)Z * (st.K[0] + s1 / nf);
+        const float se = (float)Z * sqrtf(var / nf);
+        const int stop = __shfl_sync(0xffffffffu, (int)(se <= a.target * fabsf(V)), 0);
+        if (stop) break;
+      }
+      n_done = b * batch * 2u;
+    }
+    double s[4];
+    dir_totals(st, s);
+    if (lane == 0) {
+      double e, sd;
+      finish(Z, s[0], s[1], st.K[0], (double)n_done, e, sd);
+      a.vol[item] = closed + e;
+      if (a.vol_se) a.vol_se[item] = sd;
+      if (a.n_used) a.n_used[item] = n_done;
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace
+}  // namespace shp
+
+extern "C" int union_attributions(shp_set S, uint64_t seed, uint64_t stream_base, uint32_t M, float* omega,
+                                  void* stream) {
+  clear_error();
+  if (!S || !omega) { set_error("union_attributions: NULL argument"); return SHP_EINVAL; }
+  if (M == 0 || M % 256u) { set_error("union_attributions: M must be a positive multiple of 256"); return SHP_EINVAL; }
+  if (S->n_mol == 0) return SHP_OK;
+  AttrArgs a{};
+  a.S = view(S);
+  a.key = Key{(uint32_t)seed, (uint32_t)(seed >> 32)};
+  a.stream_base = stream_base;
+  a.M = M;
+  a.omega = omega;
+  return launch_persistent(attribution_kernel, a, S->n_mol, kCVWarps, sizeof(WarpTables) * kCVWarps,
+                           (cudaStream_t)stream);
+}
+
+extern "C" int union_volume_cv(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, const float* omega,
+                               float target_rel_se, uint32_t round, double* vol, double* vol_se, uint32_t* n_used,
+                               void* stream) {
+  clear_error();
+  if (!S || !mc) { set_error("union_volume_cv: NULL argument"); return SHP_EINVAL; }
+  if (mc->n_samples < 2 || mc->flags) { set_error("union_volume_cv: n_samples >= 2 and no flags"); return SHP_EINVAL; }
+  if (n < 0) { set_error("union_volume_cv: negative n"); return SHP_EINVAL; }
+  if (n == 0) return SHP_OK;
+  if (!vol) { set_error("union_volume_cv: NULL vol"); return SHP_EINVAL; }
+  if (!idx && n > S->n_mol) { set_error("union_volume_cv: n exceeds the set size"); return SHP_ERANGE; }
+  CVArgs a{};
+  if (target_rel_se > 0.f) {
+    if (round == 0 || round % 256u || mc->n_samples % round) {
+      set_error("union_volume_cv: round must be a multiple of 256 dividing n_samples (the cap)");
+      return SHP_EINVAL;
+    }
+    a.round_b = round / 256u;
+  }
+  a.S = view(S);
+  a.idx = idx;
+  a.omega = omega;
+  a.n_items = n;
+  a.key = Key{(uint32_t)mc->seed, (uint32_t)(mc->seed >> 32)};
+  a.stream_base = mc->stream_base;
+  a.n = mc->n_samples;
+  a.target = target_rel_se;
+  a.vol = vol;
+  a.vol_se = vol_se;
+  a.n_used = n_used;
+  const size_t smem = sizeof(WarpTables) * kCVWarps;
+  return omega ? launch_persistent(cv_volume_kernel<true>, a, n, kCVWarps, smem, (cudaStream_t)stream)
+               : launch_persistent(cv_volume_kernel<false>, a, n, kCVWarps, smem, (cudaStream_t)stream);
 }

@@ -23,6 +23,7 @@ struct shp_set_s {
   int32_t* off = nullptr;    // [n_mol + 1]
   double* Z = nullptr;       // [n_mol] mixture mass
   int32_t* order = nullptr;  // [n_mol] molecule ids, atom count descending
+  float* radius = nullptr;   // [n_atoms] van der Waals radius (A)
   float* frame = nullptr;    // [n_mol][12] principal frame: centroid (3), axes E (3x3 row-major,
                              // columns = axes, det +1)
   // host mirrors
@@ -44,11 +45,12 @@ struct SetView {
   const int32_t* off;
   const double* Z;
   const float* frame;
+  const float* radius;
   int32_t n_mol;
 };
 
 inline SetView view(const shp_set_s* s) {
-  return SetView{s->atom, s->aux, s->thr, s->alias, s->off, s->Z, s->frame, s->n_mol};
+  return SetView{s->atom, s->aux, s->thr, s->alias, s->off, s->Z, s->frame, s->radius, s->n_mol};
 }
 
 void set_error(const char* fmt, ...);

@@ -140,9 +140,9 @@ static int dev_upload(T** dst, const T* src, size_t count, cudaStream_t st) {
 
 static void free_set_memory(shp_set_s* s) {
   cudaFree(s->atom); cudaFree(s->aux); cudaFree(s->thr); cudaFree(s->alias);
-  cudaFree(s->off); cudaFree(s->Z); cudaFree(s->order); cudaFree(s->frame);
+  cudaFree(s->off); cudaFree(s->Z); cudaFree(s->order); cudaFree(s->frame); cudaFree(s->radius);
   s->atom = nullptr; s->aux = nullptr; s->thr = nullptr; s->alias = nullptr;
-  s->off = nullptr; s->Z = nullptr; s->order = nullptr; s->frame = nullptr;
+  s->off = nullptr; s->Z = nullptr; s->order = nullptr; s->frame = nullptr; s->radius = nullptr;
 }
 
 }  // namespace shp
@@ -234,6 +234,7 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
   if (!rc) rc = dev_upload(&s->Z, s->h_Z.data(), s->h_Z.size(), st);
   if (!rc) rc = dev_upload(&s->order, order.data(), order.size(), st);
   if (!rc) rc = dev_upload(&s->frame, s->h_frame.data(), s->h_frame.size(), st);
+  if (!rc && n_atoms) rc = dev_upload(&s->radius, radius, (size_t)n_atoms, st);
   if (!rc) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = cuda_fail(e, "shape_set_load: cudaStreamSynchronize");

@@ -70,25 +70,33 @@ def test_pose_value_and_gradient(mols, objective):
     value, grad = shp.overlap_pose_grad(Sq, 0, pts_gpu, Sb, ib, pose, objective=objective)
     value, grad = value.cpu().numpy(), grad.cpu().numpy()
     for k in range(len(ib)):
-        F, g = O.pose_grad_fd(ZQ, pts_ref, b, int(ib[k]), pose[k].astype(np.float64), objective=objective, h=1e-3)
+        # central differences of the FP64 CRN objective: h = 1e-3 carries a
+        # truncation error up to ~2e-4 of the gradient norm, h = 1e-4 ~100x less
+        F, g3 = O.pose_grad_fd(ZQ, pts_ref, b, int(ib[k]), pose[k].astype(np.float64), objective=objective, h=1e-3)
+        _, g4 = O.pose_grad_fd(ZQ, pts_ref, b, int(ib[k]), pose[k].astype(np.float64), objective=objective, h=1e-4)
         assert value[k] == pytest.approx(F, rel=1e-5, abs=1e-7 * ZQ)
-        assert np.linalg.norm(grad[k] - g) <= 2e-4 * np.linalg.norm(g) + 1e-6 * ZQ, (k, grad[k], g)
+        assert np.linalg.norm(grad[k] - g3) <= 1e-3 * np.linalg.norm(g3) + 1e-6 * ZQ, (k, grad[k], g3)
+        assert np.linalg.norm(grad[k] - g4) <= 1e-4 * np.linalg.norm(g4) + 1e-6 * ZQ, (k, grad[k], g4)
 
 
 def test_crn_first_order_gradient_estimates_analytic(mols):
     """The IS first-order gradient is an unbiased estimate of the gradient
     of the closed form (Eq. fo)."""
     q, b, Sq, Sb = mols
-    pts = shp.align_crn_points(Sq, 0, seed=5, n=1 << 16, stream_base=1)
+    nb, per = 32, 4096
+    pts = shp.align_crn_points(Sq, 0, seed=5, n=nb * per, stream_base=1)
     rng = np.random.default_rng(5)
     ib = np.array([2, 3, 4], np.int32)
     pose = _poses(3, rng)
     pose[:, 4:] *= 0.3
-    _, grad = shp.overlap_pose_grad(Sq, 0, pts, Sb, ib, pose, objective=shp.OBJ_FO)
-    grad = grad.cpu().numpy()
+    # independent batches of points give the Monte-Carlo spread of the estimate
+    g_batches = np.stack([shp.overlap_pose_grad(Sq, 0, pts[j * per:(j + 1) * per], Sb, ib, pose,
+                                                objective=shp.OBJ_FO)[1].cpu().numpy() for j in range(nb)])
+    mean, se = g_batches.mean(0), g_batches.std(0, ddof=1) / np.sqrt(nb)
     for k in range(3):
         _, g_an = O.fo_pose_grad(q, 0, b, int(ib[k]), pose[k].astype(np.float64))
-        assert np.linalg.norm(grad[k] - g_an) < 0.03 * np.linalg.norm(g_an)
+        z = (mean[k] - g_an) / se[k]
+        assert np.sum(np.abs(z) > 4) <= 1, z
 
 
 def test_autograd_wrapper(mols):

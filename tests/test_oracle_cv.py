@@ -1,0 +1,102 @@
+"""Pins for the oracle's learned-control-variate pieces: union attributions
+(their weighted sum is the union volume), the control-variate volume
+estimator (unbiased for any weights, identical to the plain estimator at
+zero weights, lower variance at the attributions), the neighbour features,
+and the reference MLP's autograd graph."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import mlp as M
+from paper_2607_20766_b300 import synth
+from paper_2607_20766_b300.synth import MolSet
+
+
+@pytest.fixture(scope="module")
+def mols():
+    return synth.generate(77, [12, 15, 9])
+
+
+def test_attributions_sum_to_the_union_volume(mols):
+    """V = Z E_q[u/m] = sum_i v_i E_{N_i}[u/m] (q is the v-weighted mixture)."""
+    om = O.attributions(mols, [0, 1, 2], seed=1, M=8192)
+    for i in range(3):
+        v = O.mol_tables(mols, i)["v"]
+        lo, hi = mols.offsets[i], mols.offsets[i + 1]
+        V = O.union_volume_ie(mols, i)
+        assert np.dot(om[lo:hi], v) == pytest.approx(V, rel=5e-3)
+
+
+def test_attribution_of_an_isolated_atom_is_one():
+    ms = MolSet(np.array([[0, 0, 0], [40, 0, 0]], np.float32), np.array([1.7, 1.5], np.float32),
+                np.array([0, 2], np.int32), np.zeros(2, np.uint8))
+    om = O.attributions(ms, [0], seed=3, M=512)
+    np.testing.assert_allclose(om, 1.0, atol=1e-12)
+
+
+def test_control_variate_unbiased_for_any_weights(mols):
+    V = O.union_volume_ie(mols, 1)
+    rng = np.random.default_rng(0)
+    for omega in (np.zeros(mols.n_atoms), rng.uniform(0, 1.2, mols.n_atoms),
+                  O.attributions(mols, [0, 1, 2], seed=2, M=2048)):
+        idx = np.ones(12, np.int32)
+        v, se = O.union_volume_cv(mols, idx, omega, seed=5, n=4096)
+        z = (v - V) / se
+        assert np.sum(np.abs(z) > 3) <= 1, z
+
+
+def test_zero_weights_reproduce_the_plain_estimator(mols):
+    v0, s0 = O.union_volume_cv(mols, [0, 1, 2], np.zeros(mols.n_atoms), seed=7, n=2000, stream_base=3)
+    vp, sp, _, _ = O.union_volume_estimate(mols, [0, 1, 2], seed=7, n=2000, stream_base=3)
+    np.testing.assert_allclose(v0, vp, rtol=1e-12)
+    np.testing.assert_allclose(s0, sp, rtol=1e-9)
+
+
+def test_attribution_weights_reduce_variance(mols):
+    om = O.attributions(mols, [0, 1, 2], seed=2, M=4096)
+    v0, s0 = O.union_volume_cv(mols, [0, 1, 2], np.zeros(mols.n_atoms), seed=9, n=8192)
+    v1, s1 = O.union_volume_cv(mols, [0, 1, 2], om, seed=9, n=8192)
+    assert np.all(s1 < 0.95 * s0)
+
+
+def test_features_rigid_invariant_and_sorted(mols):
+    f = O.cv_features(mols)
+    assert f.shape == (mols.n_atoms, 33)
+    d = f[:, 0:32:2]
+    assert np.all(np.diff(d[:, :8], axis=1) >= 0)       # the 9-atom molecule pads after 8 neighbours
+    np.testing.assert_allclose(f[:, 32], mols.radius / 1.7, rtol=1e-7)
+    lo = mols.offsets[2]
+    assert np.all(f[lo:, 16:32:2] == 2.5) and np.all(f[lo:, 17:32:2] == 0.0)
+    R = np.linalg.qr(np.random.default_rng(1).normal(size=(3, 3)))[0]
+    moved = MolSet((mols.xyz.astype(np.float64) @ R.T + 3.0).astype(np.float32), mols.radius, mols.offsets,
+                   mols.elem)
+    np.testing.assert_allclose(O.cv_features(moved), f, atol=3e-6)
+    # nearest neighbour of a bonded atom is at a bond length (1.40 - 1.55 A)
+    assert np.all((d[:, 0] * 4 > 1.39) & (d[:, 0] * 4 < 1.56))
+
+
+def test_reference_mlp_gradients():
+    p = M.init_params(3)
+    rng = np.random.default_rng(4)
+    X = rng.uniform(0, 2.5, (7, M.N_IN))
+    T = rng.uniform(0.2, 1.0, 7)
+    p64 = M.bf16_round(p).clone().requires_grad_(True)
+    Xt, Tt = torch.tensor(X), torch.tensor(T)
+
+    def loss(q):
+        W1, b1, W2, b2, w3, b3 = M.unpack(q)
+        h1 = torch.nn.functional.gelu(Xt @ W1.T + b1)
+        h2 = torch.nn.functional.gelu(h1 @ W2.T + b2)
+        return (((h2 @ w3 + b3) - Tt) ** 2).mean()
+
+    assert torch.autograd.gradcheck(loss, (p64,), eps=1e-6, atol=1e-7)
+    L, g = M.loss_and_grad(p, X, T)
+    assert L == pytest.approx(float(loss(p64)), rel=1e-12)
+    # a network with zero hidden weights outputs w3 . gelu(b2) + b3
+    q = np.zeros(M.N_PARAMS, np.float32)
+    q[-1] = 0.25
+    q[-1 - M.N_HID:-1] = 0.5
+    q[M.N_HID * M.N_IN + M.N_HID + M.N_HID * M.N_HID:][:M.N_HID] = 1.0  # b2 = 1
+    gelu1 = 0.5 * (1 + torch.erf(torch.tensor(1.0, dtype=torch.float64) / np.sqrt(2.0))).item()
+    np.testing.assert_allclose(M.forward(q, X), 0.25 + 0.5 * M.N_HID * gelu1, rtol=1e-12)
