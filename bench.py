@@ -49,6 +49,11 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--adaptive-db", type=int, default=1_000_000,
                    help="database size of the adaptive-screen section (0 skips it)")
+    p.add_argument("--cv-train", type=int, default=200_000,
+                   help="training molecules of the control-variate section (0 skips it)")
+    p.add_argument("--cv-held", type=int, default=50_000)
+    p.add_argument("--align-db", type=int, default=10_000,
+                   help="database size of the alignment section (0 skips it)")
     return p.parse_args()
 
 
@@ -283,6 +288,12 @@ def main():
     adaptive = None
     if args.adaptive_db > 0:
         adaptive = adaptive_section(shp, torch, args.adaptive_db, rank)
+    cvres = None
+    if args.cv_train > 0:
+        cvres = cv_section(shp, torch, args.cv_train, args.cv_held, rank)
+    aligned = None
+    if args.align_db > 0:
+        aligned = align_section(shp, torch, args.align_db, rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -319,6 +330,10 @@ def main():
             line["e2e"] = e2e
         if adaptive is not None:
             line["adaptive"] = adaptive
+        if cvres is not None:
+            line["control_variate"] = cvres
+        if aligned is not None:
+            line["alignment"] = aligned
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -391,6 +406,85 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
         "spearman_rho_vs_fixed": {"mean": float(np.mean(rho)), "min": float(np.min(rho))},
         "tuned_variant": int(best), "variant_ms": [round(float(x), 3) for x in times],
     }
+
+
+def cv_section(shp, torch, n_train: int, n_held: int, rank: int, target: float = 1e-3):
+    """Learned control variate: train the crowding network on union
+    attributions of n_train molecules (18-60 atoms), then estimate the union
+    volume of n_held held-out molecules to relative SE <= target with and
+    without it (rounds of 256 samples, cap 2^21)."""
+    from paper_2607_20766_b300 import cv, synth
+    seed = 9100 + 7919 * rank
+    train = synth.generate(seed, synth.counts_uniform(seed, n_train, 18, 60))
+    held = synth.generate(seed + 1, synth.counts_uniform(seed + 1, n_held, 18, 60))
+    St, Sh = shp.shape_set_load(train), shp.shape_set_load(held)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    (feats, targets), t_data = timed(lambda: cv.attributions_and_features(St, seed=1, M=256))
+    net = cv.CrowdingNet(seed=0)
+    hist, t_train = timed(lambda: net.fit(feats, targets, epochs=8, batch=65536, lr=3e-3))
+    fh = shp.cv_features(Sh)
+    om, t_pred = timed(lambda: net.predict(fh))
+    cap = 1 << 21
+    shp.union_volume_cv(Sh, None, om, seed=5, n_samples=cap, target_rel_se=target)  # warm-up
+    (v_cv, s_cv, n_cv), t_cv = timed(lambda: shp.union_volume_cv(Sh, None, om, seed=5, n_samples=cap,
+                                                                 target_rel_se=target))
+    (v_pl, s_pl, n_pl), t_pl = timed(lambda: shp.union_volume_cv(Sh, None, None, seed=5, n_samples=cap,
+                                                                 target_rel_se=target))
+    n_cv, n_pl = n_cv.cpu().numpy().astype(np.float64), n_pl.cpu().numpy().astype(np.float64)
+    z = ((v_cv - v_pl) / torch.sqrt(s_cv ** 2 + s_pl ** 2)).cpu().numpy()
+    return {
+        "workload": f"learned control variate: train on {n_train} molecules (18-60 atoms, union attributions, 256 "
+                    f"samples/atom), union volume of {n_held} held-out molecules to relative SE <= {target}",
+        "train_seconds": t_train, "targets_seconds": t_data, "predict_seconds": t_pred,
+        "loss_first_last": [hist[0], hist[-1]],
+        "plain": {"mean_samples": float(n_pl.mean()), "seconds": t_pl, "molecules_per_s": n_held / t_pl},
+        "control_variate": {"mean_samples": float(n_cv.mean()), "seconds": t_cv, "molecules_per_s": n_held / t_cv},
+        "sample_ratio": float(n_cv.mean() / n_pl.mean()), "speedup": t_pl / t_cv,
+        "agreement_mean_z": float(z.mean()), "frac_at_cap": [float((n_pl >= cap).mean()), float((n_cv >= cap).mean())],
+    }
+
+
+def align_section(shp, torch, n_db: int, rank: int):
+    """Multi-start rigid alignment: 1 query (30 atoms) x n_db molecules
+    (18-60 atoms), 8 starts, 100 Adam steps on the union CRN objective with
+    1024 points, final union Tanimoto with 4096 samples per direction."""
+    from paper_2607_20766_b300 import synth
+    seed = 5150 + 7919 * rank
+    q = synth.principal_axes(synth.generate(seed, [30]))
+    d = synth.principal_axes(synth.generate(seed + 1, synth.counts_uniform(seed + 1, n_db, 18, 60)))
+    Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
+    sq = shp.self_overlaps(Sq, seed=2, n_samples=8192)
+    sd = shp.self_overlaps(Sd, seed=2, n_samples=8192, stream_base=1)
+    ib = torch.arange(n_db, dtype=torch.int32, device="cuda")
+    shp.align_rigid(Sq, 0, Sd, ib[:64], sq, sd, seed=1)  # warm-up
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = shp.align_rigid(Sq, 0, Sd, ib, sq, sd, seed=1, starts=8, steps=100, n_crn=1024, n_score=4096)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    pose_id = torch.tensor([[1, 0, 0, 0, 0, 0, 0]], dtype=torch.float32, device="cuda").expand(n_db, 7).contiguous()
+    est, _ = shp.overlap_estimate(Sq, torch.zeros(n_db, dtype=torch.int32, device="cuda"), Sd, ib, seed=3,
+                                  n_samples=4096, pose=pose_id)
+    S = sq[0, 1] + sd[:, 1]
+    T0 = (est[:, 1] / (S - est[:, 1])).cpu().numpy()
+    T1 = res["T"].cpu().numpy()
+    return {"workload": f"multi-start alignment: 1 query (30 atoms) x {n_db} molecules, 8 starts x 100 Adam steps, "
+                        f"1024 CRN points, union objective",
+            "seconds": t, "pairs_per_s": n_db / t, "mean_T_prealigned": float(T0.mean()),
+            "mean_T_aligned": float(T1.mean()), "frac_improved": float((T1 >= T0 - 0.005).mean())}
 
 
 def end_to_end(shp, torch, q, d, n, steps: int, warmup: int):
