@@ -221,6 +221,10 @@ int tanimoto_screen_tune(shp_set Q, shp_set D, const shp_screen* cfg, const doub
 #define SHP_TAG_START 4u /* random starting rotations of align_rigid     */
 #define SHP_OBJ_FO 0u    /* CRN objective (Z_Q/n) sum_k m_B(r_k)        */
 #define SHP_OBJ_UNION 1u /* CRN objective (Z_Q/n) sum_k w_k u_B(r_k)    */
+#define SHP_OBJ_FO_CLOSED 2u /* closed-form first-order overlap (Eq. fo): the
+                                exact, deterministic objective of the paper's
+                                hybrid pipeline (align on first order, score on
+                                the union); the CRN points are not used      */
 
 /*
  * Common random numbers: mc->n_samples points drawn from Q[iq]'s mixture

@@ -28,7 +28,7 @@ EXPORTS = ("shp_last_error", "shp_version", "shape_set_load", "shape_set_free", 
            "overlap_pose_grad", "align_rigid", "shape_set_frames", "union_attributions", "union_volume_cv",
            "cv_features", "mlp_forward", "mlp_loss_grad", "mlp_adam")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 33, 64, 6401
-OBJ_FO, OBJ_UNION = 0, 1
+OBJ_FO, OBJ_UNION, OBJ_FO_CLOSED = 0, 1, 2
 
 _P = ctypes.c_void_p
 
@@ -324,10 +324,11 @@ def overlap_pose_grad(Q: ShapeSet, iq: int, points: torch.Tensor, B: ShapeSet, i
     pose = torch.as_tensor(pose, dtype=torch.float32, device=dev).contiguous()
     if pose.shape != (n, 7):
         raise ValueError("pose must be [n, 7]")
-    points = points.contiguous()
+    points = None if points is None else points.contiguous()  # unused by OBJ_FO_CLOSED
     value = torch.empty(n, dtype=torch.float64, device=dev)
     grad = torch.empty((n, 7), dtype=torch.float32, device=dev)
-    _check(load_library().overlap_pose_grad(Q.handle, iq, _dptr(points), points.shape[0], B.handle, _dptr(ib), n,
+    n_points = 0 if points is None else points.shape[0]
+    _check(load_library().overlap_pose_grad(Q.handle, iq, _dptr(points), n_points, B.handle, _dptr(ib), n,
                                             _dptr(pose), objective, _dptr(value), _dptr(grad), _stream(stream)))
     return value, grad
 
@@ -354,8 +355,8 @@ def pose_overlap(pose, Q: ShapeSet, iq: int, points: torch.Tensor, B: ShapeSet, 
 
 
 def align_rigid(Q: ShapeSet, iq: int, B: ShapeSet, ib, self_q: torch.Tensor, self_db: torch.Tensor, seed: int = 0,
-                starts: int = 8, steps: int = 100, n_crn: int = 1024, objective: int = OBJ_UNION, lr: float = 0.05,
-                lr_t: float = 0.1, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, n_score: int = 4096,
+                starts: int = 8, steps: int = 100, n_crn: int = 1024, objective: int = OBJ_UNION, lr: float = 0.02,
+                lr_t: float = 0.05, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, n_score: int = 4096,
                 stream_base: int = 0, with_starts: bool = False, stream=None):
     """Multi-start Adam alignment of B[ib[k]] onto Q[iq]. Returns dict pose
     ([n, 7]), T ([n]) and, with with_starts, T_starts ([n, starts])."""

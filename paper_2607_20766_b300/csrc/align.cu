@@ -28,6 +28,8 @@ struct __align__(16) AlignTables {
   float4 body[SHP_MAX_ATOMS];   // B's centres (own frame), alpha
   float4 posed[SHP_MAX_ATOMS];  // R c + t, -alpha log2(e)
   float lp[SHP_MAX_ATOMS];      // log2 p
+  float4 qatom[SHP_MAX_ATOMS];  // the query's centres and alpha (closed-form objective)
+  float qlp[SHP_MAX_ATOMS];
   float g[SHP_MAX_ATOMS][32];   // per-lane Gaussian values of the current point
   float pre[SHP_MAX_ATOMS][32]; // per-lane prefix products prod_{l<j} (1 - g_l)
 };
@@ -84,14 +86,49 @@ __device__ void stage_posed(AlignTables& T, int nb, const float pose[7], int lan
   __syncwarp();
 }
 
-// CRN objective and its gradient at the staged pose. acc = {sum f, dF/dt (3),
-// dF/dR (9)} before the Z_Q / n factor, reduced over the warp (every lane
-// gets lane 0's totals).
-__device__ void value_grad(AlignTables& T, int nb, const float4* __restrict__ pts, int n, int objective, int lane,
-                           float acc[13]) {
+__device__ void stage_query(AlignTables& T, const SetView& Q, int32_t iq, int lane) {
+  const int32_t a0 = Q.off[iq], na = Q.off[iq + 1] - a0;
+  for (int i = lane; i < na; i += 32) {
+    T.qatom[i] = Q.atom[a0 + i];
+    T.qlp[i] = Q.aux[a0 + i].y;
+  }
+  __syncwarp();
+}
+
+// Objective and gradient at the staged pose. acc = {F, dF/dt (3), dF/dR
+// (9)}, reduced over the warp (every lane gets lane 0's totals). CRN
+// objectives are returned before their Z_Q / n factor; the closed-form first
+// order (Eq. fo) is exact:
+//   F = sum_ij K_ij,  K_ij = p_i p_j (pi/s)^{3/2} exp(-a d^2), s = alpha_i +
+//   alpha_j, a = alpha_i alpha_j / s, dF/dc'_j = sum_i 2 a K_ij (c_i - c'_j).
+__device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restrict__ pts, int n, int objective,
+                           int lane, float acc[13]) {
 #pragma unroll
   for (int i = 0; i < 13; ++i) acc[i] = 0.f;
-  for (int k = lane; k < n; k += 32) {
+  if (objective == SHP_OBJ_FO_CLOSED) {
+    const float kLog2e = 1.4426950408889634f, kPi = 3.14159265358979f;
+    for (int j = lane; j < nb; j += 32) {
+      const float4 c = T.posed[j];
+      const float aj = T.body[j].w;
+      float gx = 0.f, gy = 0.f, gz = 0.f;
+      for (int i = 0; i < na; ++i) {
+        const float4 qa = T.qatom[i];
+        const float dx = qa.x - c.x, dy = qa.y - c.y, dz = qa.z - c.z;
+        const float s = qa.w + aj, inv = 1.f / s, a = qa.w * aj * inv, t = kPi * inv;
+        const float K = t * sqrtf(t) * ex2_approx(fmaf(-a * kLog2e, fmaf(dx, dx, fmaf(dy, dy, dz * dz)),
+                                                        T.qlp[i] + T.lp[j]));
+        acc[0] += K;
+        const float h = 2.f * a * K;
+        gx = fmaf(h, dx, gx); gy = fmaf(h, dy, gy); gz = fmaf(h, dz, gz);
+      }
+      const float4 b = T.body[j];
+      acc[1] += gx; acc[2] += gy; acc[3] += gz;
+      acc[4] = fmaf(gx, b.x, acc[4]); acc[5] = fmaf(gx, b.y, acc[5]); acc[6] = fmaf(gx, b.z, acc[6]);
+      acc[7] = fmaf(gy, b.x, acc[7]); acc[8] = fmaf(gy, b.y, acc[8]); acc[9] = fmaf(gy, b.z, acc[9]);
+      acc[10] = fmaf(gz, b.x, acc[10]); acc[11] = fmaf(gz, b.y, acc[11]); acc[12] = fmaf(gz, b.z, acc[12]);
+    }
+  }
+  for (int k = lane; k < n && objective != SHP_OBJ_FO_CLOSED; k += 32) {
     const float4 r = pts[k];
     if (objective == SHP_OBJ_FO) {
       float m = 0.f;
@@ -204,7 +241,9 @@ struct GradArgs {
   const float4* pts;
   int n_pts;
   int objective;
-  double scale;  // Z_Q / n
+  double scale;  // Z_Q / n for the CRN objectives, 1 for the closed form
+  SetView Q;
+  int32_t iq;
   int64_t n_items;
   double* value;
   float* grad;
@@ -228,9 +267,10 @@ __global__ void __launch_bounds__(kAlignThreads) pose_grad_kernel(const GradArgs
   float pose[7];
   for (int d = 0; d < 7; ++d) pose[d] = a.pose[7 * item + d];
   stage_body(T, a.B, b0, nb, lane);
+  if (a.objective == SHP_OBJ_FO_CLOSED) stage_query(T, a.Q, a.iq, lane);
   stage_posed(T, nb, pose, lane);
   float acc[13];
-  value_grad(T, nb, a.pts, a.n_pts, a.objective, lane, acc);
+  value_grad(T, nb, a.Q.off[a.iq + 1] - a.Q.off[a.iq], a.pts, a.n_pts, a.objective, lane, acc);
   if (lane == 0) {
     float g[7];
     pose_gradient(pose, acc, (float)a.scale, g);
@@ -327,11 +367,13 @@ __global__ void __launch_bounds__(kAlignThreads) align_adam_kernel(const AdamArg
     start_pose(a, xb, pair, s, pose);
     for (int d = 0; d < 7; ++d) { m1[d] = 0.f; m2[d] = 0.f; }
     stage_body(T, a.B, b0, nb, lane);
+    if (a.objective == SHP_OBJ_FO_CLOSED) stage_query(T, a.Q, a.iq, lane);
+    const int na = a.Q.off[a.iq + 1] - a.Q.off[a.iq];
     float b1t = 1.f, b2t = 1.f, value = 0.f;
     for (int step = 0; step < a.steps; ++step) {
       stage_posed(T, nb, pose, lane);
       float acc[13];
-      value_grad(T, nb, a.pts, a.n_pts, a.objective, lane, acc);
+      value_grad(T, nb, na, a.pts, a.n_pts, a.objective, lane, acc);
       float g[7];
       pose_gradient(pose, acc, a.scale, g);
       value = a.scale * acc[0];
@@ -425,20 +467,26 @@ extern "C" int overlap_pose_grad(shp_set Q, int32_t iq, const float* points, uin
   clear_error();
   int rc = check_points_args(Q, iq, "overlap_pose_grad");
   if (rc) return rc;
-  if (!B || objective > SHP_OBJ_UNION || n_items < 0 || n_points < 1) {
+  const bool closed = objective == SHP_OBJ_FO_CLOSED;
+  if (!B || objective > SHP_OBJ_FO_CLOSED || n_items < 0 || (!closed && n_points < 1)) {
     set_error("overlap_pose_grad: bad arguments");
     return SHP_EINVAL;
   }
   if (n_items == 0) return SHP_OK;
-  if (!points || !ib || !pose || !value || !grad) { set_error("overlap_pose_grad: NULL array"); return SHP_EINVAL; }
+  if ((!closed && !points) || !ib || !pose || !value || !grad) {
+    set_error("overlap_pose_grad: NULL array");
+    return SHP_EINVAL;
+  }
   GradArgs a{};
   a.B = view(B);
+  a.Q = view(Q);
+  a.iq = iq;
   a.ib = ib;
   a.pose = pose;
   a.pts = reinterpret_cast<const float4*>(points);
-  a.n_pts = (int)n_points;
+  a.n_pts = closed ? 0 : (int)n_points;
   a.objective = (int)objective;
-  a.scale = Q->h_Z[iq] / (double)n_points;
+  a.scale = closed ? 1.0 : Q->h_Z[iq] / (double)n_points;
   a.n_items = n_items;
   a.value = value;
   a.grad = grad;
@@ -456,7 +504,7 @@ extern "C" int align_rigid(shp_set Q, int32_t iq, shp_set B, const int32_t* ib, 
   int rc = check_points_args(Q, iq, "align_rigid");
   if (rc) return rc;
   if (!B || !cfg || n_pairs < 0) { set_error("align_rigid: bad arguments"); return SHP_EINVAL; }
-  if (cfg->starts < 1 || cfg->starts > 64 || cfg->n_crn < 2 || cfg->n_score < 2 || cfg->objective > SHP_OBJ_UNION ||
+  if (cfg->starts < 1 || cfg->starts > 64 || cfg->n_crn < 2 || cfg->n_score < 2 || cfg->objective > SHP_OBJ_FO_CLOSED ||
       !(cfg->lr > 0.f) || !(cfg->lr_t > 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
       !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) || !(cfg->eps > 0.f)) {
     set_error("align_rigid: invalid configuration");
@@ -501,8 +549,8 @@ extern "C" int align_rigid(shp_set Q, int32_t iq, shp_set B, const int32_t* ib, 
   a.steps = (int)cfg->steps;
   a.objective = (int)cfg->objective;
   a.pts = pts;
-  a.n_pts = (int)cfg->n_crn;
-  a.scale = (float)(Q->h_Z[iq] / (double)cfg->n_crn);
+  a.n_pts = cfg->objective == SHP_OBJ_FO_CLOSED ? 0 : (int)cfg->n_crn;
+  a.scale = cfg->objective == SHP_OBJ_FO_CLOSED ? 1.f : (float)(Q->h_Z[iq] / (double)cfg->n_crn);
   a.lr = cfg->lr;
   a.lr_t = cfg->lr_t;
   a.beta1 = cfg->beta1;

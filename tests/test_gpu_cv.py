@@ -101,7 +101,7 @@ def test_adam_step():
     v1 = 0.999 * v + 0.001 * g * g
     p1 = p - 1e-2 * (m1 / (1 - 0.9 ** 3)) / (np.sqrt(v1 / (1 - 0.999 ** 3)) + 1e-8)
     np.testing.assert_allclose(pt.cpu().numpy(), p1, rtol=1e-5, atol=1e-6)
-    np.testing.assert_allclose(mt.cpu().numpy(), m1, rtol=1e-6)
+    np.testing.assert_allclose(mt.cpu().numpy(), m1, rtol=1e-6, atol=1e-7)
 
 
 def test_trained_network_reduces_variance():
