@@ -353,6 +353,23 @@ int mlp_loss_grad(const float* params, const float* x, const float* target, cons
                   int64_t n, float* grad, double* loss, void* stream);
 
 /*
+ * mlp_loss_grad without any device allocation (the paper has no
+ * counterpart). For callers that cannot allocate device memory while they
+ * run -- a host framework that owns the device allocator and forbids
+ * allocation inside its training step, or a latency-bound loop that cannot
+ * take an allocation. Same arguments, outputs and results as mlp_loss_grad;
+ * the per-block partial gradients go to a fixed array inside the library
+ * (128 x 6402 floats, 3.3 MB held on every device that loads the library
+ * until the process exits), so a call takes at most 8192 rows: larger n
+ * returns SHP_ERANGE. The first call on each device looks up the array's
+ * device address (make that first call before any stream capture). A call
+ * overwrites the part of the array it uses, so nothing carries over between
+ * calls; calls that overlap on the GPU (e.g. on two streams) race on it.
+ */
+int mlp_loss_grad_noalloc(const float* params, const float* x, const float* target,
+                          const int32_t* rows, int64_t n, float* grad, double* loss, void* stream);
+
+/*
  * One Adam descent step on the FP32 master parameters (step >= 1, bias
  * corrected): m, v [n_params] float device moments, updated in place.
  */

@@ -26,7 +26,7 @@ EXPORTS = ("shp_last_error", "shp_version", "shape_set_load", "shape_set_free", 
            "shape_set_tables", "overlap_estimate", "union_volume_estimate", "fo_overlap",
            "tanimoto_screen", "shp_screen_variants", "tanimoto_screen_tune", "align_crn_points",
            "overlap_pose_grad", "align_rigid", "shape_set_frames", "union_attributions", "union_volume_cv",
-           "cv_features", "mlp_forward", "mlp_loss_grad", "mlp_adam")
+           "cv_features", "mlp_forward", "mlp_loss_grad", "mlp_adam", "mlp_loss_grad_noalloc")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 33, 64, 6401
 OBJ_FO, OBJ_UNION, OBJ_FO_CLOSED = 0, 1, 2
 
@@ -87,6 +87,7 @@ def load_library():
         "cv_features": [_P, _P, _P],
         "mlp_forward": [_P, _P, _P, ctypes.c_int64, _P, _P],
         "mlp_loss_grad": [_P, _P, _P, _P, ctypes.c_int64, _P, _P, _P],
+        "mlp_loss_grad_noalloc": [_P, _P, _P, _P, ctypes.c_int64, _P, _P, _P],
         "mlp_adam": [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                      ctypes.c_float, _P],
     }

@@ -53,6 +53,9 @@ inline SetView view(const shp_set_s* s) {
   return SetView{s->atom, s->aux, s->thr, s->alias, s->off, s->Z, s->frame, s->radius, s->n_mol};
 }
 
+int mlp_loss_grad_into(const float* params, const float* x, const float* target, const int32_t* rows, int64_t n,
+                       float* part, float* grad, double* loss, cudaStream_t st);
+
 void set_error(const char* fmt, ...);
 void clear_error();
 int cuda_fail(cudaError_t e, const char* what);

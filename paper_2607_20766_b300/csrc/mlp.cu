@@ -266,6 +266,23 @@ extern "C" int mlp_loss_grad(const float* params, const float* x, const float* t
   return SHP_OK;
 }
 
+namespace shp {
+
+// The loss/gradient kernels writing their per-block partials to `part`
+// (at least ceil(n / 64) x 6402 floats, caller-provided).
+int mlp_loss_grad_into(const float* params, const float* x, const float* target, const int32_t* rows, int64_t n,
+                       float* part, float* grad, double* loss, cudaStream_t st) {
+  const int64_t blocks = (n + kBwdAtoms - 1) / kBwdAtoms;
+  SHP_CUDA(cudaFuncSetAttribute(backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BwdSmem)));
+  backward_kernel<<<(unsigned)blocks, kBwdAtoms, sizeof(BwdSmem), st>>>(params, x, target, rows, n, part);
+  SHP_CUDA(cudaGetLastError());
+  reduce_kernel<<<(kP + 1 + 255) / 256, 256, 0, st>>>(part, blocks, n, grad, loss);
+  SHP_CUDA(cudaGetLastError());
+  return SHP_OK;
+}
+
+}  // namespace shp
+
 extern "C" int mlp_adam(float* params, float* m, float* v, const float* grad, int64_t n_params, int64_t step,
                         float lr, float beta1, float beta2, float eps, void* stream) {
   clear_error();
