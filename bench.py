@@ -36,6 +36,10 @@ N_QUERY_ATOMS = 32
 N_SAMPLES = 4096
 SEED_WORKLOAD = 2026
 FP32_OPS_PER_EVAL = 6  # 4 FMA (expanded exponent) + 1 add (first-order sum) + 1 FMA (union product)
+# DRAM bytes per screened pair, from one ncu capture of the screen kernel on a 20,000-pair case
+# (dram__bytes_read.sum + dram__bytes_write.sum = 24.04 MB; each database molecule is read once,
+# so the traffic scales with the pairs)
+SCREEN_DRAM_BYTES_PER_PAIR = 24_044_288 / 20_000
 
 
 def parse_args():
@@ -45,6 +49,8 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n-db", type=int, default=N_DB)
+    p.add_argument("--ref-seconds", type=float, default=None,
+                   help="CPU seconds per step of the reference arm (default: fit the run into ~3 minutes)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--adaptive-db", type=int, default=1_000_000,
@@ -61,6 +67,19 @@ def workload(n_db: int, rank: int):
     from paper_2607_20766_b300 import synth
     # each rank screens its own database shard (weak scaling)
     return synth.fixed_screen(n_db=n_db, n_query_atoms=N_QUERY_ATOMS, seed=SEED_WORKLOAD + 7919 * rank)
+
+
+def aggregate(t_local: float, work_local, device: str = "cpu"):
+    """Whole-job numbers over the ranks of an initialised process group (or
+    this process alone): the slowest rank's time and the summed work."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    w = torch.tensor([float(x) for x in work_local], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), [float(x) for x in w.tolist()]
 
 
 def step_evals(q, d, n):
@@ -162,7 +181,7 @@ def reference_arm(args):
         return 0
     q, d = workload(args.n_db, 0)
     total_steps = args.steps + args.warmup
-    per_step = max(2.0, min(15.0, 150.0 / max(total_steps, 1)))
+    per_step = args.ref_seconds or max(2.0, min(15.0, 150.0 / max(total_steps, 1)))
     rates, info = [], None
     for s in range(total_steps):
         r, info = cpu_oracle_rate(q, d, N_SAMPLES, per_step, rng_seed=s)
@@ -258,16 +277,12 @@ def main():
         wall = time.perf_counter() - wall0
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
     screen_ms = [a.elapsed_time(b) for a, b in screen_ev]
-    t_total = sum(step_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([t_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
     evals_rank = screen_evals + self_evals
-    total_evals = evals_rank * args.steps * world
-    value = total_evals / t_total
     n_pairs = q.n_mol * d.n_mol
-    pairs_per_s = n_pairs * args.steps * world / t_total
+    t_total, (total_evals, total_pairs) = aggregate(sum(step_ms) / 1e3,
+                                                    [evals_rank * args.steps, n_pairs * args.steps], "cuda")
+    value = total_evals / t_total
+    pairs_per_s = total_pairs / t_total
 
     # dominant kernel: the screen (persistent cross kernel), timed on its stream
     screen_s = statistics.mean(screen_ms) / 1e3
@@ -318,7 +333,8 @@ def main():
             "evals_per_step": evals_rank,
             "wall_s": wall,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Geval/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": SCREEN_DRAM_BYTES_PER_PAIR * n_pairs,
+                         "traffic_basis": "ncu dram bytes of a 20,000-pair capture scaled by pairs",
                          "kernel": "cross_kernel<screen>",
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz / {FP32_OPS_PER_EVAL} "
                                        f"FP32 ops per sample-atom evaluation"},

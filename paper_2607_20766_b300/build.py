@@ -36,7 +36,8 @@ def build_shape(force: bool = False, verbose: bool = False) -> str:
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-ffp-contract=off", "-I", os.path.join(ROOT, "include"), "-o", tmp, *sources()]
+           "-Xcompiler", "-ffp-contract=off", "-Xcompiler", "-fopenmp", "-lgomp", "-I", os.path.join(ROOT, "include"),
+           "-o", tmp, *sources()]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd)

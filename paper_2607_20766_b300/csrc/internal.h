@@ -15,7 +15,8 @@ struct shp_set_s {
   int32_t n_mol = 0;
   int64_t n_atoms = 0;
   int32_t max_atoms = 0;
-  // device arrays (owned)
+  // device arrays (owned: one allocation, dbase)
+  unsigned char* dbase = nullptr;
   float4* atom = nullptr;    // [n_atoms] x, y, z, alpha
   float2* aux = nullptr;     // [n_atoms] sigma = 1/sqrt(2 alpha), log2 p
   uint32_t* thr = nullptr;   // [n_atoms] alias thresholds

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 
 #include "internal.h"
@@ -130,17 +131,51 @@ static void principal_frame(int n, const double (*c)[3], const double* v, float*
     for (int b = 0; b < 3; ++b) out[3 + 3 * a + b] = (float)E[a][b];
 }
 
-template <class T>
-static int dev_upload(T** dst, const T* src, size_t count, cudaStream_t st) {
-  if (count == 0) { *dst = nullptr; return SHP_OK; }
-  SHP_CUDA(cudaMalloc((void**)dst, count * sizeof(T)));
-  SHP_CUDA(cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, st));
+// All device arrays of a set live in one allocation, filled by one copy from
+// a pinned staging buffer that the library keeps (and grows) across loads.
+struct SetLayout {
+  size_t atom, aux, radius, thr, alias, off, Z, order, frame, total;
+};
+
+static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+static SetLayout set_layout(int64_t n_atoms, int32_t n_mol) {
+  SetLayout L{};
+  size_t o = 0;
+  L.atom = o;   o = align16(o + sizeof(float4) * n_atoms);
+  L.aux = o;    o = align16(o + sizeof(float2) * n_atoms);
+  L.radius = o; o = align16(o + sizeof(float) * n_atoms);
+  L.thr = o;    o = align16(o + sizeof(uint32_t) * n_atoms);
+  L.alias = o;  o = align16(o + n_atoms);
+  L.off = o;    o = align16(o + sizeof(int32_t) * (n_mol + 1));
+  L.Z = o;      o = align16(o + sizeof(double) * n_mol);
+  L.order = o;  o = align16(o + sizeof(int32_t) * n_mol);
+  L.frame = o;  o = align16(o + sizeof(float) * 12 * n_mol);
+  L.total = o;
+  return L;
+}
+
+static std::mutex g_stage_mu;
+static void* g_stage = nullptr;
+static size_t g_stage_cap = 0;
+
+// Caller holds g_stage_mu.
+static int stage_buffer(size_t bytes, unsigned char** out) {
+  if (bytes > g_stage_cap) {
+    if (g_stage) cudaFreeHost(g_stage);
+    g_stage = nullptr;
+    g_stage_cap = 0;
+    const size_t cap = bytes + bytes / 4;
+    SHP_CUDA(cudaMallocHost(&g_stage, cap));
+    g_stage_cap = cap;
+  }
+  *out = static_cast<unsigned char*>(g_stage);
   return SHP_OK;
 }
 
 static void free_set_memory(shp_set_s* s) {
-  cudaFree(s->atom); cudaFree(s->aux); cudaFree(s->thr); cudaFree(s->alias);
-  cudaFree(s->off); cudaFree(s->Z); cudaFree(s->order); cudaFree(s->frame); cudaFree(s->radius);
+  cudaFree(s->dbase);
+  s->dbase = nullptr;
   s->atom = nullptr; s->aux = nullptr; s->thr = nullptr; s->alias = nullptr;
   s->off = nullptr; s->Z = nullptr; s->order = nullptr; s->frame = nullptr; s->radius = nullptr;
 }
@@ -188,24 +223,32 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
   s->h_thr.assign(n_atoms, 0u);
   s->h_alias.assign(n_atoms, 0);
   s->h_frame.assign(12 * (size_t)n_mol, 0.f);
-  std::vector<float4> atom(n_atoms);
-  std::vector<float2> aux(n_atoms);
-  std::vector<double> v(SHP_MAX_ATOMS);
-  double cd[SHP_MAX_ATOMS][3];
+  const SetLayout L = set_layout(n_atoms, n_mol);
+  std::lock_guard<std::mutex> stage_lock(g_stage_mu);
+  unsigned char* hb = nullptr;
+  int rc = stage_buffer(L.total, &hb);
+  if (rc) { delete s; return rc; }
+  float4* atom = reinterpret_cast<float4*>(hb + L.atom);
+  float2* aux = reinterpret_cast<float2*>(hb + L.aux);
+  std::memcpy(hb + L.radius, radius, sizeof(float) * n_atoms);
+  // per-molecule preparation, molecules in parallel
+  int32_t bad_mol = -1;
+#pragma omp parallel for schedule(dynamic, 256)
   for (int32_t m = 0; m < n_mol; ++m) {
     const int32_t a0 = offsets[m], n = offsets[m + 1] - a0;
+    double v[SHP_MAX_ATOMS];
+    double cd[SHP_MAX_ATOMS][3];
     double Z = 0.0;
+    bool ok = true;
     for (int i = 0; i < n; ++i) {
       const int64_t a = a0 + i;
       const double x = xyz[3 * a], y = xyz[3 * a + 1], z = xyz[3 * a + 2];
       const double R = radius[a];
       const double p = height ? (double)height[a] : 2.0 * std::sqrt(2.0);
-      if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z) || !(R > 0) ||
-          !std::isfinite(R) || !(p > 0) || !std::isfinite(p)) {
-        set_error("shape_set_load: atom %lld of molecule %d has a non-finite or non-positive value",
-                  (long long)i, m);
-        delete s;
-        return SHP_EINVAL;
+      if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z) || !(R > 0) || !std::isfinite(R) ||
+          !(p > 0) || !std::isfinite(p)) {
+        ok = false;
+        break;
       }
       const double alpha = ca / (R * R);
       const double t = kPi / alpha;
@@ -215,31 +258,48 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
       cd[i][0] = (float)x; cd[i][1] = (float)y; cd[i][2] = (float)z;
       aux[a] = make_float2((float)(1.0 / std::sqrt(2.0 * alpha)), (float)std::log2(p));
     }
+    if (!ok) {
+#pragma omp critical
+      { if (bad_mol < 0 || m < bad_mol) bad_mol = m; }
+      continue;
+    }
     s->h_Z[m] = Z;
-    build_alias(n, v.data(), &s->h_thr[a0], &s->h_alias[a0]);
-    principal_frame(n, cd, v.data(), &s->h_frame[12 * (size_t)m]);
+    build_alias(n, v, &s->h_thr[a0], &s->h_alias[a0]);
+    principal_frame(n, cd, v, &s->h_frame[12 * (size_t)m]);
   }
-  std::vector<int32_t> order(n_mol);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+  if (bad_mol >= 0) {
+    set_error("shape_set_load: molecule %d has a non-finite or non-positive coordinate, radius or height", bad_mol);
+    delete s;
+    return SHP_EINVAL;
+  }
+  int32_t* order = reinterpret_cast<int32_t*>(hb + L.order);
+  std::iota(order, order + n_mol, 0);
+  std::stable_sort(order, order + n_mol, [&](int32_t a, int32_t b) {
     return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
   });
+  std::memcpy(hb + L.thr, s->h_thr.data(), sizeof(uint32_t) * n_atoms);
+  std::memcpy(hb + L.alias, s->h_alias.data(), n_atoms);
+  std::memcpy(hb + L.off, s->h_off.data(), sizeof(int32_t) * (n_mol + 1));
+  std::memcpy(hb + L.Z, s->h_Z.data(), sizeof(double) * n_mol);
+  std::memcpy(hb + L.frame, s->h_frame.data(), sizeof(float) * 12 * n_mol);
   cudaStream_t st = (cudaStream_t)stream;
-  int rc = SHP_OK;
-  if (!rc) rc = dev_upload(&s->atom, atom.data(), atom.size(), st);
-  if (!rc) rc = dev_upload(&s->aux, aux.data(), aux.size(), st);
-  if (!rc) rc = dev_upload(&s->thr, s->h_thr.data(), s->h_thr.size(), st);
-  if (!rc) rc = dev_upload(&s->alias, s->h_alias.data(), s->h_alias.size(), st);
-  if (!rc) rc = dev_upload(&s->off, s->h_off.data(), s->h_off.size(), st);
-  if (!rc) rc = dev_upload(&s->Z, s->h_Z.data(), s->h_Z.size(), st);
-  if (!rc) rc = dev_upload(&s->order, order.data(), order.size(), st);
-  if (!rc) rc = dev_upload(&s->frame, s->h_frame.data(), s->h_frame.size(), st);
-  if (!rc && n_atoms) rc = dev_upload(&s->radius, radius, (size_t)n_atoms, st);
-  if (!rc) {
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) rc = cuda_fail(e, "shape_set_load: cudaStreamSynchronize");
-  }
-  if (rc) {
+  unsigned char* db = nullptr;
+  cudaError_t e = cudaMalloc((void**)&db, L.total);
+  if (e != cudaSuccess) { delete s; return cuda_fail(e, "shape_set_load: cudaMalloc"); }
+  s->dbase = db;
+  s->atom = reinterpret_cast<float4*>(db + L.atom);
+  s->aux = reinterpret_cast<float2*>(db + L.aux);
+  s->radius = reinterpret_cast<float*>(db + L.radius);
+  s->thr = reinterpret_cast<uint32_t*>(db + L.thr);
+  s->alias = db + L.alias;
+  s->off = reinterpret_cast<int32_t*>(db + L.off);
+  s->Z = reinterpret_cast<double*>(db + L.Z);
+  s->order = reinterpret_cast<int32_t*>(db + L.order);
+  s->frame = reinterpret_cast<float*>(db + L.frame);
+  e = cudaMemcpyAsync(db, hb, L.total, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the staging buffer is reused by the next load
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "shape_set_load: upload");
     free_set_memory(s);
     delete s;
     return rc;
