@@ -130,14 +130,16 @@ __device__ __forceinline__ int pick(const WarpTables& T, int n, uint32_t x) {
 
 // m = sum g and q = prod (1 - g) over one molecule's Gaussians for SP
 // sample pairs (even sample in .x, odd in .y), and with kCV also
-// ut = sum om g. kForm 0: four scalar FMAs for the exponent; kForm 2: four
-// packed FP32x2 FMAs (two samples per instruction).
+// ut = sum om g. kForm 0: four scalar FMAs for the exponent; kForm 2, 3, 4:
+// four packed FP32x2 FMAs (two samples per instruction), with the atom loop
+// unrolled 2, 1 and 4 times.
 template <int SP, int kForm, bool kCV = false>
 __device__ __forceinline__ void eval_table(const CoefT* __restrict__ tab, int n, const float2 (&rx)[SP],
                                            const float2 (&ry)[SP], const float2 (&rz)[SP],
                                            const float2 (&rr)[SP], float2 (&m)[SP], float2 (&q)[SP],
                                            float2 (&ut)[SP]) {
-#pragma unroll 2
+  constexpr int kUnroll = kForm == 3 ? 1 : (kForm == 4 ? 4 : 2);
+#pragma unroll kUnroll
   for (int j = 0; j < n; ++j) {
     const float4 k0 = tab[j].ac, k1 = tab[j].bxy, k2 = tab[j].bzw;
 #pragma unroll
@@ -553,7 +555,8 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) self_kernel(const Sel
 struct Variant {
   int sp, form, warps, min_blocks;
 };
-constexpr Variant kVariants[] = {{4, 0, 8, 2}, {4, 2, 8, 2}, {4, 0, 4, 5}, {4, 2, 4, 5}, {8, 0, 4, 4}, {8, 2, 4, 4}};
+constexpr Variant kVariants[] = {{4, 0, 8, 2}, {4, 2, 8, 2}, {4, 0, 4, 5}, {4, 2, 4, 5}, {4, 3, 8, 2}, {4, 4, 8, 2},
+                                 {8, 0, 4, 4}, {8, 2, 4, 4}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <int V>
@@ -613,7 +616,9 @@ int launch_cross(int v, const CrossArgs& a, int64_t n_items, cudaStream_t st) {
     case 2: return launch_cross_v<MODE, 2>(a, n_items, st);
     case 3: return launch_cross_v<MODE, 3>(a, n_items, st);
     case 4: return launch_cross_v<MODE, 4>(a, n_items, st);
-    default: return launch_cross_v<MODE, 5>(a, n_items, st);
+    case 5: return launch_cross_v<MODE, 5>(a, n_items, st);
+    case 6: return launch_cross_v<MODE, 6>(a, n_items, st);
+    default: return launch_cross_v<MODE, 7>(a, n_items, st);
   }
 }
 
@@ -624,12 +629,14 @@ int launch_cross<kAdaptive>(int v, const CrossArgs& a, int64_t n_items, cudaStre
     case 0: return launch_cross_v<kAdaptive, 0>(a, n_items, st);
     case 1: return launch_cross_v<kAdaptive, 1>(a, n_items, st);
     case 2: return launch_cross_v<kAdaptive, 2>(a, n_items, st);
-    default: return launch_cross_v<kAdaptive, 3>(a, n_items, st);
+    case 3: return launch_cross_v<kAdaptive, 3>(a, n_items, st);
+    case 4: return launch_cross_v<kAdaptive, 4>(a, n_items, st);
+    default: return launch_cross_v<kAdaptive, 5>(a, n_items, st);
   }
 }
 
 int launch_self(const SelfArgs& a, int64_t n_items, cudaStream_t st) {
-  using Tr = VariantTraits<0>;
+  using Tr = VariantTraits<1>;  // packed exponent, 4 sample pairs per lane, 8 warps x 2 CTAs
   return launch_persistent(self_kernel<Tr::sp, Tr::form, Tr::warps, Tr::min_blocks>, a, n_items, Tr::warps,
                            Tr::smem, st);
 }
