@@ -202,6 +202,15 @@ int tanimoto_screen(shp_set Q, shp_set D, const shp_screen* cfg, const double* s
 int shp_screen_variants(void);
 
 /*
+ * Shape of launch variant v: info[0] sample pairs per lane per batch (the
+ * adaptive screen runs only the variants with 4), info[1] exponent/loop form,
+ * info[2] warps per CTA, info[3] CTAs per SM the register budget is set for.
+ * Returns SHP_ERANGE for v outside 0 .. shp_screen_variants()-1, SHP_EINVAL
+ * for a NULL info.
+ */
+int shp_screen_variant_info(int32_t v, int32_t info[4]);
+
+/*
  * Autotuner: times every launch variant valid for cfg (fixed or adaptive) on
  * n_sample pairs spread evenly over the screen (outputs go to the caller's
  * T/seT/n_used buffers), makes the fastest the default of this device for

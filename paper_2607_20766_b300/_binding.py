@@ -24,7 +24,7 @@ MAX_ATOMS = 64
 # Every entry point declared in include/shape.h.
 EXPORTS = ("shp_last_error", "shp_version", "shape_set_load", "shape_set_free", "shape_set_info",
            "shape_set_tables", "overlap_estimate", "union_volume_estimate", "fo_overlap",
-           "tanimoto_screen", "shp_screen_variants", "tanimoto_screen_tune", "align_crn_points",
+           "tanimoto_screen", "shp_screen_variants", "shp_screen_variant_info", "tanimoto_screen_tune", "align_crn_points",
            "overlap_pose_grad", "align_rigid", "shape_set_frames", "union_attributions", "union_volume_cv",
            "cv_features", "mlp_forward", "mlp_loss_grad", "mlp_adam", "mlp_loss_grad_noalloc")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 33, 64, 6401
@@ -76,6 +76,7 @@ def load_library():
         "fo_overlap": [_P, _P, _P, _P, ctypes.c_int64, _P, _P, _P],
         "tanimoto_screen": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
         "shp_screen_variants": [],
+        "shp_screen_variant_info": [ctypes.c_int32, _P],
         "tanimoto_screen_tune": [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int64, _P, _P, _P],
         "align_crn_points": [_P, ctypes.c_int32, _P, _P, _P],
         "overlap_pose_grad": [_P, ctypes.c_int32, _P, ctypes.c_uint32, _P, _P, ctypes.c_int64, _P, ctypes.c_uint32,
@@ -267,6 +268,14 @@ def tanimoto_screen(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: tor
 
 def screen_variants() -> int:
     return load_library().shp_screen_variants()
+
+
+def screen_variant_info(v: int) -> dict:
+    """Launch shape of screen variant v: sample pairs per lane (sp), loop
+    form, warps per CTA and CTAs per SM."""
+    info = (ctypes.c_int32 * 4)()
+    _check(load_library().shp_screen_variant_info(v, info))
+    return dict(sp=info[0], form=info[1], warps=info[2], ctas=info[3])
 
 
 def tanimoto_screen_tune(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: torch.Tensor, seed: int,

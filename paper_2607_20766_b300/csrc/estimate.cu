@@ -128,43 +128,65 @@ __device__ __forceinline__ int pick(const WarpTables& T, int n, uint32_t x) {
   return f < T.thr[j] ? (int)j : (int)T.alias[j];
 }
 
-// m = sum g and q = prod (1 - g) over one molecule's Gaussians for SP
-// sample pairs (even sample in .x, odd in .y), and with kCV also
-// ut = sum om g. kForm 0: four scalar FMAs for the exponent; kForm 2, 3, 4:
-// four packed FP32x2 FMAs (two samples per instruction), with the atom loop
-// unrolled 2, 1 and 4 times.
+// One atom's contribution to m = sum g, q = prod (1 - g) (and with kCV
+// ut = sum om g) for SP sample pairs (even sample in .x, odd in .y). kForm 0:
+// four scalar FMAs for the exponent; kForm >= 2: four packed FP32x2 FMAs
+// (two samples per instruction); kForm >= 5 also updates q with one packed
+// FMA per sample pair.
+template <int SP, int kForm, bool kCV>
+__device__ __forceinline__ void eval_atom(const float4 k0, const float4 k1, const float4 k2, const float2 (&rx)[SP],
+                                          const float2 (&ry)[SP], const float2 (&rz)[SP], const float2 (&rr)[SP],
+                                          float2 (&m)[SP], float2 (&q)[SP], float2 (&ut)[SP]) {
+#pragma unroll
+  for (int p = 0; p < SP; ++p) {
+    float2 g;
+    if (kForm == 0) {
+      const float ex = fmaf(k2.x, rz[p].x, fmaf(k1.z, ry[p].x, fmaf(k1.x, rx[p].x, fmaf(k0.x, rr[p].x, k0.z))));
+      const float ey = fmaf(k2.x, rz[p].y, fmaf(k1.z, ry[p].y, fmaf(k1.x, rx[p].y, fmaf(k0.x, rr[p].y, k0.z))));
+      g = make_float2(ex2_approx(ex), ex2_approx(ey));
+    } else {
+      float2 e = __ffma2_rn(make_float2(k0.x, k0.y), rr[p], make_float2(k0.z, k0.w));
+      e = __ffma2_rn(make_float2(k1.x, k1.y), rx[p], e);
+      e = __ffma2_rn(make_float2(k1.z, k1.w), ry[p], e);
+      e = __ffma2_rn(make_float2(k2.x, k2.y), rz[p], e);
+      g = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+    }
+    m[p] = __fadd2_rn(m[p], g);
+    if (kForm >= 5) {
+      q[p] = __ffma2_rn(make_float2(-g.x, -g.y), q[p], q[p]);
+    } else {
+      q[p].x = fmaf(-g.x, q[p].x, q[p].x);
+      q[p].y = fmaf(-g.y, q[p].y, q[p].y);
+    }
+    if (kCV) {
+      ut[p].x = fmaf(k2.z, g.x, ut[p].x);
+      ut[p].y = fmaf(k2.z, g.y, ut[p].y);
+    }
+  }
+}
+
+// m, q (and ut) over one molecule's n >= 1 Gaussians. The atom loop is
+// unrolled 2 (forms 0, 2, 6), 1 (forms 3, 5, 7) or 4 (form 4) times; form 7
+// loads the next atom's coefficients before evaluating the current one.
 template <int SP, int kForm, bool kCV = false>
 __device__ __forceinline__ void eval_table(const CoefT* __restrict__ tab, int n, const float2 (&rx)[SP],
                                            const float2 (&ry)[SP], const float2 (&rz)[SP],
                                            const float2 (&rr)[SP], float2 (&m)[SP], float2 (&q)[SP],
                                            float2 (&ut)[SP]) {
-  constexpr int kUnroll = kForm == 3 ? 1 : (kForm == 4 ? 4 : 2);
-#pragma unroll kUnroll
-  for (int j = 0; j < n; ++j) {
-    const float4 k0 = tab[j].ac, k1 = tab[j].bxy, k2 = tab[j].bzw;
-#pragma unroll
-    for (int p = 0; p < SP; ++p) {
-      float2 g;
-      if (kForm == 0) {
-        const float ex = fmaf(k2.x, rz[p].x, fmaf(k1.z, ry[p].x, fmaf(k1.x, rx[p].x, fmaf(k0.x, rr[p].x, k0.z))));
-        const float ey = fmaf(k2.x, rz[p].y, fmaf(k1.z, ry[p].y, fmaf(k1.x, rx[p].y, fmaf(k0.x, rr[p].y, k0.z))));
-        g = make_float2(ex2_approx(ex), ex2_approx(ey));
-      } else {
-        float2 e = __ffma2_rn(make_float2(k0.x, k0.y), rr[p], make_float2(k0.z, k0.w));
-        e = __ffma2_rn(make_float2(k1.x, k1.y), rx[p], e);
-        e = __ffma2_rn(make_float2(k1.z, k1.w), ry[p], e);
-        e = __ffma2_rn(make_float2(k2.x, k2.y), rz[p], e);
-        g = make_float2(ex2_approx(e.x), ex2_approx(e.y));
-      }
-      m[p] = __fadd2_rn(m[p], g);
-      q[p].x = fmaf(-g.x, q[p].x, q[p].x);
-      q[p].y = fmaf(-g.y, q[p].y, q[p].y);
-      if (kCV) {
-        ut[p].x = fmaf(k2.z, g.x, ut[p].x);
-        ut[p].y = fmaf(k2.z, g.y, ut[p].y);
-      }
+  if (kForm == 7) {
+    float4 k0 = tab[0].ac, k1 = tab[0].bxy, k2 = tab[0].bzw;
+#pragma unroll 1
+    for (int j = 0; j < n; ++j) {
+      const int jn = j + 1 < n ? j + 1 : j;  // stays inside the staged table
+      const float4 n0 = tab[jn].ac, n1 = tab[jn].bxy, n2 = tab[jn].bzw;
+      eval_atom<SP, kForm, kCV>(k0, k1, k2, rx, ry, rz, rr, m, q, ut);
+      k0 = n0; k1 = n1; k2 = n2;
     }
+    return;
   }
+  constexpr int kUnroll = (kForm == 3 || kForm == 5) ? 1 : (kForm == 4 ? 4 : 2);
+#pragma unroll kUnroll
+  for (int j = 0; j < n; ++j) eval_atom<SP, kForm, kCV>(tab[j].ac, tab[j].bxy, tab[j].bzw, rx, ry, rz, rr, m, q, ut);
 }
 
 __device__ __forceinline__ void dir_init(DirState& s) {
@@ -555,8 +577,9 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) self_kernel(const Sel
 struct Variant {
   int sp, form, warps, min_blocks;
 };
-constexpr Variant kVariants[] = {{4, 0, 8, 2}, {4, 2, 8, 2}, {4, 0, 4, 5}, {4, 2, 4, 5}, {4, 3, 8, 2}, {4, 4, 8, 2},
-                                 {8, 0, 4, 4}, {8, 2, 4, 4}};
+constexpr Variant kVariants[] = {{4, 0, 8, 2}, {4, 2, 8, 2}, {4, 0, 4, 5}, {4, 2, 4, 5}, {4, 3, 8, 2},
+                                 {4, 4, 8, 2}, {8, 0, 4, 4}, {8, 2, 4, 4}, {4, 5, 8, 2}, {4, 6, 8, 2},
+                                 {4, 7, 8, 2}, {4, 5, 4, 5}, {2, 5, 4, 5}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <int V>
@@ -604,34 +627,21 @@ int launch_persistent(Kernel k, Args args, int64_t n_items, int warps, size_t sm
 template <int MODE, int V>
 int launch_cross_v(const CrossArgs& a, int64_t n_items, cudaStream_t st) {
   using Tr = VariantTraits<V>;
-  return launch_persistent(cross_kernel<MODE, Tr::sp, Tr::form, Tr::warps, Tr::min_blocks>, a, n_items, Tr::warps,
-                           Tr::smem, st);
-}
-
-template <int MODE>
-int launch_cross(int v, const CrossArgs& a, int64_t n_items, cudaStream_t st) {
-  switch (v) {
-    case 0: return launch_cross_v<MODE, 0>(a, n_items, st);
-    case 1: return launch_cross_v<MODE, 1>(a, n_items, st);
-    case 2: return launch_cross_v<MODE, 2>(a, n_items, st);
-    case 3: return launch_cross_v<MODE, 3>(a, n_items, st);
-    case 4: return launch_cross_v<MODE, 4>(a, n_items, st);
-    case 5: return launch_cross_v<MODE, 5>(a, n_items, st);
-    case 6: return launch_cross_v<MODE, 6>(a, n_items, st);
-    default: return launch_cross_v<MODE, 7>(a, n_items, st);
+  if constexpr (MODE == kAdaptive && Tr::sp != 4) {
+    set_error("adaptive screen: launch variant %d does not run rounds of 256 samples", V);
+    return SHP_EINVAL;
+  } else {
+    return launch_persistent(cross_kernel<MODE, Tr::sp, Tr::form, Tr::warps, Tr::min_blocks>, a, n_items, Tr::warps,
+                             Tr::smem, st);
   }
 }
 
-// The adaptive mode needs rounds of whole batches: SP 4 only.
-template <>
-int launch_cross<kAdaptive>(int v, const CrossArgs& a, int64_t n_items, cudaStream_t st) {
-  switch (v) {
-    case 0: return launch_cross_v<kAdaptive, 0>(a, n_items, st);
-    case 1: return launch_cross_v<kAdaptive, 1>(a, n_items, st);
-    case 2: return launch_cross_v<kAdaptive, 2>(a, n_items, st);
-    case 3: return launch_cross_v<kAdaptive, 3>(a, n_items, st);
-    case 4: return launch_cross_v<kAdaptive, 4>(a, n_items, st);
-    default: return launch_cross_v<kAdaptive, 5>(a, n_items, st);
+template <int MODE, int V = 0>
+int launch_cross(int v, const CrossArgs& a, int64_t n_items, cudaStream_t st) {
+  if constexpr (V + 1 < kNumVariants) {
+    return v == V ? launch_cross_v<MODE, V>(a, n_items, st) : launch_cross<MODE, V + 1>(v, a, n_items, st);
+  } else {
+    return launch_cross_v<MODE, V>(a, n_items, st);
   }
 }
 
@@ -815,6 +825,17 @@ extern "C" int tanimoto_screen(shp_set Q, shp_set D, const shp_screen* cfg, cons
 }
 
 extern "C" int shp_screen_variants(void) { return kNumVariants; }
+
+extern "C" int shp_screen_variant_info(int32_t v, int32_t info[4]) {
+  clear_error();
+  if (!info) { set_error("shp_screen_variant_info: NULL info"); return SHP_EINVAL; }
+  if (v < 0 || v >= kNumVariants) { set_error("shp_screen_variant_info: no variant %d", v); return SHP_ERANGE; }
+  info[0] = kVariants[v].sp;
+  info[1] = kVariants[v].form;
+  info[2] = kVariants[v].warps;
+  info[3] = kVariants[v].min_blocks;
+  return SHP_OK;
+}
 
 extern "C" int tanimoto_screen_tune(shp_set Q, shp_set D, const shp_screen* cfg, const double* self_q,
                                     const double* self_db, float* T, float* seT, uint32_t* n_used, int64_t n_sample,

@@ -113,13 +113,17 @@ def test_variants_agree(small_screen):
     for v in range(1, nv):
         r = shp.tanimoto_screen(Sq, Sd, tq, td, seed=4, n_fixed=1000, variant=v, with_overlaps=True)
         assert_close(r["O"].cpu().numpy(), ref["O"].cpu().numpy(), rtol=2e-6, what=f"variant {v}")
-    ada = [shp.tanimoto_screen(Sq, Sd, tq, td, seed=4, tau=0.015, min_n=512, cap=4096, variant=v, with_overlaps=True)
-           for v in range(6)]
-    for v in range(1, 6):
-        np.testing.assert_array_equal(ada[v]["n_used"].cpu().numpy(), ada[0]["n_used"].cpu().numpy())
-        assert_close(ada[v]["O"].cpu().numpy(), ada[0]["O"].cpu().numpy(), rtol=2e-6, what=f"adaptive variant {v}")
+    sp4 = [v for v in range(nv) if shp.screen_variant_info(v)["sp"] == 4]
+    ada = {v: shp.tanimoto_screen(Sq, Sd, tq, td, seed=4, tau=0.015, min_n=512, cap=4096, variant=v,
+                                  with_overlaps=True) for v in sp4}
+    for v in sp4[1:]:
+        np.testing.assert_array_equal(ada[v]["n_used"].cpu().numpy(), ada[sp4[0]]["n_used"].cpu().numpy())
+        assert_close(ada[v]["O"].cpu().numpy(), ada[sp4[0]]["O"].cpu().numpy(), rtol=2e-6,
+                     what=f"adaptive variant {v}")
+    other = [v for v in range(nv) if v not in sp4]
+    assert other, "no variant with another batch width"
     with pytest.raises(shp.ShapeError):
-        shp.tanimoto_screen(Sq, Sd, tq, td, seed=4, tau=0.015, variant=7)  # SP 8 cannot run rounds of 256
+        shp.tanimoto_screen(Sq, Sd, tq, td, seed=4, tau=0.015, variant=other[0])  # cannot run rounds of 256
 
 
 def test_tuner_picks_a_valid_variant(small_screen):
@@ -129,7 +133,8 @@ def test_tuner_picks_a_valid_variant(small_screen):
     assert 0 <= best < shp.screen_variants()
     assert times[best] > 0 and np.all(times[times > 0] >= times[best])
     best_a, times_a = shp.tanimoto_screen_tune(Sq, Sd, torch.tensor(sq), torch.tensor(sd), seed=1, n_sample=64)
-    assert 0 <= best_a < 6 and np.all(times_a[6:] == -1)
+    sp4 = np.array([shp.screen_variant_info(v)["sp"] == 4 for v in range(shp.screen_variants())])
+    assert sp4[best_a] and np.all(times_a[~sp4] == -1) and np.all(times_a[sp4] > 0)
 
 
 def test_adaptive_full_size_sampled():
