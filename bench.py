@@ -244,13 +244,19 @@ def main():
     tuned, tune_ms = shp.tanimoto_screen_tune(Sq, Sd, selfq0, selfd0, seed=SEED_WORKLOAD, n_fixed=n,
                                               n_sample=min(8192, q.n_mol * d.n_mol))
 
+    # the step as two CUDA graphs (self-overlaps of both sets; the screen), so
+    # the screen kernel can be timed on its own between the replays
+    g_self = shp.StepGraph(lambda: (shp.self_overlaps(Sq, seed=1, n_samples=n, stream_base=0),
+                                    shp.self_overlaps(Sd, seed=1, n_samples=n, stream_base=1)))
+    selfq, selfd = g_self.replay()
+    g_screen = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, selfq, selfd, seed=SEED_WORKLOAD, n_fixed=n)
+
     def step():
-        selfq = shp.self_overlaps(Sq, seed=1, n_samples=n, stream_base=0)
-        selfd = shp.self_overlaps(Sd, seed=1, n_samples=n, stream_base=1)
+        g_self.replay()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        res = shp.tanimoto_screen(Sq, Sd, selfq, selfd, seed=SEED_WORKLOAD, n_fixed=n)
+        res = g_screen.replay()
         e1.record(stream)
         return res, (e0, e1)
 
@@ -328,6 +334,7 @@ def main():
                                    f"{n} samples per direction per pair, first-order + union Tanimoto with "
                                    f"self-overlaps",
                        "global_batch": n_pairs * world, "l2": "flushed between timed steps (512 MB write)",
+                       "launch": "per step two CUDA graph replays: self-overlaps of both sets, then the screen",
                        "parallelism": f"dp{world} (database shards, no collective)"},
             "pairs_per_s": pairs_per_s,
             "evals_per_step": evals_rank,
@@ -369,17 +376,23 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
     q, d = synth.adaptive_screen(n_q=16, n_db=n_db, seed=4242 + 7919 * rank)
     Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
     stream = torch.cuda.current_stream()
+    # self-overlaps and the adaptive screen, each captured as a CUDA graph
+    g_self = shp.StepGraph(lambda: (shp.self_overlaps(Sq, seed=11, n_samples=4096, stream_base=0),
+                                    shp.self_overlaps(Sd, seed=11, n_samples=4096, stream_base=16)))
+    selfq, selfd = g_self.replay()
+    best, times = shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=16384, tau=tau, cap=cap)
+    g_ad = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, selfq, selfd, seed=77, tau=tau, round=256, min_n=1024,
+                         cap=cap)
+    torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    selfq = shp.self_overlaps(Sq, seed=11, n_samples=4096, stream_base=0)
-    selfd = shp.self_overlaps(Sd, seed=11, n_samples=4096, stream_base=16)
+    g_self.replay()
     t1.record(stream)
-    best, times = shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=16384, tau=tau, cap=cap)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    res = shp.tanimoto_screen(Sq, Sd, selfq, selfd, seed=77, tau=tau, round=256, min_n=1024, cap=cap)
+    res = g_ad.replay()
     e1.record(stream)
     torch.cuda.synchronize()
     t_self = t0.elapsed_time(t1) / 1e3
@@ -411,6 +424,7 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
     return {
         "workload": f"adaptive screen: 16 queries (20-48 atoms) x {n_db} molecules (18-60, heavy-tailed toward 40), "
                     f"rounds of 256 per direction, SE(T_union) <= {tau} or {cap} per direction",
+        "launch": "CUDA graph replay (self-overlaps graph, then the persistent adaptive screen graph)",
         "pairs": npairs, "pairs_per_s": npairs / t_ad, "evals_per_s": evals / t_ad, "seconds": t_ad,
         "self_overlap_seconds": t_self,
         "mean_samples_per_direction": float(nu.mean()), "median_samples_per_direction": float(np.median(nu)),

@@ -12,6 +12,7 @@ from ._binding import (ANTITHETIC, EXPORTS, LIB_PATH, MAX_ATOMS, OBJ_FO, OBJ_FO_
                        screen_variant_info, screen_variants, self_overlaps, shape_set_load, tanimoto_screen, tanimoto_screen_tune,
                        union_volume_estimate, union_attributions, union_volume_cv, cv_features, mlp_forward,
                        mlp_loss_grad, mlp_adam, MLP_PARAMS)
+from .graph import StepGraph
 
 __all__ = ["ANTITHETIC", "EXPORTS", "LIB_PATH", "MAX_ATOMS", "OBJ_FO", "OBJ_FO_CLOSED", "OBJ_UNION", "SYMMETRIC",
            "TAG_AB", "TAG_BA",
@@ -19,4 +20,4 @@ __all__ = ["ANTITHETIC", "EXPORTS", "LIB_PATH", "MAX_ATOMS", "OBJ_FO", "OBJ_FO_C
            "ShapeError", "ShapeSet", "fo_overlap", "load_library", "overlap_estimate", "screen_config",
            "screen_variant_info", "screen_variants", "self_overlaps", "shape_set_load", "tanimoto_screen", "tanimoto_screen_tune",
            "union_volume_estimate", "union_attributions", "union_volume_cv", "cv_features", "mlp_forward",
-           "mlp_loss_grad", "mlp_adam", "MLP_PARAMS"]
+           "mlp_loss_grad", "mlp_adam", "MLP_PARAMS", "StepGraph"]

@@ -161,3 +161,28 @@ def test_adaptive_full_size_sampled():
     sd[ds, 0] = O.fo_overlap(d, ds, d, ds)
     sd[ds, 1] = [O.union_volume_estimate(d, [k], seed=11, n=4096, stream_base=16 + int(k))[2][0] for k in ds]
     check_adaptive_against_oracle(q, d, res, sq, sd, 77, 0.005, 256, 1024, 65536, pairs, d.n_mol)
+
+
+def test_graph_captured_adaptive_step_matches_eager(small_screen):
+    """The adaptive step (self-overlaps of both sets + the adaptive screen)
+    captured as one CUDA graph: every replay reproduces the eager call bit for
+    bit, and the replayed estimates pass the oracle's checks."""
+    q, d, Sq, Sd, sq, sd = small_screen
+
+    def step():
+        selfq = shp.self_overlaps(Sq, seed=1, n_samples=8192)
+        selfd = shp.self_overlaps(Sd, seed=2, n_samples=8192)
+        return selfq, selfd, shp.tanimoto_screen(Sq, Sd, selfq, selfd, seed=5, tau=0.012, round=256, min_n=512,
+                                                 cap=6144, with_overlaps=True, stream_base=3)
+
+    eager = step()
+    g = shp.StepGraph(step)
+    for _ in range(2):
+        selfq, selfd, res = g.replay()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(selfq.cpu().numpy(), eager[0].cpu().numpy())
+        np.testing.assert_array_equal(selfd.cpu().numpy(), eager[1].cpu().numpy())
+        for k in ("T", "seT", "O", "seO", "n_used"):
+            np.testing.assert_array_equal(res[k].cpu().numpy(), eager[2][k].cpu().numpy())
+    pairs = np.arange(q.n_mol * d.n_mol)
+    check_adaptive_against_oracle(q, d, res, sq, sd, 5, 0.012, 256, 512, 6144, pairs, d.n_mol, stream_base=3)
