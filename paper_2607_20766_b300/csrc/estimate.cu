@@ -121,11 +121,12 @@ __device__ __noinline__ void stage_direction(WarpTables& T, const SetView& SX, M
   __syncwarp();
 }
 
-// Alias pick: column j = hi32(x n); keep j if lo32(x n) < thr_j.
-__device__ __forceinline__ int pick(const WarpTables& T, int n, uint32_t x) {
+// Alias pick: column j = hi32(x n); keep j if lo32(x n) < thr_j. The alias
+// is masked to the table size, a no-op for a staged table (alias < n <= 64).
+__device__ __forceinline__ int pick(const uint32_t* thr, const uint8_t* alias, int n, uint32_t x) {
   const unsigned long long prod = (unsigned long long)x * (unsigned)n;
   const uint32_t j = (uint32_t)(prod >> 32), f = (uint32_t)prod;
-  return f < T.thr[j] ? (int)j : (int)T.alias[j];
+  return f < thr[j] ? (int)j : (int)(alias[j] & (SHP_MAX_ATOMS - 1));
 }
 
 // One atom's contribution to m = sum g, q = prod (1 - g) (and with kCV
@@ -195,19 +196,16 @@ __device__ __forceinline__ void dir_init(DirState& s) {
   s.K[0] = s.K[1] = 0.f;
 }
 
-// Sample pairs [b * 32 SP, (b + 1) * 32 SP) of one direction (P sample pairs
-// in total, n samples): draw, evaluate and accumulate. Values:
-//   cross: fa = m_Y (first order), fb = (u_X / m_X) u_Y (union)
-//   self:  fa = u_X / m_X (volume), fb = u_X^2 / m_X (self-overlap)
-// With antithetic pairs the unit is the mean of a sample and its
-// reflection. The first batch sets the shifts from sample 0.
-template <bool kSelf, int SP, int kForm, bool kCV = false>
-__device__ __forceinline__ void run_batch(WarpTables& T, int nx, int ny, uint32_t b, uint32_t n, Key key,
-                                          uint32_t slo, uint32_t shi, uint32_t tag, bool anti, int lane,
-                                          DirState& st) {
-  const uint32_t P = (n + 1u) >> 1;
+// Draws sample pairs [b * 32 SP, (b + 1) * 32 SP) of one direction from the
+// sampled molecule's component table (centres relative to the frame origin,
+// sigma, alias): pair s = base + 32 p + lane of this lane goes to slot p,
+// even sample in .x, odd sample (or the reflection) in .y; rr = |r|^2.
+template <int SP>
+__device__ __forceinline__ void draw_batch(const float4* __restrict__ samp, const uint32_t* thr, const uint8_t* alias,
+                                           int nx, uint32_t b, Key key, uint32_t slo, uint32_t shi, uint32_t tag,
+                                           bool anti, int lane, float2 (&rx)[SP], float2 (&ry)[SP],
+                                           float2 (&rz)[SP], float2 (&rr)[SP]) {
   const uint32_t base = b * 32u * SP;
-  float2 rx[SP], ry[SP], rz[SP], rr[SP];
 #pragma unroll
   for (int p = 0; p < SP; ++p) {
     const uint32_t s = base + (uint32_t)p * 32u + (uint32_t)lane;
@@ -217,13 +215,13 @@ __device__ __forceinline__ void run_batch(WarpTables& T, int nx, int ny, uint32_
     box_muller(w0.z, w0.w, n0, n1);
     box_muller(w1.x, w1.y, n2, n3);
     box_muller(w1.z, w1.w, n4, n5);
-    const float4 c0 = T.samp[pick(T, nx, w0.x)];
+    const float4 c0 = samp[pick(thr, alias, nx, w0.x)];
     const float ax = fmaf(c0.w, n0, c0.x), ay = fmaf(c0.w, n1, c0.y), az = fmaf(c0.w, n4, c0.z);
     float bx, by, bz;
     if (anti) {
       bx = fmaf(-c0.w, n0, c0.x); by = fmaf(-c0.w, n1, c0.y); bz = fmaf(-c0.w, n4, c0.z);
     } else {
-      const float4 c1 = T.samp[pick(T, nx, w0.y)];
+      const float4 c1 = samp[pick(thr, alias, nx, w0.y)];
       bx = fmaf(c1.w, n2, c1.x); by = fmaf(c1.w, n3, c1.y); bz = fmaf(c1.w, n5, c1.z);
     }
     rx[p] = make_float2(ax, bx);
@@ -231,6 +229,21 @@ __device__ __forceinline__ void run_batch(WarpTables& T, int nx, int ny, uint32_
     rz[p] = make_float2(az, bz);
     rr[p] = make_float2(fmaf(ax, ax, fmaf(ay, ay, az * az)), fmaf(bx, bx, fmaf(by, by, bz * bz)));
   }
+}
+
+// Evaluates and accumulates one batch of drawn sample pairs (P sample pairs
+// in total, n samples). Values:
+//   cross: fa = m_Y (first order), fb = (u_X / m_X) u_Y (union)
+//   self:  fa = u_X / m_X (volume), fb = u_X^2 / m_X (self-overlap)
+// With antithetic pairs the unit is the mean of a sample and its
+// reflection. The first batch sets the shifts from sample 0.
+template <bool kSelf, int SP, int kForm, bool kCV = false>
+__device__ __forceinline__ void eval_batch(const CoefT* __restrict__ tx, const CoefT* __restrict__ ty, int nx,
+                                           int ny, uint32_t b, uint32_t n, bool anti, int lane, DirState& st,
+                                           const float2 (&rx)[SP], const float2 (&ry)[SP], const float2 (&rz)[SP],
+                                           const float2 (&rr)[SP]) {
+  const uint32_t P = (n + 1u) >> 1;
+  const uint32_t base = b * 32u * SP;
   float2 m[SP], q[SP], ut[SP], fa[SP], fb[SP];
 #pragma unroll
   for (int p = 0; p < SP; ++p) {
@@ -238,7 +251,7 @@ __device__ __forceinline__ void run_batch(WarpTables& T, int nx, int ny, uint32_
     q[p] = make_float2(1.f, 1.f);
     ut[p] = make_float2(0.f, 0.f);
   }
-  eval_table<SP, kForm, kCV>(T.x, nx, rx, ry, rz, rr, m, q, ut);
+  eval_table<SP, kForm, kCV>(tx, nx, rx, ry, rz, rr, m, q, ut);
   if (kSelf) {
     // volume: fa = u/m (or (u - ut)/m with the control variate), fb = u^2/m
 #pragma unroll
@@ -256,7 +269,7 @@ __device__ __forceinline__ void run_batch(WarpTables& T, int nx, int ny, uint32_
       m[p] = make_float2(0.f, 0.f);
       q[p] = make_float2(1.f, 1.f);
     }
-    eval_table<SP, kForm, false>(T.y, ny, rx, ry, rz, rr, m, q, ut);
+    eval_table<SP, kForm, false>(ty, ny, rx, ry, rz, rr, m, q, ut);
 #pragma unroll
     for (int p = 0; p < SP; ++p) {
       fa[p] = m[p];
@@ -292,6 +305,16 @@ __device__ __forceinline__ void run_batch(WarpTables& T, int nx, int ny, uint32_
   }
 #pragma unroll
   for (int t = 0; t < 4; ++t) acc2(st.hi[t], st.lo[t], acc[t]);
+}
+
+// One batch of one direction (draw, evaluate, accumulate) by a single warp.
+template <bool kSelf, int SP, int kForm, bool kCV = false>
+__device__ __forceinline__ void run_batch(WarpTables& T, int nx, int ny, uint32_t b, uint32_t n, Key key,
+                                          uint32_t slo, uint32_t shi, uint32_t tag, bool anti, int lane,
+                                          DirState& st) {
+  float2 rx[SP], ry[SP], rz[SP], rr[SP];
+  draw_batch<SP>(T.samp, T.thr, T.alias, nx, b, key, slo, shi, tag, anti, lane, rx, ry, rz, rr);
+  eval_batch<kSelf, SP, kForm, kCV>(T.x, T.y, nx, ny, b, n, anti, lane, st, rx, ry, rz, rr);
 }
 
 // Compensated FP32 warp sum of hi + lo; lane 0's (hi, lo) carries the total.
@@ -400,16 +423,16 @@ __device__ void pair_epilogue(const CrossArgs& args, int32_t xa, int32_t xb, int
 // FP32 SE(T) of the watched slot from the running sums (adaptive stop rule).
 __device__ __forceinline__ float watched_se_t(const CrossArgs& args, const DirState& sa, const DirState& sb, int32_t xa,
                                               int32_t xb, float n) {
-  const int t = 2 * args.watch;
-  float h[4] = {sa.hi[t], sa.hi[t + 1], sb.hi[t], sb.hi[t + 1]};
-  float l[4] = {sa.lo[t], sa.lo[t + 1], sb.lo[t], sb.lo[t + 1]};
+  const bool w = args.watch != 0;
+  float h[4] = {w ? sa.hi[2] : sa.hi[0], w ? sa.hi[3] : sa.hi[1], w ? sb.hi[2] : sb.hi[0], w ? sb.hi[3] : sb.hi[1]};
+  float l[4] = {w ? sa.lo[2] : sa.lo[0], w ? sa.lo[3] : sa.lo[1], w ? sb.lo[2] : sb.lo[0], w ? sb.lo[3] : sb.lo[1]};
 #pragma unroll
   for (int i = 0; i < 4; ++i) warp_sum2(h[i], l[i]);
   const float ZA = (float)args.A.Z[xa], ZB = (float)args.B.Z[xb];
   const float s1a = h[0] + l[0], s2a = h[1] + l[1], s1b = h[2] + l[2], s2b = h[3] + l[3];
   const float va = fmaxf((s2a - s1a * s1a / n) / (n - 1.f), 0.f);
   const float vb = fmaxf((s2b - s1b * s1b / n) / (n - 1.f), 0.f);
-  const float ea = ZA * (sa.K[args.watch] + s1a / n), eb = ZB * (sb.K[args.watch] + s1b / n);
+  const float ea = ZA * ((w ? sa.K[1] : sa.K[0]) + s1a / n), eb = ZB * ((w ? sb.K[1] : sb.K[0]) + s1b / n);
   const float O = 0.5f * (ea + eb);
   const float seO = 0.5f * sqrtf((ZA * ZA * va + ZB * ZB * vb) / n);
   const float S = (float)(args.self_q[2 * (int64_t)xa + args.watch] + args.self_db[2 * (int64_t)xb + args.watch]);
@@ -596,17 +619,20 @@ int sm_count(int* sms) {
   return SHP_OK;
 }
 
+// Persistent launch: as many CTAs as fit on the GPU (at most one per
+// `items_per_cta` items), each of `threads` threads, pulling items from a
+// zeroed device queue counter (stream-ordered scratch unless given).
 template <class Kernel, class Args>
-int launch_persistent(Kernel k, Args args, int64_t n_items, int warps, size_t smem, cudaStream_t st,
-                      unsigned long long* queue_in = nullptr) {
+int launch_persistent(Kernel k, Args args, int64_t n_items, int items_per_cta, int threads, size_t smem,
+                      cudaStream_t st, unsigned long long* queue_in = nullptr) {
   int sms = 0;
   int rc = sm_count(&sms);
   if (rc) return rc;
   SHP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  SHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, warps * 32, smem));
+  SHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem));
   if (per_sm < 1) per_sm = 1;
-  const int64_t need = (n_items + warps - 1) / warps;
+  const int64_t need = (n_items + items_per_cta - 1) / items_per_cta;
   int64_t g = (int64_t)sms * per_sm;
   if (need < g) g = need;
   const int grid = (int)(g < 1 ? 1 : g);
@@ -615,13 +641,19 @@ int launch_persistent(Kernel k, Args args, int64_t n_items, int warps, size_t sm
   cudaError_t e = cudaMemsetAsync(q, 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess) {
     args.queue = q;
-    k<<<grid, warps * 32, smem, st>>>(args);
+    k<<<grid, threads, smem, st>>>(args);
     e = cudaGetLastError();
   }
   cudaError_t e2 = queue_in ? cudaSuccess : cudaFreeAsync(q, st);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
   return SHP_OK;
+}
+
+template <class Kernel, class Args>
+int launch_persistent(Kernel k, Args args, int64_t n_items, int warps, size_t smem, cudaStream_t st,
+                      unsigned long long* queue_in = nullptr) {
+  return launch_persistent(k, args, n_items, warps, warps * 32, smem, st, queue_in);
 }
 
 template <int MODE, int V>
