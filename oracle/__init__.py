@@ -68,7 +68,7 @@ _SIGS = {
     "orc_grid": [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_double, ctypes.c_double, _P,
                  ctypes.c_int],
     "orc_tanimoto_pairs": [_P, _P, _P, _P, _P, ctypes.c_int64, _P, _P, ctypes.c_uint64,
-                           ctypes.c_uint32, ctypes.c_uint32, _P, _P, _P, _P, ctypes.c_int],
+                           ctypes.c_uint32, ctypes.c_uint32, _P, _P, _P, _P, _P, _P, ctypes.c_int],
     "orc_crn_points": [_P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P],
     "orc_pose_objective": [ctypes.c_double, _P, ctypes.c_uint32, _P, ctypes.c_int32, _P, ctypes.c_int, _P],
     "orc_pose_grad_fd": [ctypes.c_double, _P, ctypes.c_uint32, _P, ctypes.c_int32, _P, ctypes.c_int,
@@ -274,10 +274,15 @@ def grid(A, ia, B=None, ib=0, h=0.1, pad=6.5, poseB=None, n_threads=0, c_alpha=2
 
 
 def tanimoto_pairs(Q, iq, D, idd, stream_ids, selfQ, selfD, seed, n, flags=0, n_threads=0,
-                   c_alpha=2.41798793):
+                   c_alpha=2.41798793, omega_q=None, omega_d=None):
     """Fixed-budget symmetric screen of explicit pairs. Returns dict of
-    [n_pairs, 2] arrays O, seO, T, seT (slot 0 first order, slot 1 union)."""
+    [n_pairs, 2] arrays O, seO, T, seT (slot 0 first order, slot 1 union).
+    omega_q/omega_d (per set atom): control-variate weights of the union slot."""
     sq, sd = _oset(Q, c_alpha), _oset(D, c_alpha)
+    if (omega_q is None) != (omega_d is None):
+        raise ValueError("give both omega_q and omega_d or neither")
+    wq = None if omega_q is None else np.ascontiguousarray(omega_q, dtype=np.float64)
+    wd = None if omega_d is None else np.ascontiguousarray(omega_d, dtype=np.float64)
     iq = np.ascontiguousarray(iq, dtype=np.int32)
     idd = np.ascontiguousarray(idd, dtype=np.int32)
     st = np.ascontiguousarray(stream_ids, dtype=np.uint64)
@@ -286,8 +291,8 @@ def tanimoto_pairs(Q, iq, D, idd, stream_ids, selfQ, selfD, seed, n, flags=0, n_
     k = len(iq)
     O, sO, T, sT = (np.empty((k, 2)) for _ in range(4))
     _check(lib().orc_tanimoto_pairs(sq.ref, iq.ctypes.data, sd.ref, idd.ctypes.data, st.ctypes.data, k,
-                                    selfQ.ctypes.data, selfD.ctypes.data, seed, n, flags, O.ctypes.data,
-                                    sO.ctypes.data, T.ctypes.data, sT.ctypes.data, n_threads),
+                                    selfQ.ctypes.data, selfD.ctypes.data, seed, n, flags, _ptr(wq), _ptr(wd),
+                                    O.ctypes.data, sO.ctypes.data, T.ctypes.data, sT.ctypes.data, n_threads),
            "tanimoto_pairs")
     return dict(O=O, seO=sO, T=T, seT=sT)
 

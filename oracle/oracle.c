@@ -299,8 +299,25 @@ int orc_occupancy(const orc_set* S, int32_t idx, const float* pose, int64_t n, c
 /* sums = {sum f_FO, sum f_FO^2, sum f_U, sum f_U^2}, unit count n_eff   */
 /* ------------------------------------------------------------------ */
 
+/* u~(r) = sum_i w_i g_i(r), the weighted-Gaussian control variate of u. */
+static double weighted_sum(const orc_mol* m, const double* w, const double r[3]) {
+  double s = 0.0;
+  for (int i = 0; i < m->n; ++i) {
+    double dx = r[0] - m->c[i][0], dy = r[1] - m->c[i][1], dz = r[2] - m->c[i][2];
+    s += w[i] * m->p[i] * exp(-m->alpha[i] * (dx * dx + dy * dy + dz * dz));
+  }
+  return s;
+}
+
+/*
+ * wx, wy: per-atom control-variate weights of X and Y, or NULL. With them
+ * the union value is the residual (u_X u_Y - u~_X u~_Y) / m_X, whose
+ * expectation is the union overlap minus the closed form of
+ * integral u~_X u~_Y.
+ */
 static void sums_cross(const orc_mol* X, const orc_mol* Y, uint64_t seed, uint64_t stream,
-                       uint32_t tag, uint32_t n, int antithetic, double sums[4], double* n_eff) {
+                       uint32_t tag, uint32_t n, int antithetic, const double* wx, const double* wy,
+                       double sums[4], double* n_eff) {
   double s[4] = {0, 0, 0, 0};
   for (uint32_t k = 0; k < n; k += 2) {
     double r[2][3];
@@ -313,7 +330,10 @@ static void sums_cross(const orc_mol* X, const orc_mol* Y, uint64_t seed, uint64
       occupancy(X, r[j], &mx, &ux);
       occupancy(Y, r[j], &my, &uy);
       ffo[j] = my;                 /* first order: f = m_Y        */
-      fu[j] = (ux / mx) * uy;      /* union: f = w_X u_Y, w = u/m */
+      if (wx && wy)                /* union residual (control variate) */
+        fu[j] = (ux * uy - weighted_sum(X, wx, r[j]) * weighted_sum(Y, wy, r[j])) / mx;
+      else
+        fu[j] = (ux / mx) * uy;    /* union: f = w_X u_Y, w = u/m */
     }
     if (antithetic) {
       double g0 = 0.5 * (ffo[0] + ffo[1]), g1 = 0.5 * (fu[0] + fu[1]);
@@ -376,9 +396,9 @@ int orc_direction_sums(const orc_set* A, int32_t ia, const orc_set* B, int32_t i
   if (!rc) rc = load_mol(B, ib, poseB, &mb);
   if (rc) return rc;
   if (tag == ORC_TAG_BA)
-    sums_cross(&mb, &ma, seed, stream, tag, n, (flags & ORC_ANTITHETIC) != 0, sums, n_eff);
+    sums_cross(&mb, &ma, seed, stream, tag, n, (flags & ORC_ANTITHETIC) != 0, NULL, NULL, sums, n_eff);
   else
-    sums_cross(&ma, &mb, seed, stream, tag, n, (flags & ORC_ANTITHETIC) != 0, sums, n_eff);
+    sums_cross(&ma, &mb, seed, stream, tag, n, (flags & ORC_ANTITHETIC) != 0, NULL, NULL, sums, n_eff);
   return ORC_OK;
 }
 
@@ -414,12 +434,12 @@ int orc_overlap_estimate(const orc_set* A, const int32_t* ia, const orc_set* B, 
     }
     uint64_t stream = stream_base + (uint64_t)k;
     double s[4], ne, e_fo, s_fo, e_u, s_u;
-    sums_cross(&ma, &mb, seed, stream, ORC_TAG_AB, n, anti, s, &ne);
+    sums_cross(&ma, &mb, seed, stream, ORC_TAG_AB, n, anti, NULL, NULL, s, &ne);
     finish(ma.Z, s[0], s[1], ne, &e_fo, &s_fo);
     finish(ma.Z, s[2], s[3], ne, &e_u, &s_u);
     if (flags & ORC_SYMMETRIC) {
       double e2_fo, s2_fo, e2_u, s2_u;
-      sums_cross(&mb, &ma, seed, stream, ORC_TAG_BA, n, anti, s, &ne);
+      sums_cross(&mb, &ma, seed, stream, ORC_TAG_BA, n, anti, NULL, NULL, s, &ne);
       finish(mb.Z, s[0], s[1], ne, &e2_fo, &s2_fo);
       finish(mb.Z, s[2], s[3], ne, &e2_u, &s2_u);
       e_fo = 0.5 * (e_fo + e2_fo);
@@ -466,17 +486,21 @@ int orc_union_volume_estimate(const orc_set* S, const int32_t* idx, int64_t n_mo
 /* First-order closed form (Eq. fo, with heights p_i p_j)              */
 /* ------------------------------------------------------------------ */
 
-static double fo_closed(const orc_mol* a, const orc_mol* b) {
+/* sum_ij wa_i wb_j integral g_i g_j (Eq. fo); wa, wb NULL = unit weights. */
+static double fo_closed_w(const orc_mol* a, const double* wa, const orc_mol* b, const double* wb) {
   double s = 0.0;
   for (int i = 0; i < a->n; ++i)
     for (int j = 0; j < b->n; ++j) {
       double ai = a->alpha[i], bj = b->alpha[j], sum = ai + bj;
       double dx = a->c[i][0] - b->c[j][0], dy = a->c[i][1] - b->c[j][1], dz = a->c[i][2] - b->c[j][2];
       double t = ORC_PI / sum;
-      s += a->p[i] * b->p[j] * t * sqrt(t) * exp(-ai * bj / sum * (dx * dx + dy * dy + dz * dz));
+      double w = (wa ? wa[i] : 1.0) * (wb ? wb[j] : 1.0);
+      s += w * a->p[i] * b->p[j] * t * sqrt(t) * exp(-ai * bj / sum * (dx * dx + dy * dy + dz * dz));
     }
   return s;
 }
+
+static double fo_closed(const orc_mol* a, const orc_mol* b) { return fo_closed_w(a, NULL, b, NULL); }
 
 int orc_fo_overlap(const orc_set* A, const int32_t* ia, const orc_set* B, const int32_t* ib,
                    int64_t n_pairs, const float* poses, double* out, int n_threads) {
@@ -697,11 +721,23 @@ int orc_grid(const orc_set* A, int32_t ia, const orc_set* B, int32_t ib, const f
  * Outputs (slot 0 first order, slot 1 union), each [n_pairs][2]:
  * O, seO, T = O / (S - O) with S = O_QQ + O_DD, seT = S / (S - O)^2 seO.
  */
+/*
+ * omega_q, omega_d: per-atom control-variate weights of each set (set atom
+ * order), or both NULL. With them the union slot is estimated as
+ *   O_U = C + (Z_A mean_AB + Z_B mean_BA) / 2,
+ *   C = sum_ij w_i w_j integral g_i g_j (closed form),
+ * from the residual values of sums_cross: unbiased for any weights, since
+ * E_q[u~_A u~_B / m_A] Z_A = C (a weighted first-order overlap). Not in the
+ * paper: it applies the learned crowding weights of the volume control
+ * variate to both molecules of a pair.
+ */
 int orc_tanimoto_pairs(const orc_set* Q, const int32_t* iq, const orc_set* D, const int32_t* id,
                        const uint64_t* stream_ids, int64_t n_pairs, const double* selfQ,
-                       const double* selfD, uint64_t seed, uint32_t n, uint32_t flags, double* O,
-                       double* seO, double* T, double* seT, int n_threads) {
+                       const double* selfD, uint64_t seed, uint32_t n, uint32_t flags,
+                       const double* omega_q, const double* omega_d, double* O, double* seO, double* T,
+                       double* seT, int n_threads) {
   if (n < 2) return ORC_EINVAL;
+  if ((omega_q == NULL) != (omega_d == NULL)) return ORC_EINVAL;
   nthreads_set(n_threads);
   int err = 0;
   const int anti = (flags & ORC_ANTITHETIC) != 0;
@@ -709,15 +745,18 @@ int orc_tanimoto_pairs(const orc_set* Q, const int32_t* iq, const orc_set* D, co
   for (int64_t k = 0; k < n_pairs; ++k) {
     orc_mol mq, md;
     if (load_mol(Q, iq[k], NULL, &mq) || load_mol(D, id[k], NULL, &md)) { err |= 1; continue; }
+    const double* wq = omega_q ? omega_q + Q->offsets[iq[k]] : NULL;
+    const double* wd = omega_d ? omega_d + D->offsets[id[k]] : NULL;
     double s[4], ne, e1[2], s1[2], e2[2], s2[2];
-    sums_cross(&mq, &md, seed, stream_ids[k], ORC_TAG_AB, n, anti, s, &ne);
+    sums_cross(&mq, &md, seed, stream_ids[k], ORC_TAG_AB, n, anti, wq, wd, s, &ne);
     finish(mq.Z, s[0], s[1], ne, &e1[0], &s1[0]);
     finish(mq.Z, s[2], s[3], ne, &e1[1], &s1[1]);
-    sums_cross(&md, &mq, seed, stream_ids[k], ORC_TAG_BA, n, anti, s, &ne);
+    sums_cross(&md, &mq, seed, stream_ids[k], ORC_TAG_BA, n, anti, wd, wq, s, &ne);
     finish(md.Z, s[0], s[1], ne, &e2[0], &s2[0]);
     finish(md.Z, s[2], s[3], ne, &e2[1], &s2[1]);
+    const double C = wq ? fo_closed_w(&mq, wq, &md, wd) : 0.0;
     for (int slot = 0; slot < 2; ++slot) {
-      double o = 0.5 * (e1[slot] + e2[slot]);
+      double o = 0.5 * (e1[slot] + e2[slot]) + (slot == 1 ? C : 0.0);
       double so = 0.5 * sqrt(s1[slot] * s1[slot] + s2[slot] * s2[slot]);
       double S = selfQ[2 * (size_t)iq[k] + slot] + selfD[2 * (size_t)id[k] + slot];
       double den = S - o;
