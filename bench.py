@@ -306,12 +306,12 @@ def main():
     if not args.no_e2e:
         e2e = end_to_end(shp, torch, q, d, n, steps=max(2, min(args.steps, 5)), warmup=1)
 
+    cvres, net = None, None
+    if args.cv_train > 0:
+        net, cvres = cv_section(shp, torch, args.cv_train, args.cv_held, rank)
     adaptive = None
     if args.adaptive_db > 0:
-        adaptive = adaptive_section(shp, torch, args.adaptive_db, rank)
-    cvres = None
-    if args.cv_train > 0:
-        cvres = cv_section(shp, torch, args.cv_train, args.cv_held, rank)
+        adaptive = adaptive_section(shp, torch, args.adaptive_db, rank, net=net)
     aligned = None
     if args.align_db > 0:
         aligned = align_section(shp, torch, args.align_db, rank)
@@ -365,12 +365,14 @@ def main():
     return 0
 
 
-def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: int = 65536):
+def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: int = 65536, net=None):
     """Confidence-bounded screen: 16 queries (20-48 atoms) x n_db molecules
     (18-60, heavy-tailed toward 40), rounds of 256 samples per direction
     until SE(T_union) <= tau or cap. Compared with the plain fixed budget
     that gives the same guarantee (cap samples per direction for every pair),
-    timed on every 64th database molecule."""
+    timed on every 64th database molecule. With a trained crowding network,
+    also the adaptive screen with the union slot's control variate (weights
+    predicted per atom for both sets)."""
     from scipy import stats
     from paper_2607_20766_b300 import synth
     q, d = synth.adaptive_screen(n_q=16, n_db=n_db, seed=4242 + 7919 * rank)
@@ -421,6 +423,40 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
     T_fx = fix["T"].cpu().numpy()[:, 1].reshape(q.n_mol, len(sub))
     rho = [float(stats.spearmanr(T_ad[i], T_fx[i]).statistic) for i in range(q.n_mol)]
     se_ad = res["seT"].cpu().numpy()[:, 1]
+    with_cv = None
+    if net is not None:
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        wq = net.predict(shp.cv_features(Sq))
+        wd = net.predict(shp.cv_features(Sd))
+        c1.record(stream)
+        best_cv, times_cv = shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=16384, tau=tau, cap=cap,
+                                                     omega_q=wq, omega_db=wd)
+        g_cv = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, selfq, selfd, seed=77, tau=tau, round=256, min_n=1024,
+                             cap=cap, omega_q=wq, omega_db=wd)
+        torch.cuda.synchronize()
+        v0 = torch.cuda.Event(enable_timing=True)
+        v1 = torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        rcv = g_cv.replay()
+        v1.record(stream)
+        torch.cuda.synchronize()
+        t_cv = v0.elapsed_time(v1) / 1e3
+        t_w = c0.elapsed_time(c1) / 1e3
+        nu_cv = rcv["n_used"].cpu().numpy().astype(np.int64)
+        T_cv = rcv["T"].cpu().numpy()[:, 1].reshape(q.n_mol, d.n_mol)[:, sub]
+        rho_cv = [float(stats.spearmanr(T_cv[i], T_fx[i]).statistic) for i in range(q.n_mol)]
+        se_cv = rcv["seT"].cpu().numpy()[:, 1]
+        with_cv = {
+            "pairs_per_s": npairs / (t_cv + t_w), "seconds": t_cv, "weights_seconds": t_w,
+            "mean_samples_per_direction": float(nu_cv.mean()), "frac_at_cap": float((nu_cv >= cap).mean()),
+            "frac_se_met": float((se_cv <= tau * (1 + 1e-6)).mean()),
+            "speedup_vs_fixed": (npairs / (t_cv + t_w)) / (fixed_pairs / t_fix),
+            "speedup_vs_adaptive": t_ad / (t_cv + t_w),
+            "spearman_rho_vs_fixed": {"mean": float(np.mean(rho_cv)), "min": float(np.min(rho_cv))},
+            "tuned_variant": int(best_cv),
+        }
     return {
         "workload": f"adaptive screen: 16 queries (20-48 atoms) x {n_db} molecules (18-60, heavy-tailed toward 40), "
                     f"rounds of 256 per direction, SE(T_union) <= {tau} or {cap} per direction",
@@ -435,6 +471,7 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
         "speedup_pairs_per_s": (npairs / t_ad) / (fixed_pairs / t_fix),
         "spearman_rho_vs_fixed": {"mean": float(np.mean(rho)), "min": float(np.min(rho))},
         "tuned_variant": int(best), "variant_ms": [round(float(x), 3) for x in times],
+        "with_control_variate": with_cv,
     }
 
 
@@ -472,7 +509,7 @@ def cv_section(shp, torch, n_train: int, n_held: int, rank: int, target: float =
                                                                  target_rel_se=target))
     n_cv, n_pl = n_cv.cpu().numpy().astype(np.float64), n_pl.cpu().numpy().astype(np.float64)
     z = ((v_cv - v_pl) / torch.sqrt(s_cv ** 2 + s_pl ** 2)).cpu().numpy()
-    return {
+    return net, {
         "workload": f"learned control variate: train on {n_train} molecules (18-60 atoms, union attributions, 256 "
                     f"samples/atom), union volume of {n_held} held-out molecules to relative SE <= {target}",
         "train_seconds": t_train, "targets_seconds": t_data, "predict_seconds": t_pred,

@@ -171,6 +171,10 @@ typedef struct {
                            0 = first order                                         */
   int32_t variant;      /* launch variant, -1 = the tuned (or built-in) default,
                            else 0 .. shp_screen_variants()-1                      */
+  const float* omega_q; /* control variate of the union slot: per-atom weights of
+                           Q and of D (device, set atom order), both or neither;
+                           NULL = plain estimator                                  */
+  const float* omega_db;
 } shp_screen;
 
 /*
@@ -184,6 +188,10 @@ typedef struct {
  *   seT[p][s] = (S_Q + S_D) / (S_Q + S_D - O)^2 * SE(O)   (delta method)
  *   O_out[p][s], seO_out[p][s] (double, may be NULL)
  *   n_used[p] samples drawn per direction (may be NULL)
+ * Control variate (omega_q, omega_db given): the union overlap is estimated
+ * as C + Z E_q[(u_A u_B - u~_A u~_B) / m_A] per direction, u~ = sum_i w_i g_i,
+ * with C = sum_ij w_i w_j integral g_i g_j in closed form (Eq. fo with
+ * weights): unbiased for any weights; the first-order slot is unchanged.
  * Fixed budget: n_fixed samples per direction. Adaptive (n_fixed == 0):
  * rounds of `round` samples per direction are drawn until, after at least
  * min_n, the watched SE(T) (computed in FP32 from the running sums) is

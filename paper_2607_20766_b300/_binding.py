@@ -42,7 +42,7 @@ class ShpScreen(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("stream_base", ctypes.c_uint64), ("n_fixed", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("tau", ctypes.c_float), ("round", ctypes.c_uint32),
                 ("min_n", ctypes.c_uint32), ("cap", ctypes.c_uint32), ("watch", ctypes.c_uint32),
-                ("variant", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("omega_q", ctypes.c_void_p), ("omega_db", ctypes.c_void_p)]
 
 
 class ShpAlign(ctypes.Structure):
@@ -235,19 +235,31 @@ def fo_overlap(A: ShapeSet, ia, B: ShapeSet, ib, pose=None, stream=None, out=Non
 
 def screen_config(seed: int, n_fixed: int = 0, tau: float = 0.005, round: int = 256, min_n: int = 1024,
                   cap: int = 65536, watch: int = 1, flags: int = 0, stream_base: int = 0,
-                  variant: int = -1) -> ShpScreen:
-    """A shp_screen: fixed budget when n_fixed > 0, else adaptive (tau, round, min_n, cap, watch)."""
-    return ShpScreen(seed, stream_base, n_fixed, flags, tau, round, min_n, cap, watch, variant)
+                  variant: int = -1, omega_q: torch.Tensor | None = None,
+                  omega_db: torch.Tensor | None = None) -> ShpScreen:
+    """A shp_screen: fixed budget when n_fixed > 0, else adaptive (tau, round, min_n, cap, watch);
+    omega_q/omega_db (float32 device, per set atom): control variate of the union slot."""
+    return ShpScreen(seed, stream_base, n_fixed, flags, tau, round, min_n, cap, watch, variant,
+                     _dptr(omega_q), _dptr(omega_db))
+
+
+def _weights(omega, S: "ShapeSet"):
+    if omega is None:
+        return None
+    return omega.to(device=S.device, dtype=torch.float32).contiguous()
 
 
 def tanimoto_screen(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: torch.Tensor, seed: int,
                     n_fixed: int = 0, flags: int = 0, stream_base: int = 0, stream=None, with_overlaps: bool = False,
                     out=None, tau: float = 0.005, round: int = 256, min_n: int = 1024, cap: int = 65536,
-                    watch: int = 1, variant: int = -1):
+                    watch: int = 1, variant: int = -1, omega_q: torch.Tensor | None = None,
+                    omega_db: torch.Tensor | None = None):
     """Screen every query against every database molecule (fixed budget when
     n_fixed > 0, else adaptive). Returns dict T, seT ([n_q * n_db, 2]
     float32), n_used ([n_q * n_db] int32 view of uint32) and, with
-    with_overlaps, O, seO ([n_q * n_db, 2] float64)."""
+    with_overlaps, O, seO ([n_q * n_db, 2] float64). omega_q, omega_db
+    (per-atom weights of each set) turn on the union slot's control
+    variate."""
     dev = Q.device
     npairs = Q.n_mol * D.n_mol
     if out is None:
@@ -257,7 +269,8 @@ def tanimoto_screen(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: tor
         if with_overlaps:
             out["O"] = torch.empty((npairs, 2), dtype=torch.float64, device=dev)
             out["seO"] = torch.empty((npairs, 2), dtype=torch.float64, device=dev)
-    cfg = screen_config(seed, n_fixed, tau, round, min_n, cap, watch, flags, stream_base, variant)
+    omega_q, omega_db = _weights(omega_q, Q), _weights(omega_db, D)
+    cfg = screen_config(seed, n_fixed, tau, round, min_n, cap, watch, flags, stream_base, variant, omega_q, omega_db)
     self_q = self_q.to(device=dev, dtype=torch.float64).contiguous()
     self_db = self_db.to(device=dev, dtype=torch.float64).contiguous()
     _check(load_library().tanimoto_screen(Q.handle, D.handle, ctypes.byref(cfg), _dptr(self_q), _dptr(self_db),
@@ -280,15 +293,18 @@ def screen_variant_info(v: int) -> dict:
 
 def tanimoto_screen_tune(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: torch.Tensor, seed: int,
                          n_fixed: int = 0, n_sample: int = 4096, stream=None, tau: float = 0.005, round: int = 256,
-                         min_n: int = 1024, cap: int = 65536, watch: int = 1):
-    """Autotune the screen's launch variant on n_sample pairs; returns
-    (best variant, per-variant milliseconds, -1 where not valid)."""
+                         min_n: int = 1024, cap: int = 65536, watch: int = 1, omega_q: torch.Tensor | None = None,
+                         omega_db: torch.Tensor | None = None):
+    """Autotune the screen's launch variant on n_sample pairs (with the
+    control variate when omega_q/omega_db are given); returns (best variant,
+    per-variant milliseconds, -1 where not valid)."""
     dev = Q.device
     npairs = Q.n_mol * D.n_mol
     T = torch.empty((npairs, 2), dtype=torch.float32, device=dev)
     seT = torch.empty((npairs, 2), dtype=torch.float32, device=dev)
     nu = torch.empty(npairs, dtype=torch.int32, device=dev)
-    cfg = screen_config(seed, n_fixed, tau, round, min_n, cap, watch)
+    omega_q, omega_db = _weights(omega_q, Q), _weights(omega_db, D)
+    cfg = screen_config(seed, n_fixed, tau, round, min_n, cap, watch, omega_q=omega_q, omega_db=omega_db)
     nv = screen_variants()
     times = np.empty(nv, np.float32)
     best = ctypes.c_int32(-1)

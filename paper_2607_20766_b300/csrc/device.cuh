@@ -58,15 +58,6 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, fl
 
 // ---------------------------------------------------------------- tables
 
-// Expanded Gaussian exponent of one atom in a frame with origin o, in log2
-// units: log2 g(r') = a |r'|^2 + b . r' + c0, r' = r - o, with
-// a = -alpha log2(e), b = 2 alpha log2(e) (c - o),
-// c0 = -alpha log2(e) |c - o|^2 + log2 p. Each scalar is stored twice so a
-// packed FP32x2 operation evaluates two samples at once.
-struct __align__(16) Coef {
-  float2 a, bx, by, bz, c0, pad;
-};
-
 struct Pose {
   float r[9];
   float t[3];

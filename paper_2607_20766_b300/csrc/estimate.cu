@@ -111,12 +111,12 @@ __device__ void stage_samp(WarpTables& T, const SetView& S, MolRef M, const Pose
 // identity) are rebuilt here so no pose is held in registers while sampling.
 __device__ __noinline__ void stage_direction(WarpTables& T, const SetView& SX, MolRef MX, const float* pose_x,
                                              const SetView* SY, MolRef MY, const float* pose_y, int lane,
-                                             const float* omega_x = nullptr) {
+                                             const float* omega_x = nullptr, const float* omega_y = nullptr) {
   const Pose PX = make_pose(pose_x), PY = make_pose(pose_y);
   const float3 o = centroid(SX, MX, PX, lane);
   __syncwarp();
   stage_coef(T.x, SX, MX, PX, o, omega_x, lane);
-  if (SY) stage_coef(T.y, *SY, MY, PY, o, nullptr, lane);
+  if (SY) stage_coef(T.y, *SY, MY, PY, o, omega_y, lane);
   stage_samp(T, SX, MX, PX, o, lane);
   __syncwarp();
 }
@@ -233,8 +233,10 @@ __device__ __forceinline__ void draw_batch(const float4* __restrict__ samp, cons
 
 // Evaluates and accumulates one batch of drawn sample pairs (P sample pairs
 // in total, n samples). Values:
-//   cross: fa = m_Y (first order), fb = (u_X / m_X) u_Y (union)
-//   self:  fa = u_X / m_X (volume), fb = u_X^2 / m_X (self-overlap)
+//   cross: fa = m_Y (first order), fb = (u_X / m_X) u_Y (union), with kCV
+//          fb = (u_X u_Y - ut_X ut_Y) / m_X (union residual, ut = sum om g)
+//   self:  fa = u_X / m_X (volume), with kCV (u_X - ut_X) / m_X,
+//          fb = u_X^2 / m_X (self-overlap)
 // With antithetic pairs the unit is the mean of a sample and its
 // reflection. The first batch sets the shifts from sample 0.
 template <bool kSelf, int SP, int kForm, bool kCV = false>
@@ -262,18 +264,26 @@ __device__ __forceinline__ void eval_batch(const CoefT* __restrict__ tx, const C
       fb[p] = make_float2(ux * ux * ix, uy * uy * iy);
     }
   } else {
-    float2 w[SP];
+    float2 w[SP], wt[SP];
 #pragma unroll
     for (int p = 0; p < SP; ++p) {
       w[p] = make_float2(__fdividef(1.f - q[p].x, m[p].x), __fdividef(1.f - q[p].y, m[p].y));
+      if (kCV) {
+        wt[p] = make_float2(__fdividef(ut[p].x, m[p].x), __fdividef(ut[p].y, m[p].y));
+        ut[p] = make_float2(0.f, 0.f);
+      }
       m[p] = make_float2(0.f, 0.f);
       q[p] = make_float2(1.f, 1.f);
     }
-    eval_table<SP, kForm, false>(ty, ny, rx, ry, rz, rr, m, q, ut);
+    eval_table<SP, kForm, kCV>(ty, ny, rx, ry, rz, rr, m, q, ut);
 #pragma unroll
     for (int p = 0; p < SP; ++p) {
       fa[p] = m[p];
-      fb[p] = make_float2(w[p].x * (1.f - q[p].x), w[p].y * (1.f - q[p].y));
+      if (kCV)
+        fb[p] = make_float2(fmaf(-wt[p].x, ut[p].x, w[p].x * (1.f - q[p].x)),
+                            fmaf(-wt[p].y, ut[p].y, w[p].y * (1.f - q[p].y)));
+      else
+        fb[p] = make_float2(w[p].x * (1.f - q[p].x), w[p].y * (1.f - q[p].y));
     }
   }
   if (b == 0) {
@@ -372,6 +382,9 @@ struct CrossArgs {
   double* O;
   double* seO;
   uint32_t* n_used;
+  // control variate of the union slot (screen modes): per-atom weights
+  const float* omega_a;
+  const float* omega_b;
   // adaptive
   float tau;
   uint32_t round_b, min_b, cap_b;  // in batches
@@ -386,10 +399,35 @@ struct CrossArgs {
   unsigned long long* queue;
 };
 
-// Pair epilogue: symmetrised estimates, Tanimoto and SEs; lane 0 only.
+// Closed-form integral of the control variate for one pair,
+// C = sum_ij om_i om_j integral g_i g_j (Eq. fo with weights): lanes over A's
+// atoms, FP32 terms (SFU exp2), FP64 warp sum, valid in every lane.
+__device__ double weighted_fo(const SetView& A, MolRef MA, const float* wa, const SetView& B, MolRef MB,
+                             const float* wb, int lane) {
+  const float kLog2e = 1.4426950408889634f, kPi = 3.14159265358979f;
+  float acc = 0.f;
+  for (int i = lane; i < MA.n; i += 32) {
+    const float4 ai = A.atom[MA.a0 + i];
+    const float lpi = A.aux[MA.a0 + i].y, wi = wa[MA.a0 + i];
+    for (int j = 0; j < MB.n; ++j) {
+      const float4 bj = B.atom[MB.a0 + j];
+      const float dx = ai.x - bj.x, dy = ai.y - bj.y, dz = ai.z - bj.z;
+      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      const float inv = 1.0f / (ai.w + bj.w);
+      const float t = kPi * inv;
+      const float e = fmaf(-kLog2e * ai.w * bj.w * inv, d2, lpi + B.aux[MB.a0 + j].y);
+      acc = fmaf(wi * wb[MB.a0 + j] * t * sqrtf(t), ex2_approx(e), acc);
+    }
+  }
+  return warp_sum((double)acc);
+}
+
+// Pair epilogue: symmetrised estimates, Tanimoto and SEs; lane 0 only. C is
+// the control variate's closed-form part of the union slot (0 without it).
 template <int MODE>
 __device__ void pair_epilogue(const CrossArgs& args, int32_t xa, int32_t xb, int64_t out_idx, const double s0[4],
-                              const float k0[2], const double s1[4], const float k1[2], double n_eff) {
+                              const float k0[2], const double s1[4], const float k1[2], double n_eff,
+                              double C = 0.0) {
   const double ZA = args.A.Z[xa], ZB = args.B.Z[xb];
   double e[2], sd[2];
   for (int slot = 0; slot < 2; ++slot) {
@@ -405,6 +443,7 @@ __device__ void pair_epilogue(const CrossArgs& args, int32_t xa, int32_t xb, int
       sd[slot] = se0;
     }
   }
+  e[1] += C;
   if (MODE == kPairs) {
     args.est[2 * out_idx] = e[0]; args.est[2 * out_idx + 1] = e[1];
     args.se[2 * out_idx] = sd[0]; args.se[2 * out_idx + 1] = sd[1];
@@ -422,7 +461,7 @@ __device__ void pair_epilogue(const CrossArgs& args, int32_t xa, int32_t xb, int
 
 // FP32 SE(T) of the watched slot from the running sums (adaptive stop rule).
 __device__ __forceinline__ float watched_se_t(const CrossArgs& args, const DirState& sa, const DirState& sb, int32_t xa,
-                                              int32_t xb, float n) {
+                                              int32_t xb, float n, float C = 0.f) {
   const bool w = args.watch != 0;
   float h[4] = {w ? sa.hi[2] : sa.hi[0], w ? sa.hi[3] : sa.hi[1], w ? sb.hi[2] : sb.hi[0], w ? sb.hi[3] : sb.hi[1]};
   float l[4] = {w ? sa.lo[2] : sa.lo[0], w ? sa.lo[3] : sa.lo[1], w ? sb.lo[2] : sb.lo[0], w ? sb.lo[3] : sb.lo[1]};
@@ -433,14 +472,15 @@ __device__ __forceinline__ float watched_se_t(const CrossArgs& args, const DirSt
   const float va = fmaxf((s2a - s1a * s1a / n) / (n - 1.f), 0.f);
   const float vb = fmaxf((s2b - s1b * s1b / n) / (n - 1.f), 0.f);
   const float ea = ZA * ((w ? sa.K[1] : sa.K[0]) + s1a / n), eb = ZB * ((w ? sb.K[1] : sb.K[0]) + s1b / n);
-  const float O = 0.5f * (ea + eb);
+  const float O = 0.5f * (ea + eb) + (w ? C : 0.f);
   const float seO = 0.5f * sqrtf((ZA * ZA * va + ZB * ZB * vb) / n);
   const float S = (float)(args.self_q[2 * (int64_t)xa + args.watch] + args.self_db[2 * (int64_t)xb + args.watch]);
   const float den = S - O;
   return fabsf(S / (den * den)) * seO;
 }
 
-template <int MODE, int SP, int kForm, int kWarps, int kMinBlocks>
+// kCV (screen modes): union slot with the weighted-Gaussian control variate.
+template <int MODE, int SP, int kForm, int kWarps, int kMinBlocks, bool kCV = false>
 __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) cross_kernel(const CrossArgs args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -482,17 +522,21 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) cross_kernel(const Cr
     DirState& sb = T.st[1][lane];
     dir_init(sa);
     dir_init(sb);
+    const float* wa = kCV ? args.omega_a : nullptr;
+    const float* wb = kCV ? args.omega_b : nullptr;
+    const double Ccv = kCV ? weighted_fo(args.A, MA, wa, args.B, MB, wb, lane) : 0.0;
     uint32_t n_dir;
     if (MODE != kAdaptive) {
       const uint32_t nb = ((args.n + 1u) / 2u + batch - 1u) / batch;
-      stage_direction(T, args.A, MA, nullptr, &args.B, MB, pose, lane);
+      stage_direction(T, args.A, MA, nullptr, &args.B, MB, pose, lane, wa, wb);
       for (uint32_t b = 0; b < nb; ++b)
-        run_batch<false, SP, kForm>(T, MA.n, MB.n, b, args.n, args.key, slo, shi, SHP_TAG_AB, args.anti, lane, sa);
+        run_batch<false, SP, kForm, kCV>(T, MA.n, MB.n, b, args.n, args.key, slo, shi, SHP_TAG_AB, args.anti, lane,
+                                         sa);
       if (args.symmetric) {
-        stage_direction(T, args.B, MB, pose, &args.A, MA, nullptr, lane);
+        stage_direction(T, args.B, MB, pose, &args.A, MA, nullptr, lane, wb, wa);
         for (uint32_t b = 0; b < nb; ++b)
-          run_batch<false, SP, kForm>(T, MB.n, MA.n, b, args.n, args.key, slo, shi, SHP_TAG_BA, args.anti, lane,
-                                      sb);
+          run_batch<false, SP, kForm, kCV>(T, MB.n, MA.n, b, args.n, args.key, slo, shi, SHP_TAG_BA, args.anti,
+                                           lane, sb);
       }
       n_dir = args.n;
     } else {
@@ -501,16 +545,16 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) cross_kernel(const Cr
       for (;;) {
         const uint32_t nxt = b + args.round_b;
         const uint32_t n_now = nxt * batch * 2u;
-        stage_direction(T, args.A, MA, nullptr, &args.B, MB, nullptr, lane);
+        stage_direction(T, args.A, MA, nullptr, &args.B, MB, nullptr, lane, wa, wb);
         for (uint32_t k = b; k < nxt; ++k)
-          run_batch<false, SP, kForm>(T, MA.n, MB.n, k, n_now, args.key, slo, shi, SHP_TAG_AB, false, lane, sa);
-        stage_direction(T, args.B, MB, nullptr, &args.A, MA, nullptr, lane);
+          run_batch<false, SP, kForm, kCV>(T, MA.n, MB.n, k, n_now, args.key, slo, shi, SHP_TAG_AB, false, lane, sa);
+        stage_direction(T, args.B, MB, nullptr, &args.A, MA, nullptr, lane, wb, wa);
         for (uint32_t k = b; k < nxt; ++k)
-          run_batch<false, SP, kForm>(T, MB.n, MA.n, k, n_now, args.key, slo, shi, SHP_TAG_BA, false, lane, sb);
+          run_batch<false, SP, kForm, kCV>(T, MB.n, MA.n, k, n_now, args.key, slo, shi, SHP_TAG_BA, false, lane, sb);
         b = nxt;
         if (b >= args.cap_b) break;
         if (b >= args.min_b) {
-          const float se_t = watched_se_t(args, sa, sb, xa, xb, (float)n_now);
+          const float se_t = watched_se_t(args, sa, sb, xa, xb, (float)n_now, (float)Ccv);
           const int stop = __shfl_sync(0xffffffffu, (int)(se_t <= args.tau), 0);
           if (stop) break;
         }
@@ -522,7 +566,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) cross_kernel(const Cr
     if (args.symmetric) dir_totals(sb, s1);
     if (lane == 0) {
       const double n_eff = args.anti ? (double)(n_dir / 2u) : (double)n_dir;
-      pair_epilogue<MODE>(args, xa, xb, out_idx, s0, sa.K, s1, sb.K, n_eff);
+      pair_epilogue<MODE>(args, xa, xb, out_idx, s0, sa.K, s1, sb.K, n_eff, Ccv);
       if (MODE != kPairs && args.n_used) args.n_used[out_idx] = n_dir;
     }
     __syncwarp();
@@ -605,6 +649,13 @@ constexpr Variant kVariants[] = {{4, 0, 8, 2}, {4, 2, 8, 2}, {4, 0, 4, 5}, {4, 2
                                  {4, 7, 8, 2}, {4, 5, 4, 5}, {2, 5, 4, 5}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
+// Variants also built with the control variate of the union slot (one more
+// FMA per evaluation and two more values per sample pair in registers).
+constexpr bool cv_variant(int v) {
+  return kVariants[v].sp == 4 && kVariants[v].warps == 8 && kVariants[v].min_blocks == 2 &&
+         (kVariants[v].form == 2 || kVariants[v].form == 3 || kVariants[v].form == 5);
+}
+
 template <int V>
 struct VariantTraits {
   static constexpr int sp = kVariants[V].sp, form = kVariants[V].form, warps = kVariants[V].warps;
@@ -656,24 +707,27 @@ int launch_persistent(Kernel k, Args args, int64_t n_items, int warps, size_t sm
   return launch_persistent(k, args, n_items, warps, warps * 32, smem, st, queue_in);
 }
 
-template <int MODE, int V>
+template <int MODE, int V, bool kCV>
 int launch_cross_v(const CrossArgs& a, int64_t n_items, cudaStream_t st) {
   using Tr = VariantTraits<V>;
   if constexpr (MODE == kAdaptive && Tr::sp != 4) {
     set_error("adaptive screen: launch variant %d does not run rounds of 256 samples", V);
     return SHP_EINVAL;
+  } else if constexpr (kCV && (MODE == kPairs || !cv_variant(V))) {
+    set_error("screen with control variate: launch variant %d is not built with it", V);
+    return SHP_EINVAL;
   } else {
-    return launch_persistent(cross_kernel<MODE, Tr::sp, Tr::form, Tr::warps, Tr::min_blocks>, a, n_items, Tr::warps,
-                             Tr::smem, st);
+    return launch_persistent(cross_kernel<MODE, Tr::sp, Tr::form, Tr::warps, Tr::min_blocks, kCV>, a, n_items,
+                             Tr::warps, Tr::smem, st);
   }
 }
 
-template <int MODE, int V = 0>
+template <int MODE, bool kCV = false, int V = 0>
 int launch_cross(int v, const CrossArgs& a, int64_t n_items, cudaStream_t st) {
   if constexpr (V + 1 < kNumVariants) {
-    return v == V ? launch_cross_v<MODE, V>(a, n_items, st) : launch_cross<MODE, V + 1>(v, a, n_items, st);
+    return v == V ? launch_cross_v<MODE, V, kCV>(a, n_items, st) : launch_cross<MODE, kCV, V + 1>(v, a, n_items, st);
   } else {
-    return launch_cross_v<MODE, V>(a, n_items, st);
+    return launch_cross_v<MODE, V, kCV>(a, n_items, st);
   }
 }
 
@@ -683,35 +737,41 @@ int launch_self(const SelfArgs& a, int64_t n_items, cudaStream_t st) {
                            Tr::smem, st);
 }
 
-// Tuned defaults per (device, mode); -1 = not tuned.
+// Tuned defaults per (device, mode, control variate); -1 = not tuned, then
+// variant 4 (4 sample pairs per lane, packed exponent, valid everywhere).
+constexpr int kDefaultVariant = 4;
 std::mutex g_tune_mu;
-int g_tuned[64][3];
+int g_tuned[64][3][2];
 bool g_tuned_init = false;
 
-int default_variant(int mode) {
+int default_variant(int mode, bool cv = false) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   if (!g_tuned_init) {
-    for (auto& row : g_tuned) row[0] = row[1] = row[2] = -1;
+    for (auto& dev : g_tuned)
+      for (auto& row : dev) row[0] = row[1] = -1;
     g_tuned_init = true;
   }
   int dev = 0;
   cudaGetDevice(&dev);
-  const int v = (dev >= 0 && dev < 64) ? g_tuned[dev][mode] : -1;
-  return v >= 0 ? v : 0;
+  const int v = (dev >= 0 && dev < 64) ? g_tuned[dev][mode][cv] : -1;
+  return v >= 0 ? v : kDefaultVariant;
 }
 
-void set_default_variant(int mode, int v) {
-  default_variant(mode);
+void set_default_variant(int mode, bool cv, int v) {
+  default_variant(mode, cv);
   std::lock_guard<std::mutex> lk(g_tune_mu);
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64) g_tuned[dev][mode] = v;
+  if (dev >= 0 && dev < 64) g_tuned[dev][mode][cv] = v;
 }
 
-bool variant_valid(int mode, int v) {
+bool variant_valid(int mode, bool cv, int v) {
   if (v < 0 || v >= kNumVariants) return false;
+  if (cv && !cv_variant(v)) return false;
   return mode != kAdaptive || kVariants[v].sp == 4;
 }
+
+static_assert(cv_variant(kDefaultVariant), "the default variant must be built with the control variate");
 
 int check_mc(const shp_mc* mc, const char* who) {
   if (!mc) { set_error("%s: NULL shp_mc", who); return SHP_EINVAL; }
@@ -776,10 +836,19 @@ int screen_args(shp_set Q, shp_set D, const shp_screen* cfg, const double* self_
   a.stream_base = cfg->stream_base;
   a.anti = (cfg->flags & SHP_ANTITHETIC) != 0;
   a.symmetric = true;
+  if ((cfg->omega_q == nullptr) != (cfg->omega_db == nullptr)) {
+    set_error("%s: give both control-variate weight arrays or neither", who);
+    return SHP_EINVAL;
+  }
+  a.omega_a = cfg->omega_q;
+  a.omega_b = cfg->omega_db;
   return SHP_OK;
 }
 
 int launch_screen(int mode, int v, const CrossArgs& a, int64_t n_items, cudaStream_t st) {
+  if (a.omega_a)
+    return mode == kScreen ? launch_cross<kScreen, true>(v, a, n_items, st)
+                           : launch_cross<kAdaptive, true>(v, a, n_items, st);
   return mode == kScreen ? launch_cross<kScreen>(v, a, n_items, st) : launch_cross<kAdaptive>(v, a, n_items, st);
 }
 
@@ -851,8 +920,9 @@ extern "C" int tanimoto_screen(shp_set Q, shp_set D, const shp_screen* cfg, cons
   if (rc) return rc;
   if (a.n_items == 0) return SHP_OK;
   int v = cfg->variant;
-  if (v < 0) v = default_variant(mode);
-  if (!variant_valid(mode, v)) { set_error("tanimoto_screen: variant %d not valid for this mode", v); return SHP_EINVAL; }
+  const bool cv = a.omega_a != nullptr;
+  if (v < 0) v = default_variant(mode, cv);
+  if (!variant_valid(mode, cv, v)) { set_error("tanimoto_screen: variant %d not valid for this mode", v); return SHP_EINVAL; }
   return launch_screen(mode, v, a, a.n_items, (cudaStream_t)stream);
 }
 
@@ -889,7 +959,7 @@ extern "C" int tanimoto_screen_tune(shp_set Q, shp_set D, const shp_screen* cfg,
   float best_ms = 0.f;
   for (int v = 0; v < kNumVariants; ++v) {
     if (timings_ms) timings_ms[v] = -1.f;
-    if (!variant_valid(mode, v)) continue;
+    if (!variant_valid(mode, a.omega_a != nullptr, v)) continue;
     rc = launch_screen(mode, v, a, n_sample, st);  // warm-up (first launch pays set-up)
     if (!rc) {
       cudaEventRecord(e0, st);
@@ -907,7 +977,7 @@ extern "C" int tanimoto_screen_tune(shp_set Q, shp_set D, const shp_screen* cfg,
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  set_default_variant(mode, best_v);
+  set_default_variant(mode, a.omega_a != nullptr, best_v);
   if (best) *best = best_v;
   return SHP_OK;
 }

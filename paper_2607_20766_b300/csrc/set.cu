@@ -186,7 +186,7 @@ using namespace shp;
 
 extern "C" const char* shp_last_error(void) { return g_err.c_str(); }
 
-extern "C" int shp_version(void) { return 2; }
+extern "C" int shp_version(void) { return 3; }
 
 extern "C" int shape_set_load(const float* xyz, const float* radius, const float* height,
                               double c_alpha, const int32_t* offsets, int32_t n_mol, void* stream,

@@ -42,7 +42,8 @@ def small_screen():
     return q, d, shp.shape_set_load(q), shp.shape_set_load(d), oracle_self(q, 1, 8192), oracle_self(d, 2, 8192)
 
 
-def check_adaptive_against_oracle(q, d, res, sq, sd, seed, tau, rnd, min_n, cap, pairs, n_db, stream_base=0):
+def check_adaptive_against_oracle(q, d, res, sq, sd, seed, tau, rnd, min_n, cap, pairs, n_db, stream_base=0,
+                                  omega_q=None, omega_d=None):
     nu = res["n_used"].cpu().numpy().astype(np.int64)[pairs]
     iq, idd = pairs // n_db, pairs % n_db
     assert np.all(nu % rnd == 0) and np.all(nu >= min_n) and np.all(nu <= cap)
@@ -53,7 +54,7 @@ def check_adaptive_against_oracle(q, d, res, sq, sd, seed, tau, rnd, min_n, cap,
     for n in np.unique(nu):
         sel = nu == n
         ref = O.tanimoto_pairs(q, iq[sel], d, idd[sel], (stream_base + pairs[sel]).astype(np.uint64), sq, sd,
-                               seed=seed, n=int(n))
+                               seed=seed, n=int(n), omega_q=omega_q, omega_d=omega_d)
         assert_close(O_[sel], ref["O"], what=f"O at n={n}")
         assert_close(seO[sel], ref["seO"], what=f"seO at n={n}")
         assert_close(T[sel], ref["T"], what=f"T at n={n}")
@@ -63,7 +64,7 @@ def check_adaptive_against_oracle(q, d, res, sq, sd, seed, tau, rnd, min_n, cap,
             assert np.all(ref["seT"][:, 1] <= tau * (1 + 1e-4)), "stopped before SE(T) <= tau"
         if n > min_n:
             prev = O.tanimoto_pairs(q, iq[sel], d, idd[sel], (stream_base + pairs[sel]).astype(np.uint64), sq, sd,
-                                    seed=seed, n=int(n - rnd))
+                                    seed=seed, n=int(n - rnd), omega_q=omega_q, omega_d=omega_d)
             assert np.all(prev["seT"][:, 1] > tau * (1 - 1e-4)), "did not stop when SE(T) <= tau"
     return nu
 
@@ -186,3 +187,35 @@ def test_graph_captured_adaptive_step_matches_eager(small_screen):
             np.testing.assert_array_equal(res[k].cpu().numpy(), eager[2][k].cpu().numpy())
     pairs = np.arange(q.n_mol * d.n_mol)
     check_adaptive_against_oracle(q, d, res, sq, sd, 5, 0.012, 256, 512, 6144, pairs, d.n_mol, stream_base=3)
+
+
+def test_control_variate_screen_parity(small_screen):
+    """Union slot with the weighted-Gaussian control variate (any weights),
+    fixed budget and adaptive, against the oracle on the same streams; every
+    variant built with it agrees."""
+    q, d, Sq, Sd, sq, sd = small_screen
+    rng = np.random.default_rng(8)
+    wq = rng.uniform(0.3, 1.1, q.n_atoms).astype(np.float32)
+    wd = rng.uniform(0.3, 1.1, d.n_atoms).astype(np.float32)
+    tq, td = torch.tensor(sq), torch.tensor(sd)
+    gq, gd = torch.tensor(wq), torch.tensor(wd)
+    pairs = np.arange(q.n_mol * d.n_mol)
+    ref = O.tanimoto_pairs(q, pairs // d.n_mol, d, pairs % d.n_mol, (2 + pairs).astype(np.uint64), sq, sd, seed=6,
+                           n=1500, omega_q=wq.astype(np.float64), omega_d=wd.astype(np.float64))
+    cv_variants = []
+    for v in range(shp.screen_variants()):
+        try:
+            res = shp.tanimoto_screen(Sq, Sd, tq, td, seed=6, n_fixed=1500, stream_base=2, with_overlaps=True,
+                                      omega_q=gq, omega_db=gd, variant=v)
+        except shp.ShapeError:
+            continue
+        cv_variants.append(v)
+        for k in ("O", "seO", "T", "seT"):
+            assert_close(res[k].cpu().numpy(), ref[k], what=f"{k} (variant {v})")
+    assert len(cv_variants) >= 2
+    res = shp.tanimoto_screen(Sq, Sd, tq, td, seed=5, tau=0.012, round=256, min_n=512, cap=6144, with_overlaps=True,
+                              stream_base=3, omega_q=gq, omega_db=gd)
+    check_adaptive_against_oracle(q, d, res, sq, sd, 5, 0.012, 256, 512, 6144, pairs, d.n_mol, stream_base=3,
+                                  omega_q=wq.astype(np.float64), omega_d=wd.astype(np.float64))
+    with pytest.raises(shp.ShapeError):
+        shp.tanimoto_screen(Sq, Sd, tq, td, seed=5, n_fixed=512, omega_q=gq)  # one weight array only
