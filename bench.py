@@ -37,9 +37,9 @@ N_SAMPLES = 4096
 SEED_WORKLOAD = 2026
 FP32_OPS_PER_EVAL = 6  # 4 FMA (expanded exponent) + 1 add (first-order sum) + 1 FMA (union product)
 # DRAM bytes per screened pair, from one ncu capture of the screen kernel on a 20,000-pair case
-# (dram__bytes_read.sum + dram__bytes_write.sum = 24.04 MB; each database molecule is read once,
+# (dram__bytes_read.sum + dram__bytes_write.sum = 24.08 MB; each database molecule is read once,
 # so the traffic scales with the pairs)
-SCREEN_DRAM_BYTES_PER_PAIR = 24_044_288 / 20_000
+SCREEN_DRAM_BYTES_PER_PAIR = (23_700_480 + 381_184) / 20_000
 
 
 def parse_args():
@@ -109,25 +109,29 @@ class ClockSampler:
         self.thread = None
         self.samples = []
 
-    def _nvml_loop(self, nv, h):
-        while not self.stop.is_set():
-            try:
-                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
-                mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
-                rs = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
-                self.samples.append((float(sm), float(mx), int(rs)))
-            except Exception:
-                pass
-            self.stop.wait(0.02)
+    def _sample(self):
+        nv, h = self.nv, self.handle
+        try:
+            sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
+            mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+            rs = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+            self.samples.append((float(sm), float(mx), int(rs)))
+        except Exception:
+            pass
+
+    def _nvml_loop(self):
+        while not self.stop.wait(0.02):
+            self._sample()
 
     def __enter__(self):
         try:
             import threading
             import pynvml as nv
             nv.nvmlInit()
-            h = nv.nvmlDeviceGetHandleByIndex(self.index)
+            self.nv, self.handle = nv, nv.nvmlDeviceGetHandleByIndex(self.index)
             self.stop = threading.Event()
-            self.thread = threading.Thread(target=self._nvml_loop, args=(nv, h), daemon=True)
+            self.thread = threading.Thread(target=self._nvml_loop, daemon=True)
+            self._sample()  # at the start of the timed region, then every 20 ms and once at its end
             self.thread.start()
             return self
         except Exception:
@@ -145,6 +149,7 @@ class ClockSampler:
         if self.thread is not None:
             self.stop.set()
             self.thread.join(timeout=5)
+            self._sample()
         if self.proc is not None:
             self.proc.terminate()
             try:
