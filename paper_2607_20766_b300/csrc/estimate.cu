@@ -670,20 +670,20 @@ int sm_count(int* sms) {
   return SHP_OK;
 }
 
-// Persistent launch: as many CTAs as fit on the GPU (at most one per
-// `items_per_cta` items), each of `threads` threads, pulling items from a
-// zeroed device queue counter (stream-ordered scratch unless given).
+// Persistent launch: as many CTAs of `warps` warps as fit on the GPU (at
+// most one per `warps` items), pulling items from a zeroed device queue
+// counter (stream-ordered scratch unless given).
 template <class Kernel, class Args>
-int launch_persistent(Kernel k, Args args, int64_t n_items, int items_per_cta, int threads, size_t smem,
-                      cudaStream_t st, unsigned long long* queue_in = nullptr) {
+int launch_persistent(Kernel k, Args args, int64_t n_items, int warps, size_t smem, cudaStream_t st,
+                      unsigned long long* queue_in = nullptr) {
   int sms = 0;
   int rc = sm_count(&sms);
   if (rc) return rc;
   SHP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  SHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem));
+  SHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, warps * 32, smem));
   if (per_sm < 1) per_sm = 1;
-  const int64_t need = (n_items + items_per_cta - 1) / items_per_cta;
+  const int64_t need = (n_items + warps - 1) / warps;
   int64_t g = (int64_t)sms * per_sm;
   if (need < g) g = need;
   const int grid = (int)(g < 1 ? 1 : g);
@@ -692,19 +692,13 @@ int launch_persistent(Kernel k, Args args, int64_t n_items, int items_per_cta, i
   cudaError_t e = cudaMemsetAsync(q, 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess) {
     args.queue = q;
-    k<<<grid, threads, smem, st>>>(args);
+    k<<<grid, warps * 32, smem, st>>>(args);
     e = cudaGetLastError();
   }
   cudaError_t e2 = queue_in ? cudaSuccess : cudaFreeAsync(q, st);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
   return SHP_OK;
-}
-
-template <class Kernel, class Args>
-int launch_persistent(Kernel k, Args args, int64_t n_items, int warps, size_t smem, cudaStream_t st,
-                      unsigned long long* queue_in = nullptr) {
-  return launch_persistent(k, args, n_items, warps, warps * 32, smem, st, queue_in);
 }
 
 template <int MODE, int V, bool kCV>
