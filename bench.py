@@ -134,8 +134,9 @@ class ClockSampler:
             self._sample()  # at the start of the timed region, then every 20 ms and once at its end
             self.thread.start()
             return self
-        except Exception:
+        except Exception as exc:
             self.thread = None
+            self.nvml_error = f"{type(exc).__name__}: {exc}"[:120]
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -180,7 +181,7 @@ class ClockSampler:
                 for nm, v in zip(names, parts[3:7]):
                     if v.lower() in ("active", "1", "yes"):
                         reasons.add(nm)
-            source = "nvidia-smi, 200 ms"
+            source = "nvidia-smi, 200 ms" + (f" (NVML: {self.nvml_error})" if getattr(self, "nvml_error", None) else "")
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),

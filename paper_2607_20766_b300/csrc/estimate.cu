@@ -52,6 +52,7 @@ struct __align__(16) WarpTables {
   uint32_t thr[SHP_MAX_ATOMS];
   uint8_t alias[SHP_MAX_ATOMS];
   DirState st[2][32];          // per-lane running sums of both directions
+  float4 origin;               // frame shared by both directions (adaptive screen)
 };
 
 struct MolRef {
@@ -118,6 +119,34 @@ __device__ __noinline__ void stage_direction(WarpTables& T, const SetView& SX, M
   stage_coef(T.x, SX, MX, PX, o, omega_x, lane);
   if (SY) stage_coef(T.y, *SY, MY, PY, o, omega_y, lane);
   stage_samp(T, SX, MX, PX, o, lane);
+  __syncwarp();
+}
+
+// Both molecules' coefficient tables (A into x, B into y) in one frame for
+// both proposal directions, when their centroids lie within 2 A of each
+// other (the frame is then their midpoint, which keeps every sample as close
+// to the origin as a per-direction frame would). Returns false, staging
+// nothing, otherwise. Later rounds restage only the sampled molecule's
+// component table (stage_samp_in_frame).
+__device__ __noinline__ bool stage_pair_frame(WarpTables& T, const SetView& SA, MolRef MA, const SetView& SB,
+                                              MolRef MB, int lane, const float* omega_a, const float* omega_b) {
+  const Pose P = make_pose(nullptr);
+  const float3 oa = centroid(SA, MA, P, lane), ob = centroid(SB, MB, P, lane);
+  const float dx = oa.x - ob.x, dy = oa.y - ob.y, dz = oa.z - ob.z;
+  if (dx * dx + dy * dy + dz * dz > 4.f) return false;
+  const float3 o = make_float3(0.5f * (oa.x + ob.x), 0.5f * (oa.y + ob.y), 0.5f * (oa.z + ob.z));
+  __syncwarp();
+  stage_coef(T.x, SA, MA, P, o, omega_a, lane);
+  stage_coef(T.y, SB, MB, P, o, omega_b, lane);
+  if (lane == 0) T.origin = make_float4(o.x, o.y, o.z, 0.f);
+  __syncwarp();
+  return true;
+}
+
+__device__ __noinline__ void stage_samp_in_frame(WarpTables& T, const SetView& S, MolRef M, int lane) {
+  const float4 o = T.origin;
+  __syncwarp();
+  stage_samp(T, S, M, make_pose(nullptr), make_float3(o.x, o.y, o.z), lane);
   __syncwarp();
 }
 
@@ -317,14 +346,16 @@ __device__ __forceinline__ void eval_batch(const CoefT* __restrict__ tx, const C
   for (int t = 0; t < 4; ++t) acc2(st.hi[t], st.lo[t], acc[t]);
 }
 
-// One batch of one direction (draw, evaluate, accumulate) by a single warp.
+// One batch of one direction (draw, evaluate, accumulate) by a single warp;
+// tx/ty are the sampled and the other molecule's coefficient tables (T.x and
+// T.y unless given).
 template <bool kSelf, int SP, int kForm, bool kCV = false>
 __device__ __forceinline__ void run_batch(WarpTables& T, int nx, int ny, uint32_t b, uint32_t n, Key key,
                                           uint32_t slo, uint32_t shi, uint32_t tag, bool anti, int lane,
-                                          DirState& st) {
+                                          DirState& st, const CoefT* tx = nullptr, const CoefT* ty = nullptr) {
   float2 rx[SP], ry[SP], rz[SP], rr[SP];
   draw_batch<SP>(T.samp, T.thr, T.alias, nx, b, key, slo, shi, tag, anti, lane, rx, ry, rz, rr);
-  eval_batch<kSelf, SP, kForm, kCV>(T.x, T.y, nx, ny, b, n, anti, lane, st, rx, ry, rz, rr);
+  eval_batch<kSelf, SP, kForm, kCV>(tx ? tx : T.x, ty ? ty : T.y, nx, ny, b, n, anti, lane, st, rx, ry, rz, rr);
 }
 
 // Compensated FP32 warp sum of hi + lo; lane 0's (hi, lo) carries the total.
@@ -540,17 +571,27 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) cross_kernel(const Cr
       }
       n_dir = args.n;
     } else {
-      // rounds of round_b batches per direction until SE(T) <= tau or cap
+      // rounds of round_b batches per direction until SE(T) <= tau or cap;
+      // with a shared frame only the sampled molecule's component table is
+      // restaged per direction and round
+      const bool shared = stage_pair_frame(T, args.A, MA, args.B, MB, lane, wa, wb);
       uint32_t b = 0;
       for (;;) {
         const uint32_t nxt = b + args.round_b;
         const uint32_t n_now = nxt * batch * 2u;
-        stage_direction(T, args.A, MA, nullptr, &args.B, MB, nullptr, lane, wa, wb);
+        if (shared)
+          stage_samp_in_frame(T, args.A, MA, lane);
+        else
+          stage_direction(T, args.A, MA, nullptr, &args.B, MB, nullptr, lane, wa, wb);
         for (uint32_t k = b; k < nxt; ++k)
           run_batch<false, SP, kForm, kCV>(T, MA.n, MB.n, k, n_now, args.key, slo, shi, SHP_TAG_AB, false, lane, sa);
-        stage_direction(T, args.B, MB, nullptr, &args.A, MA, nullptr, lane, wb, wa);
+        if (shared)
+          stage_samp_in_frame(T, args.B, MB, lane);
+        else
+          stage_direction(T, args.B, MB, nullptr, &args.A, MA, nullptr, lane, wb, wa);
         for (uint32_t k = b; k < nxt; ++k)
-          run_batch<false, SP, kForm, kCV>(T, MB.n, MA.n, k, n_now, args.key, slo, shi, SHP_TAG_BA, false, lane, sb);
+          run_batch<false, SP, kForm, kCV>(T, MB.n, MA.n, k, n_now, args.key, slo, shi, SHP_TAG_BA, false, lane, sb,
+                                           shared ? T.y : T.x, shared ? T.x : T.y);
         b = nxt;
         if (b >= args.cap_b) break;
         if (b >= args.min_b) {

@@ -219,3 +219,19 @@ def test_control_variate_screen_parity(small_screen):
                                   omega_q=wq.astype(np.float64), omega_d=wd.astype(np.float64))
     with pytest.raises(shp.ShapeError):
         shp.tanimoto_screen(Sq, Sd, tq, td, seed=5, n_fixed=512, omega_q=gq)  # one weight array only
+
+
+def test_adaptive_parity_when_centroids_are_apart(small_screen):
+    """Database molecules shifted 6 A away from the queries: the adaptive
+    kernel stages each direction in its own frame instead of the shared one;
+    estimates and stop decisions still match the oracle."""
+    q, d, Sq, Sd, sq, sd = small_screen
+    from paper_2607_20766_b300.synth import MolSet
+    dd = MolSet(d.xyz + np.float32([6.0, 0.0, 0.0]), d.radius, d.offsets, d.elem)
+    Sdd = shp.shape_set_load(dd)
+    sdd = oracle_self(dd, 2, 8192)
+    tau, rnd, min_n, cap = 0.02, 256, 512, 4096
+    res = shp.tanimoto_screen(Sq, Sdd, torch.tensor(sq), torch.tensor(sdd), seed=15, tau=tau, round=rnd,
+                              min_n=min_n, cap=cap, with_overlaps=True)
+    pairs = np.arange(q.n_mol * dd.n_mol)
+    check_adaptive_against_oracle(q, dd, res, sq, sdd, 15, tau, rnd, min_n, cap, pairs, dd.n_mol)
