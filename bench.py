@@ -94,6 +94,61 @@ def step_evals(q, d, n):
 
 # ---------------------------------------------------------------- clocks
 
+def gpu_uuid(torch, index: int):
+    """NVML-style UUID ("GPU-…") of CUDA device `index`, or None."""
+    try:
+        u = str(torch.cuda.get_device_properties(index).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+class _NvmlC:
+    """The four read-only NVML queries the clock sampler needs, through ctypes
+    on the driver's libnvidia-ml (used when the pynvml module is missing)."""
+    NVML_CLOCK_SM = 1
+
+    def __init__(self):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit_v2 failed")
+        self.reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def nvmlDeviceGetHandleByIndex(self, i):
+        h = self.ct.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(self.ct.c_uint(i), self.ct.byref(h)) != 0:
+            raise RuntimeError("nvmlDeviceGetHandleByIndex_v2 failed")
+        return h
+
+    def nvmlDeviceGetHandleByUUID(self, uuid):
+        h = self.ct.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByUUID(uuid.encode() if isinstance(uuid, str) else uuid,
+                                              self.ct.byref(h)) != 0:
+            raise RuntimeError("nvmlDeviceGetHandleByUUID failed")
+        return h
+
+    def _clock(self, fn, h, kind):
+        v = self.ct.c_uint()
+        if fn(h, self.ct.c_int(kind), self.ct.byref(v)) != 0:
+            raise RuntimeError("clock query failed")
+        return v.value
+
+    def nvmlDeviceGetClockInfo(self, h, kind):
+        return self._clock(self.lib.nvmlDeviceGetClockInfo, h, kind)
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind):
+        return self._clock(self.lib.nvmlDeviceGetMaxClockInfo, h, kind)
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        v = self.ct.c_ulonglong()
+        if self.reasons(h, self.ct.byref(v)) != 0:
+            raise RuntimeError("clock event reasons query failed")
+        return v.value
+
+
 class ClockSampler:
     """SM clock and throttle reasons sampled during the timed region: NVML
     from a thread every 20 ms (read-only queries), else nvidia-smi at 200 ms."""
@@ -103,8 +158,9 @@ class ClockSampler:
     # NVML clock event reason bits (nvml.h)
     REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, uuid: str | None = None):
         self.index = index
+        self.uuid = uuid  # "GPU-…" of the CUDA device (NVML indices need not match CUDA's)
         self.proc = None
         self.thread = None
         self.samples = []
@@ -126,9 +182,14 @@ class ClockSampler:
     def __enter__(self):
         try:
             import threading
-            import pynvml as nv
-            nv.nvmlInit()
-            self.nv, self.handle = nv, nv.nvmlDeviceGetHandleByIndex(self.index)
+            try:
+                import pynvml as nv
+                nv.nvmlInit()
+            except ImportError:
+                nv = _NvmlC()
+            self.nv = nv
+            self.handle = (nv.nvmlDeviceGetHandleByUUID(self.uuid) if self.uuid
+                           else nv.nvmlDeviceGetHandleByIndex(self.index))
             self.stop = threading.Event()
             self.thread = threading.Thread(target=self._nvml_loop, daemon=True)
             self._sample()  # at the start of the timed region, then every 20 ms and once at its end
@@ -139,7 +200,7 @@ class ClockSampler:
             self.nvml_error = f"{type(exc).__name__}: {exc}"[:120]
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                ["nvidia-smi", "-i", self.uuid or str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -310,7 +371,7 @@ def main():
     torch.cuda.synchronize()
 
     step_ev, screen_ev = [], []
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, gpu_uuid(torch, local)) as clk:
         barrier()
         torch.cuda.synchronize()
         wall0 = time.perf_counter()

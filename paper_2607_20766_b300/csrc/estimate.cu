@@ -517,11 +517,14 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) cross_kernel(const Cr
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WarpTables& T = reinterpret_cast<WarpTables*>(smem_raw)[warp];
   const uint32_t batch = 32u * SP;  // sample pairs per batch
+  // lane 0 holds the next item, taken from the queue while the current one
+  // runs so the atomic's latency is hidden
+  unsigned long long next = 0;
+  if (lane == 0) next = atomicAdd(args.queue, 1ull);
   for (;;) {
-    unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(args.queue, 1ull);
-    item = __shfl_sync(0xffffffffu, item, 0);
+    const unsigned long long item = __shfl_sync(0xffffffffu, next, 0);
     if (item >= (unsigned long long)args.n_items) break;
+    if (lane == 0) next = atomicAdd(args.queue, 1ull);
     int32_t xa, xb;
     int64_t out_idx;
     const float* pose = nullptr;
@@ -559,15 +562,23 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) cross_kernel(const Cr
     uint32_t n_dir;
     if (MODE != kAdaptive) {
       const uint32_t nb = ((args.n + 1u) / 2u + batch - 1u) / batch;
-      stage_direction(T, args.A, MA, nullptr, &args.B, MB, pose, lane, wa, wb);
+      // screens (no poses, both directions): one shared frame when possible
+      const bool shared = MODE == kScreen && stage_pair_frame(T, args.A, MA, args.B, MB, lane, wa, wb);
+      if (shared)
+        stage_samp_in_frame(T, args.A, MA, lane);
+      else
+        stage_direction(T, args.A, MA, nullptr, &args.B, MB, pose, lane, wa, wb);
       for (uint32_t b = 0; b < nb; ++b)
         run_batch<false, SP, kForm, kCV>(T, MA.n, MB.n, b, args.n, args.key, slo, shi, SHP_TAG_AB, args.anti, lane,
                                          sa);
       if (args.symmetric) {
-        stage_direction(T, args.B, MB, pose, &args.A, MA, nullptr, lane, wb, wa);
+        if (shared)
+          stage_samp_in_frame(T, args.B, MB, lane);
+        else
+          stage_direction(T, args.B, MB, pose, &args.A, MA, nullptr, lane, wb, wa);
         for (uint32_t b = 0; b < nb; ++b)
           run_batch<false, SP, kForm, kCV>(T, MB.n, MA.n, b, args.n, args.key, slo, shi, SHP_TAG_BA, args.anti,
-                                           lane, sb);
+                                           lane, sb, shared ? T.y : T.x, shared ? T.x : T.y);
       }
       n_dir = args.n;
     } else {
