@@ -646,11 +646,12 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) self_kernel(const Sel
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WarpTables& T = reinterpret_cast<WarpTables*>(smem_raw)[warp];
   const uint32_t batch = 32u * SP;
+  unsigned long long next = 0;  // the next item, taken while the current one runs
+  if (lane == 0) next = atomicAdd(args.queue, 1ull);
   for (;;) {
-    unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(args.queue, 1ull);
-    item = __shfl_sync(0xffffffffu, item, 0);
+    const unsigned long long item = __shfl_sync(0xffffffffu, next, 0);
     if (item >= (unsigned long long)args.n_items) break;
+    if (lane == 0) next = atomicAdd(args.queue, 1ull);
     const int32_t xm = args.idx ? args.idx[item] : (int32_t)item;
     if (xm < 0 || xm >= args.S.n_mol) {
       if (lane == 0) {
@@ -778,7 +779,7 @@ int launch_cross(int v, const CrossArgs& a, int64_t n_items, cudaStream_t st) {
 }
 
 int launch_self(const SelfArgs& a, int64_t n_items, cudaStream_t st) {
-  using Tr = VariantTraits<1>;  // packed exponent, 4 sample pairs per lane, 8 warps x 2 CTAs
+  using Tr = VariantTraits<8>;  // packed exponent and union product, 4 sample pairs per lane, 8 warps x 2 CTAs
   return launch_persistent(self_kernel<Tr::sp, Tr::form, Tr::warps, Tr::min_blocks>, a, n_items, Tr::warps,
                            Tr::smem, st);
 }
@@ -1155,7 +1156,7 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_volume_kernel(const CVArg
     if (a.target <= 0.f) {
       const uint32_t nb = ((a.n + 1u) / 2u + batch - 1u) / batch;
       for (uint32_t b = 0; b < nb; ++b)
-        run_batch<true, SP, 0, kCV>(T, M.n, 0, b, a.n, a.key, slo, shi, SHP_TAG_SELF, false, lane, st);
+        run_batch<true, SP, 5, kCV>(T, M.n, 0, b, a.n, a.key, slo, shi, SHP_TAG_SELF, false, lane, st);
       n_done = a.n;
     } else {
       const uint32_t cap_b = a.n / (2u * batch);
@@ -1164,7 +1165,7 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_volume_kernel(const CVArg
         const uint32_t nxt = b + a.round_b;
         const uint32_t n_now = nxt * batch * 2u;
         for (uint32_t k = b; k < nxt; ++k)
-          run_batch<true, SP, 0, kCV>(T, M.n, 0, k, n_now, a.key, slo, shi, SHP_TAG_SELF, false, lane, st);
+          run_batch<true, SP, 5, kCV>(T, M.n, 0, k, n_now, a.key, slo, shi, SHP_TAG_SELF, false, lane, st);
         b = nxt;
         if (b >= cap_b) break;
         float h1 = st.hi[0], l1 = st.lo[0], h2 = st.hi[1], l2 = st.lo[1];
