@@ -79,9 +79,14 @@ int shp_version(void);
  *   n_mol         >= 0
  * Builds per molecule the mixture mass Z, the integer alias table of the
  * component probabilities v_i / Z, and a largest-first order used to
- * balance screens. Copies on `stream` and synchronises it before returning.
- * On success *out owns all device memory of the set (free with
- * shape_set_free). Errors: SHP_EINVAL (NULL, non-finite or non-positive
+ * balance screens. Host preparation runs on the host threads (OpenMP);
+ * the device memory is allocated and filled on `stream` (stream-ordered:
+ * work enqueued on `stream` after the call sees the set; other streams must
+ * order themselves after it). The host arrays may be reused as soon as the
+ * call returns (they are copied into one of two library-owned pinned
+ * staging buffers, and a call waits only for the upload made from the same
+ * buffer two calls earlier). On success *out owns all device memory of the
+ * set (free with shape_set_free or shape_set_free_async). Errors: SHP_EINVAL (NULL, non-finite or non-positive
  * values), SHP_ERANGE (atom counts), SHP_ENOMEM, SHP_ECUDA.
  */
 int shape_set_load(const float* xyz_host, const float* radius_host, const float* height_host,
@@ -91,13 +96,22 @@ int shape_set_load(const float* xyz_host, const float* radius_host, const float*
 /* Free a set (NULL is a no-op). Synchronises the device first. */
 int shape_set_free(shp_set s);
 
+/*
+ * Free a set in stream order (NULL is a no-op): its device memory returns to
+ * the pool once the work enqueued on `stream` before this call has run. The
+ * caller guarantees that no work on another stream still uses the set. Does
+ * not synchronise.
+ */
+int shape_set_free_async(shp_set s, void* stream);
+
 /* Sizes of a set; any output may be NULL. */
 int shape_set_info(shp_set s, int32_t* n_mol, int64_t* n_atoms, int32_t* max_atoms);
 
 /*
  * Host copies of the per-molecule mixture masses Z ([n_mol] double) and of
  * the alias tables ([n_atoms] uint32 thresholds, [n_atoms] uint8 aliases,
- * indices local to each molecule). Any output may be NULL.
+ * indices local to each molecule). Any output may be NULL. The tables are
+ * read back from the device (synchronises it).
  */
 int shape_set_tables(shp_set s, double* Z_host, uint32_t* thr_host, uint8_t* alias_host);
 
@@ -397,7 +411,8 @@ int mlp_adam(float* params, float* m, float* v, const float* grad, int64_t n_par
  * Host copy of each molecule's principal frame ([n_mol][12] float: the
  * Gaussian-volume-weighted centroid, then the 3x3 axis matrix row-major with
  * the axes as columns, sorted by decreasing second moment, the first two
- * oriented to a non-negative third moment, det +1).
+ * oriented to a non-negative third moment, det +1), read back from the
+ * device (synchronises it).
  */
 int shape_set_frames(shp_set s, float* frames_host);
 

@@ -22,7 +22,7 @@ TAG_AB, TAG_BA, TAG_SELF = 0, 1, 2
 MAX_ATOMS = 64
 
 # Every entry point declared in include/shape.h.
-EXPORTS = ("shp_last_error", "shp_version", "shape_set_load", "shape_set_free", "shape_set_info",
+EXPORTS = ("shp_last_error", "shp_version", "shape_set_load", "shape_set_free", "shape_set_free_async", "shape_set_info",
            "shape_set_tables", "overlap_estimate", "union_volume_estimate", "fo_overlap",
            "tanimoto_screen", "shp_screen_variants", "shp_screen_variant_info", "tanimoto_screen_tune", "align_crn_points",
            "overlap_pose_grad", "align_rigid", "shape_set_frames", "union_attributions", "union_volume_cv",
@@ -69,6 +69,7 @@ def load_library():
     sig = {
         "shape_set_load": [_P, _P, _P, ctypes.c_double, _P, ctypes.c_int32, _P, _P],
         "shape_set_free": [_P],
+        "shape_set_free_async": [_P, _P],
         "shape_set_info": [_P, _P, _P, _P],
         "shape_set_tables": [_P, _P, _P, _P],
         "overlap_estimate": [_P, _P, _P, _P, ctypes.c_int64, _P, _P, _P, _P, _P],
@@ -153,9 +154,14 @@ class ShapeSet:
         _check(load_library().shape_set_frames(self.handle, out.ctypes.data))
         return out
 
-    def free(self):
+    def free(self, stream=None):
+        """Release the device memory: synchronously, or in stream order on
+        `stream` (no other stream may still use the set)."""
         if self.handle is not None and self.handle.value:
-            load_library().shape_set_free(self.handle)
+            if stream is None:
+                load_library().shape_set_free(self.handle)
+            else:
+                load_library().shape_set_free_async(self.handle, _stream(stream))
         self.handle = None
 
     def __del__(self):
@@ -166,7 +172,9 @@ class ShapeSet:
 
 
 def shape_set_load(ms, c_alpha: float = 2.41798793, stream=None, device=None) -> ShapeSet:
-    """Upload a MolSet (host arrays) to the current CUDA device."""
+    """Upload a MolSet (host arrays) to the current CUDA device, in order on
+    `stream` (default: the current stream); returns once the host arrays
+    have been consumed."""
     if not torch.cuda.is_available():
         raise RuntimeError("shape_set_load needs a CUDA device")
     L = load_library()

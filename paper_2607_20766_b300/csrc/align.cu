@@ -513,6 +513,9 @@ extern "C" int align_rigid(shp_set Q, int32_t iq, shp_set B, const int32_t* ib, 
   if (n_pairs == 0) return SHP_OK;
   if (!ib || !self_q || !self_db || !pose_out || !T_out) { set_error("align_rigid: NULL array"); return SHP_EINVAL; }
   cudaStream_t st = (cudaStream_t)stream;
+  rc = ensure_frames(Q, st);  // the principal-frame starts
+  if (!rc) rc = ensure_frames(B, st);
+  if (rc) return rc;
   const int64_t n_items = n_pairs * cfg->starts;
   float4* pts = nullptr;
   float* poses = nullptr;

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -26,13 +27,12 @@ struct shp_set_s {
   int32_t* order = nullptr;  // [n_mol] molecule ids, atom count descending
   float* radius = nullptr;   // [n_atoms] van der Waals radius (A)
   float* frame = nullptr;    // [n_mol][12] principal frame: centroid (3), axes E (3x3 row-major,
-                             // columns = axes, det +1)
-  // host mirrors
-  std::vector<int32_t> h_off;
+                             // columns = axes, det +1); computed on the device at first use
+  bool frames_ready = false;
+  cudaEvent_t frames_done = nullptr;
+  std::mutex frames_mu;
+  // host mirror of Z (alignment scales its estimates on the host)
   std::vector<double> h_Z;
-  std::vector<uint32_t> h_thr;
-  std::vector<uint8_t> h_alias;
-  std::vector<float> h_frame;
 };
 
 namespace shp {
@@ -49,6 +49,10 @@ struct SetView {
   const float* radius;
   int32_t n_mol;
 };
+
+// Makes the principal frames of s available to work enqueued on `stream`
+// after this call (computes them on the device the first time).
+int ensure_frames(shp_set_s* s, cudaStream_t stream);
 
 inline SetView view(const shp_set_s* s) {
   return SetView{s->atom, s->aux, s->thr, s->alias, s->off, s->Z, s->frame, s->radius, s->n_mol};

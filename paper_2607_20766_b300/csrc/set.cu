@@ -5,7 +5,6 @@
 #include <cstdarg>
 #include <cstring>
 #include <mutex>
-#include <numeric>
 
 #include "internal.h"
 
@@ -65,23 +64,35 @@ static void build_alias(int n, const double* v, uint32_t* thr, uint8_t* alias) {
   for (; lh < lt; ++lh) { thr[lq[lh]] = 0xFFFFFFFFu; alias[lq[lh]] = (uint8_t)lq[lh]; }
 }
 
+// Gaussian volume v_i = p_i (pi/alpha_i)^{3/2} and centre of atom i, from
+// the stored alpha and log2 p (FP64).
+__device__ __forceinline__ double atom_volume(const float4* atom, const float2* aux, int i, double c[3]) {
+  const float4 a = atom[i];
+  c[0] = a.x; c[1] = a.y; c[2] = a.z;
+  const double t = 3.14159265358979323846 / (double)a.w;
+  return exp2((double)aux[i].y) * t * sqrt(t);
+}
+
 // Principal frame of one molecule: centroid weighted by the Gaussian
 // volumes v_i, and the eigenvectors of the weighted second-moment matrix
 // (cyclic Jacobi rotations, FP64) sorted by decreasing eigenvalue; the first
 // two axes point so the weighted third moment of the projection is >= 0, the
 // third completes a proper rotation. out = centroid (3), E row-major (9)
-// with the axes as columns.
-static void principal_frame(int n, const double (*c)[3], const double* v, float* out) {
-  double W = 0.0, cen[3] = {0, 0, 0};
+// with the axes as columns. Computed on the device at first use.
+__device__ void principal_frame(int n, const float4* atom, const float2* aux, float* out) {
+  double W = 0.0, cen[3] = {0, 0, 0}, c[3];
   for (int i = 0; i < n; ++i) {
-    W += v[i];
-    for (int k = 0; k < 3; ++k) cen[k] += v[i] * c[i][k];
+    const double v = atom_volume(atom, aux, i, c);
+    W += v;
+    for (int k = 0; k < 3; ++k) cen[k] += v * c[k];
   }
   for (int k = 0; k < 3; ++k) cen[k] /= W;
   double A[3][3] = {{0}};
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
+    const double v = atom_volume(atom, aux, i, c);
     for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) A[a][b] += v[i] * (c[i][a] - cen[a]) * (c[i][b] - cen[b]);
+      for (int b = 0; b < 3; ++b) A[a][b] += v * (c[a] - cen[a]) * (c[b] - cen[b]);
+  }
   double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
   for (int sweep = 0; sweep < 50; ++sweep) {
     const double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
@@ -91,8 +102,8 @@ static void principal_frame(int n, const double (*c)[3], const double* v, float*
       for (int q = p + 1; q < 3; ++q) {
         if (A[p][q] == 0.0) continue;
         const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-        const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
         for (int k = 0; k < 3; ++k) {  // A <- A J
           const double akp = A[k][p], akq = A[k][q];
           A[k][p] = cs * akp - sn * akq;
@@ -110,15 +121,19 @@ static void principal_frame(int n, const double (*c)[3], const double* v, float*
         }
       }
   }
-  int ord[3] = {0, 1, 2};
-  std::sort(ord, ord + 3, [&](int a, int b) { return A[a][a] > A[b][b]; });
+  int ord[3] = {0, 1, 2};  // axes by decreasing second moment (stable)
+  for (int i = 1; i < 3; ++i)
+    for (int j = i; j > 0 && A[ord[j]][ord[j]] > A[ord[j - 1]][ord[j - 1]]; --j) {
+      const int t = ord[j]; ord[j] = ord[j - 1]; ord[j - 1] = t;
+    }
   double E[3][3];
   for (int a = 0; a < 2; ++a) {
     double skew = 0.0;
     for (int i = 0; i < n; ++i) {
+      const double v = atom_volume(atom, aux, i, c);
       double pr = 0.0;
-      for (int k = 0; k < 3; ++k) pr += (c[i][k] - cen[k]) * V[k][ord[a]];
-      skew += v[i] * pr * pr * pr;
+      for (int k = 0; k < 3; ++k) pr += (c[k] - cen[k]) * V[k][ord[a]];
+      skew += v * pr * pr * pr;
     }
     const double sg = skew < 0 ? -1.0 : 1.0;
     for (int k = 0; k < 3; ++k) E[k][a] = sg * V[k][ord[a]];
@@ -131,8 +146,20 @@ static void principal_frame(int n, const double (*c)[3], const double* v, float*
     for (int b = 0; b < 3; ++b) out[3 + 3 * a + b] = (float)E[a][b];
 }
 
-// All device arrays of a set live in one allocation, filled by one copy from
-// a pinned staging buffer that the library keeps (and grows) across loads.
+// One thread per molecule.
+__global__ void frames_kernel(const float4* __restrict__ atom, const float2* __restrict__ aux,
+                              const int32_t* __restrict__ off, int32_t n_mol, float* __restrict__ frame) {
+  const int32_t m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_mol) return;
+  const int32_t a0 = off[m];
+  principal_frame(off[m + 1] - a0, atom + a0, aux + a0, frame + 12 * (size_t)m);
+}
+
+// All device arrays of a set live in one stream-ordered allocation, filled
+// by one copy from one of two pinned staging buffers that the library keeps
+// (and grows) across loads; each buffer's event marks the end of its last
+// upload, so a load waits only for the upload two loads back, never for the
+// caller's kernels.
 struct SetLayout {
   size_t atom, aux, radius, thr, alias, off, Z, order, frame, total;
 };
@@ -155,29 +182,69 @@ static SetLayout set_layout(int64_t n_atoms, int32_t n_mol) {
   return L;
 }
 
+struct StageBuf {
+  void* ptr = nullptr;
+  size_t cap = 0;
+  cudaEvent_t done = nullptr;  // recorded after the buffer's last upload
+};
 static std::mutex g_stage_mu;
-static void* g_stage = nullptr;
-static size_t g_stage_cap = 0;
+static StageBuf g_stage[2];
+static int g_stage_next = 0;
 
+// A staging buffer of at least `bytes`, its previous upload finished.
 // Caller holds g_stage_mu.
-static int stage_buffer(size_t bytes, unsigned char** out) {
-  if (bytes > g_stage_cap) {
-    if (g_stage) cudaFreeHost(g_stage);
-    g_stage = nullptr;
-    g_stage_cap = 0;
+static int stage_buffer(size_t bytes, StageBuf** out) {
+  StageBuf& b = g_stage[g_stage_next];
+  g_stage_next ^= 1;
+  if (!b.done) SHP_CUDA(cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming));
+  SHP_CUDA(cudaEventSynchronize(b.done));
+  if (bytes > b.cap) {
+    if (b.ptr) cudaFreeHost(b.ptr);
+    b.ptr = nullptr;
+    b.cap = 0;
     const size_t cap = bytes + bytes / 4;
-    SHP_CUDA(cudaMallocHost(&g_stage, cap));
-    g_stage_cap = cap;
+    SHP_CUDA(cudaMallocHost(&b.ptr, cap));
+    b.cap = cap;
   }
-  *out = static_cast<unsigned char*>(g_stage);
+  *out = &b;
   return SHP_OK;
 }
 
-static void free_set_memory(shp_set_s* s) {
-  cudaFree(s->dbase);
+// Stable order of molecule ids by atom count, descending (counting sort).
+static void order_by_size(const int32_t* offsets, int32_t n_mol, int32_t* order) {
+  int64_t start[SHP_MAX_ATOMS + 2] = {0};
+  for (int32_t m = 0; m < n_mol; ++m) ++start[SHP_MAX_ATOMS - (offsets[m + 1] - offsets[m]) + 1];
+  for (int k = 1; k <= SHP_MAX_ATOMS + 1; ++k) start[k] += start[k - 1];
+  for (int32_t m = 0; m < n_mol; ++m) order[start[SHP_MAX_ATOMS - (offsets[m + 1] - offsets[m])]++] = m;
+}
+
+// Stream-ordered free (the set's memory comes from cudaMallocAsync); callers
+// that free synchronously have synchronised the device first.
+static void free_set_memory(shp_set_s* s, cudaStream_t stream = nullptr) {
+  if (s->dbase) cudaFreeAsync(s->dbase, stream);
+  if (s->frames_done) cudaEventDestroy(s->frames_done);
+  s->frames_done = nullptr;
   s->dbase = nullptr;
   s->atom = nullptr; s->aux = nullptr; s->thr = nullptr; s->alias = nullptr;
   s->off = nullptr; s->Z = nullptr; s->order = nullptr; s->frame = nullptr; s->radius = nullptr;
+}
+
+int ensure_frames(shp_set_s* s, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lk(s->frames_mu);
+  if (!s->frames_ready) {
+    if (s->n_mol > 0) {
+      if (!s->frames_done) SHP_CUDA(cudaEventCreateWithFlags(&s->frames_done, cudaEventDisableTiming));
+      const int threads = 128;
+      frames_kernel<<<(s->n_mol + threads - 1) / threads, threads, 0, stream>>>(s->atom, s->aux, s->off, s->n_mol,
+                                                                               s->frame);
+      SHP_CUDA(cudaGetLastError());
+      SHP_CUDA(cudaEventRecord(s->frames_done, stream));
+    }
+    s->frames_ready = true;
+    return SHP_OK;
+  }
+  if (s->frames_done) SHP_CUDA(cudaStreamWaitEvent(stream, s->frames_done, 0));
+  return SHP_OK;
 }
 
 }  // namespace shp
@@ -218,26 +285,26 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
   s->n_mol = n_mol;
   s->n_atoms = n_atoms;
   s->max_atoms = max_atoms;
-  s->h_off.assign(offsets, offsets + n_mol + 1);
   s->h_Z.assign(n_mol, 0.0);
-  s->h_thr.assign(n_atoms, 0u);
-  s->h_alias.assign(n_atoms, 0);
-  s->h_frame.assign(12 * (size_t)n_mol, 0.f);
   const SetLayout L = set_layout(n_atoms, n_mol);
   std::lock_guard<std::mutex> stage_lock(g_stage_mu);
-  unsigned char* hb = nullptr;
-  int rc = stage_buffer(L.total, &hb);
+  StageBuf* sb = nullptr;
+  int rc = stage_buffer(L.total, &sb);
   if (rc) { delete s; return rc; }
+  unsigned char* hb = static_cast<unsigned char*>(sb->ptr);
   float4* atom = reinterpret_cast<float4*>(hb + L.atom);
   float2* aux = reinterpret_cast<float2*>(hb + L.aux);
-  std::memcpy(hb + L.radius, radius, sizeof(float) * n_atoms);
-  // per-molecule preparation, molecules in parallel
+  float* rad = reinterpret_cast<float*>(hb + L.radius);
+  uint32_t* thr = reinterpret_cast<uint32_t*>(hb + L.thr);
+  uint8_t* alias = hb + L.alias;
+  double* Zs = reinterpret_cast<double*>(hb + L.Z);
+  // per-molecule preparation, molecules in parallel, written straight into
+  // the staging buffer
   int32_t bad_mol = -1;
 #pragma omp parallel for schedule(dynamic, 256)
   for (int32_t m = 0; m < n_mol; ++m) {
     const int32_t a0 = offsets[m], n = offsets[m + 1] - a0;
     double v[SHP_MAX_ATOMS];
-    double cd[SHP_MAX_ATOMS][3];
     double Z = 0.0;
     bool ok = true;
     for (int i = 0; i < n; ++i) {
@@ -255,8 +322,8 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
       v[i] = p * t * std::sqrt(t);
       Z += v[i];
       atom[a] = make_float4((float)x, (float)y, (float)z, (float)alpha);
-      cd[i][0] = (float)x; cd[i][1] = (float)y; cd[i][2] = (float)z;
       aux[a] = make_float2((float)(1.0 / std::sqrt(2.0 * alpha)), (float)std::log2(p));
+      rad[a] = radius[a];
     }
     if (!ok) {
 #pragma omp critical
@@ -264,28 +331,20 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
       continue;
     }
     s->h_Z[m] = Z;
-    build_alias(n, v, &s->h_thr[a0], &s->h_alias[a0]);
-    principal_frame(n, cd, v, &s->h_frame[12 * (size_t)m]);
+    Zs[m] = Z;
+    build_alias(n, v, thr + a0, alias + a0);
   }
   if (bad_mol >= 0) {
     set_error("shape_set_load: molecule %d has a non-finite or non-positive coordinate, radius or height", bad_mol);
     delete s;
     return SHP_EINVAL;
   }
-  int32_t* order = reinterpret_cast<int32_t*>(hb + L.order);
-  std::iota(order, order + n_mol, 0);
-  std::stable_sort(order, order + n_mol, [&](int32_t a, int32_t b) {
-    return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
-  });
-  std::memcpy(hb + L.thr, s->h_thr.data(), sizeof(uint32_t) * n_atoms);
-  std::memcpy(hb + L.alias, s->h_alias.data(), n_atoms);
-  std::memcpy(hb + L.off, s->h_off.data(), sizeof(int32_t) * (n_mol + 1));
-  std::memcpy(hb + L.Z, s->h_Z.data(), sizeof(double) * n_mol);
-  std::memcpy(hb + L.frame, s->h_frame.data(), sizeof(float) * 12 * n_mol);
+  order_by_size(offsets, n_mol, reinterpret_cast<int32_t*>(hb + L.order));
+  std::memcpy(hb + L.off, offsets, sizeof(int32_t) * (n_mol + 1));
   cudaStream_t st = (cudaStream_t)stream;
   unsigned char* db = nullptr;
-  cudaError_t e = cudaMalloc((void**)&db, L.total);
-  if (e != cudaSuccess) { delete s; return cuda_fail(e, "shape_set_load: cudaMalloc"); }
+  cudaError_t e = cudaMallocAsync((void**)&db, L.total, st);
+  if (e != cudaSuccess) { delete s; return cuda_fail(e, "shape_set_load: cudaMallocAsync"); }
   s->dbase = db;
   s->atom = reinterpret_cast<float4*>(db + L.atom);
   s->aux = reinterpret_cast<float2*>(db + L.aux);
@@ -296,11 +355,12 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
   s->Z = reinterpret_cast<double*>(db + L.Z);
   s->order = reinterpret_cast<int32_t*>(db + L.order);
   s->frame = reinterpret_cast<float*>(db + L.frame);
-  e = cudaMemcpyAsync(db, hb, L.total, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the staging buffer is reused by the next load
+  e = cudaMemcpyAsync(db, hb, L.frame, cudaMemcpyHostToDevice, st);  // the frames (last) are computed on demand
+  if (e == cudaSuccess) e = cudaEventRecord(sb->done, st);
   if (e != cudaSuccess) {
     rc = cuda_fail(e, "shape_set_load: upload");
-    free_set_memory(s);
+    cudaStreamSynchronize(st);
+    free_set_memory(s, st);
     delete s;
     return rc;
   }
@@ -321,6 +381,18 @@ extern "C" int shape_set_free(shp_set s) {
   return SHP_OK;
 }
 
+extern "C" int shape_set_free_async(shp_set s, void* stream) {
+  clear_error();
+  if (!s) return SHP_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != s->device) cudaSetDevice(s->device);
+  free_set_memory(s, (cudaStream_t)stream);
+  if (prev != s->device) cudaSetDevice(prev);
+  delete s;
+  return SHP_OK;
+}
+
 extern "C" int shape_set_info(shp_set s, int32_t* n_mol, int64_t* n_atoms, int32_t* max_atoms) {
   clear_error();
   if (!s) { set_error("shape_set_info: NULL set"); return SHP_EINVAL; }
@@ -334,14 +406,22 @@ extern "C" int shape_set_tables(shp_set s, double* Z, uint32_t* thr, uint8_t* al
   clear_error();
   if (!s) { set_error("shape_set_tables: NULL set"); return SHP_EINVAL; }
   if (Z && s->n_mol) std::memcpy(Z, s->h_Z.data(), sizeof(double) * s->n_mol);
-  if (thr && s->n_atoms) std::memcpy(thr, s->h_thr.data(), sizeof(uint32_t) * s->n_atoms);
-  if (alias && s->n_atoms) std::memcpy(alias, s->h_alias.data(), s->n_atoms);
+  if ((thr || alias) && s->n_atoms) {
+    SHP_CUDA(cudaDeviceSynchronize());
+    if (thr) SHP_CUDA(cudaMemcpy(thr, s->thr, sizeof(uint32_t) * s->n_atoms, cudaMemcpyDeviceToHost));
+    if (alias) SHP_CUDA(cudaMemcpy(alias, s->alias, s->n_atoms, cudaMemcpyDeviceToHost));
+  }
   return SHP_OK;
 }
 
 extern "C" int shape_set_frames(shp_set s, float* frames) {
   clear_error();
   if (!s || !frames) { set_error("shape_set_frames: NULL argument"); return SHP_EINVAL; }
-  if (s->n_mol) std::memcpy(frames, s->h_frame.data(), sizeof(float) * 12 * (size_t)s->n_mol);
+  if (s->n_mol) {
+    const int rc = ensure_frames(s, nullptr);
+    if (rc) return rc;
+    SHP_CUDA(cudaDeviceSynchronize());
+    SHP_CUDA(cudaMemcpy(frames, s->frame, sizeof(float) * 12 * (size_t)s->n_mol, cudaMemcpyDeviceToHost));
+  }
   return SHP_OK;
 }
