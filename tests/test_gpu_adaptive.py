@@ -141,13 +141,16 @@ def test_tuner_picks_a_valid_variant(small_screen):
 def test_adaptive_full_size_sampled():
     """16 queries (20-48 atoms) x 1,000,000 molecules (18-60, heavy-tailed
     toward 40), rounds of 256, SE(T) <= 0.005 or 65,536 per direction: the
-    launch the benchmark times; 24 sampled pairs checked by the oracle."""
+    launch the benchmark times (autotuned variant, replayed CUDA graph); 24
+    sampled pairs checked by the oracle."""
     q, d = synth.adaptive_screen()
     Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
     selfq = shp.self_overlaps(Sq, seed=11, n_samples=4096, stream_base=0)
     selfd = shp.self_overlaps(Sd, seed=11, n_samples=4096, stream_base=16)
-    res = shp.tanimoto_screen(Sq, Sd, selfq, selfd, seed=77, tau=0.005, round=256, min_n=1024, cap=65536,
-                              with_overlaps=True)
+    shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=16384, tau=0.005, cap=65536)
+    g = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, selfq, selfd, seed=77, tau=0.005, round=256, min_n=1024,
+                      cap=65536, with_overlaps=True)
+    res = g.replay()
     torch.cuda.synchronize()
     nu = res["n_used"].cpu().numpy()
     assert np.all(nu % 256 == 0) and nu.min() >= 1024 and nu.max() <= 65536

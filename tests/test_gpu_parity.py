@@ -143,13 +143,19 @@ def test_screen_parity_small():
 def test_screen_full_size_sampled():
     """The fixed-budget screen at its full size (1 query of 32 atoms x
     100,000 molecules of 18-60 atoms, 4096 samples per direction), in the
-    launch configuration the benchmark times; 40 sampled pairs and 24
-    sampled self-overlaps recomputed by the oracle one by one."""
+    launch configuration the benchmark times (autotuned variant, replayed
+    CUDA graphs); 40 sampled pairs and 24 sampled self-overlaps recomputed
+    by the oracle one by one."""
     q, d = synth.fixed_screen(n_db=100_000)
     Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
-    selfq = shp.self_overlaps(Sq, seed=1, n_samples=4096, stream_base=0)
-    selfd = shp.self_overlaps(Sd, seed=1, n_samples=4096, stream_base=1)
-    res = shp.tanimoto_screen(Sq, Sd, selfq, selfd, seed=2026, n_fixed=4096, with_overlaps=True)
+    g_self = shp.StepGraph(lambda: (shp.self_overlaps(Sq, seed=1, n_samples=4096, stream_base=0),
+                                    shp.self_overlaps(Sd, seed=1, n_samples=4096, stream_base=1)))
+    selfq, selfd = g_self.replay()
+    shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=2026, n_fixed=4096, n_sample=8192)
+    g_screen = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, selfq, selfd, seed=2026, n_fixed=4096,
+                             with_overlaps=True)
+    g_self.replay()
+    res = g_screen.replay()
     torch.cuda.synchronize()
     rng = np.random.default_rng(0)
     pick = rng.choice(d.n_mol, 40, replace=False)
