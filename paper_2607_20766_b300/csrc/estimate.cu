@@ -510,6 +510,31 @@ __device__ __forceinline__ float watched_se_t(const CrossArgs& args, const DirSt
   return fabsf(S / (den * den)) * seO;
 }
 
+// Stages direction dir of a pair (0: A sampled and B evaluated, 1: the
+// reverse; the pose, if any, moves B) and runs its batches [b0, b1) into the
+// direction's running sums. With a shared frame (both coefficient tables
+// already staged, A in x and B in y) only the component table is restaged.
+template <int SP, int kForm, bool kCV>
+__device__ __forceinline__ void run_direction(WarpTables& T, const CrossArgs& args, int dir, bool shared, MolRef MA,
+                                              MolRef MB, const float* pose, const float* wa, const float* wb,
+                                              uint32_t b0, uint32_t b1, uint32_t n, bool anti, uint32_t slo,
+                                              uint32_t shi, int lane) {
+  const SetView& SX = dir ? args.B : args.A;
+  const SetView& SY = dir ? args.A : args.B;
+  const MolRef MX = dir ? MB : MA, MY = dir ? MA : MB;
+  if (shared)
+    stage_samp_in_frame(T, SX, MX, lane);
+  else
+    stage_direction(T, SX, MX, dir ? pose : nullptr, &SY, MY, dir ? nullptr : pose, lane, dir ? wb : wa,
+                    dir ? wa : wb);
+  const CoefT* tx = (shared && dir) ? T.y : T.x;
+  const CoefT* ty = (shared && dir) ? T.x : T.y;
+  DirState& st = T.st[dir][lane];
+  for (uint32_t k = b0; k < b1; ++k)
+    run_batch<false, SP, kForm, kCV>(T, MX.n, MY.n, k, n, args.key, slo, shi, dir ? SHP_TAG_BA : SHP_TAG_AB, anti,
+                                     lane, st, tx, ty);
+}
+
 // kCV (screen modes): union slot with the weighted-Gaussian control variate.
 template <int MODE, int SP, int kForm, int kWarps, int kMinBlocks, bool kCV = false>
 __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) cross_kernel(const CrossArgs args) {
@@ -560,26 +585,17 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) cross_kernel(const Cr
     const float* wb = kCV ? args.omega_b : nullptr;
     const double Ccv = kCV ? weighted_fo(args.A, MA, wa, args.B, MB, wb, lane) : 0.0;
     uint32_t n_dir;
+    // one inlined copy of the evaluation serves both directions (a loop, not
+    // two copies: the adaptive rounds alternate directions every batch)
     if (MODE != kAdaptive) {
       const uint32_t nb = ((args.n + 1u) / 2u + batch - 1u) / batch;
       // screens (no poses, both directions): one shared frame when possible
       const bool shared = MODE == kScreen && stage_pair_frame(T, args.A, MA, args.B, MB, lane, wa, wb);
-      if (shared)
-        stage_samp_in_frame(T, args.A, MA, lane);
-      else
-        stage_direction(T, args.A, MA, nullptr, &args.B, MB, pose, lane, wa, wb);
-      for (uint32_t b = 0; b < nb; ++b)
-        run_batch<false, SP, kForm, kCV>(T, MA.n, MB.n, b, args.n, args.key, slo, shi, SHP_TAG_AB, args.anti, lane,
-                                         sa);
-      if (args.symmetric) {
-        if (shared)
-          stage_samp_in_frame(T, args.B, MB, lane);
-        else
-          stage_direction(T, args.B, MB, pose, &args.A, MA, nullptr, lane, wb, wa);
-        for (uint32_t b = 0; b < nb; ++b)
-          run_batch<false, SP, kForm, kCV>(T, MB.n, MA.n, b, args.n, args.key, slo, shi, SHP_TAG_BA, args.anti,
-                                           lane, sb, shared ? T.y : T.x, shared ? T.x : T.y);
-      }
+      const int ndir = args.symmetric ? 2 : 1;
+#pragma unroll 1
+      for (int dir = 0; dir < ndir; ++dir)
+        run_direction<SP, kForm, kCV>(T, args, dir, shared, MA, MB, pose, wa, wb, 0, nb, args.n, args.anti, slo, shi,
+                                      lane);
       n_dir = args.n;
     } else {
       // rounds of round_b batches per direction until SE(T) <= tau or cap;
@@ -590,19 +606,10 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) cross_kernel(const Cr
       for (;;) {
         const uint32_t nxt = b + args.round_b;
         const uint32_t n_now = nxt * batch * 2u;
-        if (shared)
-          stage_samp_in_frame(T, args.A, MA, lane);
-        else
-          stage_direction(T, args.A, MA, nullptr, &args.B, MB, nullptr, lane, wa, wb);
-        for (uint32_t k = b; k < nxt; ++k)
-          run_batch<false, SP, kForm, kCV>(T, MA.n, MB.n, k, n_now, args.key, slo, shi, SHP_TAG_AB, false, lane, sa);
-        if (shared)
-          stage_samp_in_frame(T, args.B, MB, lane);
-        else
-          stage_direction(T, args.B, MB, nullptr, &args.A, MA, nullptr, lane, wb, wa);
-        for (uint32_t k = b; k < nxt; ++k)
-          run_batch<false, SP, kForm, kCV>(T, MB.n, MA.n, k, n_now, args.key, slo, shi, SHP_TAG_BA, false, lane, sb,
-                                           shared ? T.y : T.x, shared ? T.x : T.y);
+#pragma unroll 1
+        for (int dir = 0; dir < 2; ++dir)
+          run_direction<SP, kForm, kCV>(T, args, dir, shared, MA, MB, nullptr, wa, wb, b, nxt, n_now, false, slo, shi,
+                                        lane);
         b = nxt;
         if (b >= args.cap_b) break;
         if (b >= args.min_b) {
