@@ -410,7 +410,7 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        e2e = end_to_end(shp, torch, q, d, n, steps=max(2, min(args.steps, 5)), warmup=1)
+        e2e = end_to_end(shp, torch, q, d, n, steps=max(2, args.steps), warmup=max(3, args.warmup))
 
     cvres, net = None, None
     if args.cv_train > 0:
@@ -695,7 +695,7 @@ def end_to_end(shp, torch, q, d, n, steps: int, warmup: int):
             prev = done
         prev.synchronize()
 
-    run(max(1, warmup))
+    run(warmup)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     run(steps)

@@ -80,9 +80,11 @@ int shp_version(void);
  * Builds per molecule the mixture mass Z, the integer alias table of the
  * component probabilities v_i / Z, and a largest-first order used to
  * balance screens. Host preparation runs on the host threads (OpenMP);
- * the device memory is allocated and filled on `stream` (stream-ordered:
- * work enqueued on `stream` after the call sees the set; other streams must
- * order themselves after it). The host arrays may be reused as soon as the
+ * the device memory is allocated and filled on a library-owned upload
+ * stream and `stream` is made to wait for the upload (work enqueued on
+ * `stream` after the call sees the set, while kernels already queued on it
+ * overlap the copy; other streams must order themselves after `stream`).
+ * Not capturable into a CUDA graph. The host arrays may be reused as soon as the
  * call returns (they are copied into one of two library-owned pinned
  * staging buffers, and a call waits only for the upload made from the same
  * buffer two calls earlier). On success *out owns all device memory of the

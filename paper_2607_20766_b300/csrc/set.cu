@@ -190,6 +190,16 @@ struct StageBuf {
 static std::mutex g_stage_mu;
 static StageBuf g_stage[2];
 static int g_stage_next = 0;
+static cudaStream_t g_copy_stream[64];  // per device: uploads overlap the caller's kernels
+
+// The library's upload stream of device `dev` (non-blocking, created once).
+// Caller holds g_stage_mu.
+static int copy_stream(int dev, cudaStream_t* out) {
+  if (dev < 0 || dev >= 64) { *out = nullptr; return SHP_OK; }
+  if (!g_copy_stream[dev]) SHP_CUDA(cudaStreamCreateWithFlags(&g_copy_stream[dev], cudaStreamNonBlocking));
+  *out = g_copy_stream[dev];
+  return SHP_OK;
+}
 
 // A staging buffer of at least `bytes`, its previous upload finished.
 // Caller holds g_stage_mu.
@@ -341,9 +351,15 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
   }
   order_by_size(offsets, n_mol, reinterpret_cast<int32_t*>(hb + L.order));
   std::memcpy(hb + L.off, offsets, sizeof(int32_t) * (n_mol + 1));
-  cudaStream_t st = (cudaStream_t)stream;
+  // allocate and upload on the library's copy stream, then order the
+  // caller's stream after the upload: the copy overlaps kernels already
+  // queued on the caller's stream
+  cudaStream_t st = (cudaStream_t)stream, cs = nullptr;
+  rc = copy_stream(s->device, &cs);
+  if (rc) { delete s; return rc; }
+  if (!cs) cs = st;
   unsigned char* db = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&db, L.total, st);
+  cudaError_t e = cudaMallocAsync((void**)&db, L.total, cs);
   if (e != cudaSuccess) { delete s; return cuda_fail(e, "shape_set_load: cudaMallocAsync"); }
   s->dbase = db;
   s->atom = reinterpret_cast<float4*>(db + L.atom);
@@ -355,12 +371,13 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
   s->Z = reinterpret_cast<double*>(db + L.Z);
   s->order = reinterpret_cast<int32_t*>(db + L.order);
   s->frame = reinterpret_cast<float*>(db + L.frame);
-  e = cudaMemcpyAsync(db, hb, L.frame, cudaMemcpyHostToDevice, st);  // the frames (last) are computed on demand
-  if (e == cudaSuccess) e = cudaEventRecord(sb->done, st);
+  e = cudaMemcpyAsync(db, hb, L.frame, cudaMemcpyHostToDevice, cs);  // the frames (last) are computed on demand
+  if (e == cudaSuccess) e = cudaEventRecord(sb->done, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, sb->done, 0);
   if (e != cudaSuccess) {
     rc = cuda_fail(e, "shape_set_load: upload");
-    cudaStreamSynchronize(st);
-    free_set_memory(s, st);
+    cudaStreamSynchronize(cs);
+    free_set_memory(s, cs);
     delete s;
     return rc;
   }
