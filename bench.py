@@ -288,16 +288,18 @@ def reference_arm(args):
     q, d = workload(args.n_db, 0)
     total_steps = args.steps + args.warmup
     per_step = args.ref_seconds or max(2.0, min(15.0, 150.0 / max(total_steps, 1)))
-    rates, info = [], None
+    rates, secs, info = [], [], None
     for s in range(total_steps):
         r, info = cpu_oracle_rate(q, d, N_SAMPLES, per_step, rng_seed=s)
         if s >= args.warmup:
             rates.append(r)
+            secs.append(info["seconds"])
     value = float(np.mean(rates))
     pair_evals = 2 * N_SAMPLES * (N_QUERY_ATOMS + float(d.counts.mean())) + N_SAMPLES * float(d.counts.mean())
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"fixed-budget screen, 1 query ({N_QUERY_ATOMS} atoms) x {args.n_db} molecules "
                                f"(18-60 atoms), {N_SAMPLES} samples per direction per pair, FO + union Tanimoto",
