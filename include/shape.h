@@ -69,6 +69,15 @@ const char* shp_last_error(void);
 int shp_version(void);
 
 /*
+ * Test hook: the next `count` device allocations made by library calls fail
+ * as out of memory (the call returns SHP_ENOMEM with a message, having
+ * released what it had allocated) without calling CUDA; 0 clears the hook.
+ * Lets callers exercise their error paths on the host. SHP_EINVAL for a
+ * negative count.
+ */
+int shp_fail_next_allocations(int32_t count);
+
+/*
  * Load n_mol molecules into device memory (Eq. occ, Eq. expectation).
  *   xyz_host      [n_atoms][3] float, Angstrom (n_atoms = offsets_host[n_mol])
  *   radius_host   [n_atoms] float > 0, Angstrom

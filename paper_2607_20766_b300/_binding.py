@@ -22,7 +22,7 @@ TAG_AB, TAG_BA, TAG_SELF = 0, 1, 2
 MAX_ATOMS = 64
 
 # Every entry point declared in include/shape.h.
-EXPORTS = ("shp_last_error", "shp_version", "shape_set_load", "shape_set_free", "shape_set_free_async", "shape_set_info",
+EXPORTS = ("shp_last_error", "shp_version", "shp_fail_next_allocations", "shape_set_load", "shape_set_free", "shape_set_free_async", "shape_set_info",
            "shape_set_tables", "overlap_estimate", "union_volume_estimate", "fo_overlap",
            "tanimoto_screen", "shp_screen_variants", "shp_screen_variant_info", "tanimoto_screen_tune", "align_crn_points",
            "overlap_pose_grad", "align_rigid", "shape_set_frames", "union_attributions", "union_volume_cv",
@@ -68,6 +68,7 @@ def load_library():
     L.shp_version.restype = ctypes.c_int
     sig = {
         "shape_set_load": [_P, _P, _P, ctypes.c_double, _P, ctypes.c_int32, _P, _P],
+        "shp_fail_next_allocations": [ctypes.c_int32],
         "shape_set_free": [_P],
         "shape_set_free_async": [_P, _P],
         "shape_set_info": [_P, _P, _P, _P],
@@ -285,6 +286,12 @@ def tanimoto_screen(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: tor
                                           _dptr(out["T"]), _dptr(out["seT"]), _dptr(out.get("O")),
                                           _dptr(out.get("seO")), _dptr(out.get("n_used")), _stream(stream)))
     return out
+
+
+def fail_next_allocations(count: int) -> None:
+    """Test hook: the next `count` device allocations of library calls fail
+    as out of memory (0 clears)."""
+    _check(load_library().shp_fail_next_allocations(count))
 
 
 def screen_variants() -> int:

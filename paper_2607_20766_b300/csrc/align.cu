@@ -526,17 +526,18 @@ extern "C" int align_rigid(shp_set Q, int32_t iq, shp_set B, const int32_t* ib, 
   double* se = nullptr;
   unsigned long long* queue = nullptr;
   auto release = [&]() {
-    cudaFreeAsync(pts, st); cudaFreeAsync(poses, st); cudaFreeAsync(values, st); cudaFreeAsync(ia2, st);
-    cudaFreeAsync(ib2, st); cudaFreeAsync(est, st); cudaFreeAsync(se, st); cudaFreeAsync(queue, st);
+    for (void* p : {(void*)pts, (void*)poses, (void*)values, (void*)ia2, (void*)ib2, (void*)est, (void*)se,
+                    (void*)queue})
+      if (p) cudaFreeAsync(p, st);
   };
-  cudaError_t e = cudaMallocAsync((void**)&pts, sizeof(float4) * cfg->n_crn, st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&poses, sizeof(float) * 7 * n_items, st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&values, sizeof(float) * n_items, st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&ia2, sizeof(int32_t) * n_items, st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&ib2, sizeof(int32_t) * n_items, st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&est, sizeof(double) * 2 * n_items, st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&se, sizeof(double) * 2 * n_items, st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&queue, sizeof(unsigned long long), st);
+  cudaError_t e = dev_alloc((void**)&pts, sizeof(float4) * cfg->n_crn, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&poses, sizeof(float) * 7 * n_items, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&values, sizeof(float) * n_items, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&ia2, sizeof(int32_t) * n_items, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&ib2, sizeof(int32_t) * n_items, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&est, sizeof(double) * 2 * n_items, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&se, sizeof(double) * 2 * n_items, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&queue, sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) { release(); return cuda_fail(e, "align_rigid: scratch"); }
   shp_mc mc{cfg->seed, cfg->stream, cfg->n_crn, 0u};

@@ -748,7 +748,7 @@ int launch_persistent(Kernel k, Args args, int64_t n_items, int warps, size_t sm
   if (need < g) g = need;
   const int grid = (int)(g < 1 ? 1 : g);
   unsigned long long* q = queue_in;
-  if (!q) SHP_CUDA(cudaMallocAsync((void**)&q, sizeof(unsigned long long), st));
+  if (!q) SHP_CUDA(dev_alloc((void**)&q, sizeof(unsigned long long), st));
   cudaError_t e = cudaMemsetAsync(q, 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess) {
     args.queue = q;

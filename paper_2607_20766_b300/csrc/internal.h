@@ -50,6 +50,11 @@ struct SetView {
   int32_t n_mol;
 };
 
+// Stream-ordered device allocation used by every library call; fails with
+// cudaErrorMemoryAllocation, without calling CUDA, while the test hook of
+// shp_fail_next_allocations has failures pending.
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t stream);
+
 // Makes the principal frames of s available to work enqueued on `stream`
 // after this call (computes them on the device the first time).
 int ensure_frames(shp_set_s* s, cudaStream_t stream);

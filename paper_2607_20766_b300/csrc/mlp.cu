@@ -249,7 +249,7 @@ extern "C" int mlp_loss_grad(const float* params, const float* x, const float* t
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t blocks = (n + kBwdAtoms - 1) / kBwdAtoms;
   float* part = nullptr;
-  SHP_CUDA(cudaMallocAsync((void**)&part, sizeof(float) * (size_t)blocks * (kP + 1), st));
+  SHP_CUDA(dev_alloc((void**)&part, sizeof(float) * (size_t)blocks * (kP + 1), st));
   cudaError_t e = cudaFuncSetAttribute(backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(BwdSmem));
   if (e == cudaSuccess) {

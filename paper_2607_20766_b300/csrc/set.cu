@@ -1,6 +1,7 @@
 // Molecule sets: validation, per-atom parameters, mixture masses and alias
 // tables (Eq. occ, Eq. expectation), device upload. Host code.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -239,6 +240,19 @@ static void free_set_memory(shp_set_s* s, cudaStream_t stream = nullptr) {
   s->off = nullptr; s->Z = nullptr; s->order = nullptr; s->frame = nullptr; s->radius = nullptr;
 }
 
+static std::atomic<int32_t> g_fail_allocs{0};
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t stream) {
+  int32_t pending = g_fail_allocs.load();
+  while (pending > 0) {
+    if (g_fail_allocs.compare_exchange_weak(pending, pending - 1)) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+  }
+  return cudaMallocAsync(p, bytes, stream);
+}
+
 int ensure_frames(shp_set_s* s, cudaStream_t stream) {
   std::lock_guard<std::mutex> lk(s->frames_mu);
   if (!s->frames_ready) {
@@ -264,6 +278,13 @@ using namespace shp;
 extern "C" const char* shp_last_error(void) { return g_err.c_str(); }
 
 extern "C" int shp_version(void) { return 3; }
+
+extern "C" int shp_fail_next_allocations(int32_t count) {
+  clear_error();
+  if (count < 0) { set_error("shp_fail_next_allocations: negative count"); return SHP_EINVAL; }
+  g_fail_allocs.store(count);
+  return SHP_OK;
+}
 
 extern "C" int shape_set_load(const float* xyz, const float* radius, const float* height,
                               double c_alpha, const int32_t* offsets, int32_t n_mol, void* stream,
@@ -359,8 +380,8 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
   if (rc) { delete s; return rc; }
   if (!cs) cs = st;
   unsigned char* db = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&db, L.total, cs);
-  if (e != cudaSuccess) { delete s; return cuda_fail(e, "shape_set_load: cudaMallocAsync"); }
+  cudaError_t e = dev_alloc((void**)&db, L.total, cs);
+  if (e != cudaSuccess) { delete s; return cuda_fail(e, "shape_set_load: device allocation"); }
   s->dbase = db;
   s->atom = reinterpret_cast<float4*>(db + L.atom);
   s->aux = reinterpret_cast<float2*>(db + L.aux);

@@ -56,4 +56,7 @@ def test_null_and_bad_arguments_rejected(lib):
     zero = (ctypes.c_int32 * 2)(0, 0)
     assert lib.shape_set_load(None, None, None, 0.0, zero, 1, None, ctypes.byref(out)) == -4
     assert lib.shape_set_free(None) == 0
+    assert lib.shape_set_free_async(None, None) == 0
     assert lib.shape_set_info(None, None, None, None) == -1
+    assert lib.shp_fail_next_allocations(-1) == -1
+    assert lib.shp_fail_next_allocations(0) == 0

@@ -253,3 +253,50 @@ def test_pipelined_set_loads_match_sequential():
         S.free(stream)
     for a, b in zip(outs, ref):
         np.testing.assert_array_equal(a.cpu().numpy(), b)
+
+
+def test_allocation_failure_is_reported_and_recoverable():
+    """A device allocation that fails (simulated on the host by the test hook,
+    no GPU fault) surfaces as SHP_ENOMEM with a message; the library keeps
+    working afterwards."""
+    ms = synth.generate(81, [12, 20, 7])
+    S = shp.shape_set_load(ms)
+    ia = np.arange(3, dtype=np.int32)
+    ok, _ = shp.overlap_estimate(S, ia, S, ia[::-1].copy(), seed=1, n_samples=512)
+    shp.fail_next_allocations(1)
+    with pytest.raises(shp.ShapeError, match="out of memory"):
+        shp.overlap_estimate(S, ia, S, ia[::-1].copy(), seed=1, n_samples=512)
+    again, _ = shp.overlap_estimate(S, ia, S, ia[::-1].copy(), seed=1, n_samples=512)
+    np.testing.assert_array_equal(again.cpu().numpy(), ok.cpu().numpy())
+    shp.fail_next_allocations(1)
+    with pytest.raises(shp.ShapeError, match="out of memory"):
+        shp.shape_set_load(ms)
+    so = shp.self_overlaps(S, seed=1, n_samples=512)
+    shp.fail_next_allocations(2)
+    with pytest.raises(shp.ShapeError, match="out of memory"):
+        shp.align_rigid(S, 0, S, torch.tensor([1, 2], dtype=torch.int32), so, so, seed=2, starts=2, steps=2)
+    shp.fail_next_allocations(0)
+    S2 = shp.shape_set_load(ms)
+    np.testing.assert_array_equal(S2.tables()[1], S.tables()[1])
+
+
+def test_chunked_screen_reproduces_the_full_screen():
+    """Pairs are keyed by their global index, so a database screened in two
+    chunks (stream bases offset by the first chunk's size) reproduces the
+    one-launch screen bit for bit -- fixed budget and adaptive: a screen can
+    be sharded over devices or resumed from its last finished chunk."""
+    q = synth.principal_axes(synth.generate(71, [28]))
+    d = synth.principal_axes(synth.generate(72, synth.counts_uniform(72, 600, 18, 60)))
+    Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
+    sq = shp.self_overlaps(Sq, seed=1, n_samples=2048)
+    sd = shp.self_overlaps(Sd, seed=2, n_samples=2048)
+    halves = [np.arange(0, 250), np.arange(250, 600)]
+    for kw in (dict(n_fixed=1024), dict(tau=0.01, min_n=512, cap=8192)):
+        full = shp.tanimoto_screen(Sq, Sd, sq, sd, seed=3, with_overlaps=True, **kw)
+        parts = []
+        for h in halves:
+            Sh = shp.shape_set_load(d.subset(h))
+            sh = shp.self_overlaps(Sh, seed=2, n_samples=2048, stream_base=int(h[0]))
+            parts.append(shp.tanimoto_screen(Sq, Sh, sq, sh, seed=3, stream_base=int(h[0]), with_overlaps=True, **kw))
+        for k in ("T", "seT", "O", "n_used"):
+            np.testing.assert_array_equal(np.concatenate([p[k].cpu().numpy() for p in parts]), full[k].cpu().numpy())
