@@ -531,6 +531,17 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
     T_fx = fix["T"].cpu().numpy()[:, 1].reshape(q.n_mol, len(sub))
     rho = [float(stats.spearmanr(T_ad[i], T_fx[i]).statistic) for i in range(q.n_mol)]
     se_ad = res["seT"].cpu().numpy()[:, 1]
+
+    def stopping_effect(T_a, se_a):
+        """Optional stopping: mean of T_adaptive - T_fixed and the share of
+        pairs whose nominal 95% interval (both SEs) covers the difference."""
+        se_f = fix["seT"].cpu().numpy()[:, 1].reshape(q.n_mol, len(sub))
+        diff = T_a - T_fx
+        z = diff / np.sqrt(se_a ** 2 + se_f ** 2)
+        return {"mean_T_minus_fixed": float(diff.mean()), "mean_z": float(z.mean()),
+                "coverage_95": float((np.abs(z) <= 1.959964).mean())}
+
+    se_ad_sub = se_ad.reshape(q.n_mol, d.n_mol)[:, sub]
     with_cv = None
     if net is not None:
         c0 = torch.cuda.Event(enable_timing=True)
@@ -557,6 +568,7 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
         rho_cv = [float(stats.spearmanr(T_cv[i], T_fx[i]).statistic) for i in range(q.n_mol)]
         se_cv = rcv["seT"].cpu().numpy()[:, 1]
         with_cv = {
+            "optional_stopping": stopping_effect(T_cv, se_cv.reshape(q.n_mol, d.n_mol)[:, sub]),
             "pairs_per_s": npairs / (t_cv + t_w), "seconds": t_cv, "weights_seconds": t_w,
             "mean_samples_per_direction": float(nu_cv.mean()), "frac_at_cap": float((nu_cv >= cap).mean()),
             "frac_se_met": float((se_cv <= tau * (1 + 1e-6)).mean()),
@@ -578,6 +590,7 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
                          "pairs_per_s": fixed_pairs / t_fix, "seconds": t_fix},
         "speedup_pairs_per_s": (npairs / t_ad) / (fixed_pairs / t_fix),
         "spearman_rho_vs_fixed": {"mean": float(np.mean(rho)), "min": float(np.min(rho))},
+        "optional_stopping": stopping_effect(T_ad, se_ad_sub),
         "tuned_variant": int(best), "variant_ms": [round(float(x), 3) for x in times],
         "with_control_variate": with_cv,
     }
