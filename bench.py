@@ -10,7 +10,16 @@ union by 4096 importance samples) that the Tanimotos need.
 
 Metric: sample x atom Gaussian evaluations per second (each sample
 evaluates every atom of both molecules; self-overlap samples evaluate their
-own molecule), with Tanimoto pairs/s reported beside it.
+own molecule), with Tanimoto pairs/s reported beside it. The step runs as two
+CUDA-graph replays; `roofline` times the screen kernel alone, `e2e` the same
+work through the public API from host arrays (pipelined steps), and
+`cpu_baseline` the FP64 oracle on the host cores.
+
+Further sections of the JSON line (each skippable): the adaptive screen of
+16 queries x 1,000,000 molecules to SE(T) <= 0.005 against the fixed budget
+with the same guarantee, with and without the learned control variate; the
+control variate's training and its union volumes at relative SE <= 1e-3;
+multi-start rigid alignment of 1 query x 10,000 molecules.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
