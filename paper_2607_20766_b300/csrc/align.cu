@@ -30,8 +30,7 @@ struct __align__(16) AlignTables {
   float lp[SHP_MAX_ATOMS];      // log2 p
   float4 qatom[SHP_MAX_ATOMS];  // the query's centres and alpha (closed-form objective)
   float qlp[SHP_MAX_ATOMS];
-  float g[SHP_MAX_ATOMS][32];   // per-lane Gaussian values of the current point
-  float pre[SHP_MAX_ATOMS][32]; // per-lane prefix products prod_{l<j} (1 - g_l)
+  float pre[SHP_MAX_ATOMS][32]; // per-lane prefix products prod_{l<j} (1 - g_l) of the current point
 };
 constexpr size_t kAlignSmem = sizeof(AlignTables) * kAlignWarps;
 
@@ -153,17 +152,18 @@ __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restr
         const float dx = r.x - c.x, dy = r.y - c.y, dz = r.z - c.z;
         const float g = ex2_approx(fmaf(c.w, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), T.lp[j]));
         T.pre[j][lane] = q;
-        T.g[j][lane] = g;
         q = fmaf(-g, q, q);
       }
       acc[0] = fmaf(r.w, 1.f - q, acc[0]);
       float S = r.w;  // w_k times the suffix product
       for (int j = nb - 1; j >= 0; --j) {
-        const float g = T.g[j][lane];
+        // g_j again, from the same expression as the forward pass (the same
+        // float): storing it would halve the warps per SM
         const float4 c = T.posed[j];
+        const float dx = r.x - c.x, dy = r.y - c.y, dz = r.z - c.z;
+        const float g = ex2_approx(fmaf(c.w, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), T.lp[j]));
         const float h = -2.f * c.w * 0.6931471805599453f * g * T.pre[j][lane] * S;
         S = fmaf(-g, S, S);
-        const float dx = r.x - c.x, dy = r.y - c.y, dz = r.z - c.z;
         const float4 b = T.body[j];
         const float gx = h * dx, gy = h * dy, gz = h * dz;
         acc[1] += gx; acc[2] += gy; acc[3] += gz;
