@@ -75,6 +75,8 @@ _SIGS = {
                          ctypes.c_double, _P, _P],
     "orc_fo_pose_grad": [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _P],
     "orc_attributions": [_P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, ctypes.c_int],
+    "orc_cv_fit_weights": [_P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
+                           _P, ctypes.c_int],
     "orc_union_volume_cv": [_P, _P, ctypes.c_int64, _P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, _P,
                             ctypes.c_int],
     "orc_cv_features": [_P, _P],
@@ -370,6 +372,18 @@ def union_volume_cv(S, idx, omega, seed, n, stream_base=0, n_threads=0, c_alpha=
     _check(lib().orc_union_volume_cv(s.ref, idx.ctypes.data, len(idx), om.ctypes.data, seed, stream_base, n,
                                      v.ctypes.data, vs.ctypes.data, n_threads), "union_volume_cv")
     return v, vs
+
+
+def cv_fit_weights(S, idx, seed, n, stream_base=0, ridge=1e-6, n_threads=0, c_alpha=2.41798793):
+    """[n_atoms] float64: least-squares control-variate weights of the listed
+    molecules (other atoms 0): the projection of u onto the molecule's own
+    Gaussians, with b estimated from n samples (tag 6)."""
+    s = _oset(S, c_alpha)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    om = np.zeros(int(s.offsets[-1]))
+    _check(lib().orc_cv_fit_weights(s.ref, idx.ctypes.data, len(idx), seed, stream_base, n, ridge, om.ctypes.data,
+                                    n_threads), "cv_fit_weights")
+    return om
 
 
 def cv_features(S, c_alpha=2.41798793):

@@ -60,7 +60,7 @@
 
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ERANGE = -4 };
 enum { ORC_SYMMETRIC = 1u, ORC_ANTITHETIC = 2u };
-enum { ORC_TAG_AB = 0u, ORC_TAG_BA = 1u, ORC_TAG_SELF = 2u };
+enum { ORC_TAG_AB = 0u, ORC_TAG_BA = 1u, ORC_TAG_SELF = 2u, ORC_TAG_FIT = 6u };
 
 /* A set of molecules as flat arrays (host). p may be NULL (2 sqrt 2). */
 typedef struct {
@@ -1023,6 +1023,85 @@ int orc_union_volume_cv(const orc_set* S, const int32_t* idx, int64_t n_mol, con
     if (var < 0) var = 0;
     vol[k] = closed + m.Z * mean;
     if (vol_se) vol_se[k] = m.Z * sqrt(var / n);
+  }
+  return err ? ORC_EINVAL : ORC_OK;
+}
+
+/*
+ * Least-squares control-variate weights (not in the paper): per molecule the
+ * w minimising the integral of (u - sum_i w_i g_i)^2, the L2 projection of
+ * the union occupancy onto the span of the molecule's own Gaussians:
+ *   (G + lambda I) w = b,
+ *   G_ij = integral g_i g_j        (closed form, the terms of Eq. fo),
+ *   b_i  = integral u g_i = Z E_q[(u / m) g_i]
+ *          (n samples of the molecule's own mixture, tag 6, stream
+ *          stream_base + k, the usual sample layout),
+ *   lambda = ridge * trace(G) / N.
+ * Cholesky in FP64. omega [n_atoms] is written for the listed molecules.
+ */
+int orc_cv_fit_weights(const orc_set* S, const int32_t* idx, int64_t n_mol, uint64_t seed, uint64_t stream_base,
+                       uint32_t n, double ridge, double* omega, int n_threads) {
+  if (n < 2 || !(ridge >= 0.0)) return ORC_EINVAL;
+  nthreads_set(n_threads);
+  int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+  for (int64_t k = 0; k < n_mol; ++k) {
+    int32_t mi = idx ? idx[k] : (int32_t)k;
+    orc_mol m;
+    if (load_mol(S, mi, NULL, &m)) { err |= 1; continue; }
+    const int N = m.n;
+    double b[ORC_MAXN] = {0}, A[ORC_MAXN][ORC_MAXN], L[ORC_MAXN][ORC_MAXN], y[ORC_MAXN];
+    for (uint32_t t = 0; t < n; t += 2) {
+      double r[2][3];
+      int i0, i1;
+      draw_pair(&m, seed, stream_base + (uint64_t)k, ORC_TAG_FIT, t / 2, 0, r[0], r[1], &i0, &i1);
+      for (int j = 0; j < 2 && t + j < n; ++j) {
+        double g[ORC_MAXN], ms = 0.0, prod = 1.0;
+        for (int i = 0; i < N; ++i) {
+          double dx = r[j][0] - m.c[i][0], dy = r[j][1] - m.c[i][1], dz = r[j][2] - m.c[i][2];
+          g[i] = m.p[i] * exp(-m.alpha[i] * (dx * dx + dy * dy + dz * dz));
+          ms += g[i];
+          prod *= 1.0 - g[i];
+        }
+        const double w = (1.0 - prod) / ms;
+        for (int i = 0; i < N; ++i) b[i] += w * g[i];
+      }
+    }
+    double tr = 0.0;
+    for (int i = 0; i < N; ++i) {
+      b[i] *= m.Z / n;
+      for (int j = 0; j < N; ++j) {
+        double s2 = m.alpha[i] + m.alpha[j], t2 = ORC_PI / s2;
+        double dx = m.c[i][0] - m.c[j][0], dy = m.c[i][1] - m.c[j][1], dz = m.c[i][2] - m.c[j][2];
+        A[i][j] = m.p[i] * m.p[j] * t2 * sqrt(t2) * exp(-m.alpha[i] * m.alpha[j] / s2 * (dx * dx + dy * dy + dz * dz));
+      }
+      tr += A[i][i];
+    }
+    for (int i = 0; i < N; ++i) A[i][i] += ridge * tr / N;
+    int ok = 1;
+    for (int j = 0; j < N && ok; ++j) {  /* A = L L^T */
+      double d = A[j][j];
+      for (int l = 0; l < j; ++l) d -= L[j][l] * L[j][l];
+      if (!(d > 0.0)) { ok = 0; break; }
+      L[j][j] = sqrt(d);
+      for (int i = j + 1; i < N; ++i) {
+        double v = A[i][j];
+        for (int l = 0; l < j; ++l) v -= L[i][l] * L[j][l];
+        L[i][j] = v / L[j][j];
+      }
+    }
+    if (!ok) { err |= 1; continue; }
+    for (int i = 0; i < N; ++i) {  /* L y = b */
+      double v = b[i];
+      for (int l = 0; l < i; ++l) v -= L[i][l] * y[l];
+      y[i] = v / L[i][i];
+    }
+    double* om = omega + S->offsets[mi];
+    for (int i = N - 1; i >= 0; --i) {  /* L^T w = y */
+      double v = y[i];
+      for (int l = i + 1; l < N; ++l) v -= L[l][i] * om[l];
+      om[i] = v / L[i][i];
+    }
   }
   return err ? ORC_EINVAL : ORC_OK;
 }

@@ -173,3 +173,60 @@ def test_screen_cv_attributions_reduce_variance_on_drug_size_molecules():
     ratio = (cv["seO"][:, 1] / pl["seO"][:, 1]) ** 2
     assert ratio.mean() < 0.85, ratio
     np.testing.assert_array_equal(cv["O"][:, 0], pl["O"][:, 0])  # first-order slot untouched
+
+
+# ------------------------------------------------ least-squares weights
+
+
+def _gauss_product_integral(ps, alphas, centres):
+    """Integral over R^3 of prod_k p_k exp(-alpha_k |r - c_k|^2) (Gaussian
+    product theorem)."""
+    A = sum(alphas)
+    s = sum(a * c for a, c in zip(alphas, centres))
+    q = sum(a * float(c @ c) for a, c in zip(alphas, centres)) - float(s @ s) / A
+    return float(np.prod(ps)) * (np.pi / A) ** 1.5 * np.exp(-q)
+
+
+def test_least_squares_weights_two_atoms_closed_form():
+    """Two overlapping atoms: u = g1 + g2 - g1 g2, so every integral of the
+    projection has a closed form; the sampled fit matches it."""
+    c = np.array([[0.0, 0.0, 0.0], [1.3, 0.4, -0.2]])
+    R = np.array([1.7, 1.52])
+    ms = MolSet(c.astype(np.float32), R.astype(np.float32), np.array([0, 2], np.int32), np.zeros(2, np.uint8))
+    c = ms.xyz.astype(np.float64)
+    a = 2.41798793 / ms.radius.astype(np.float64) ** 2
+    p = 2.0 * np.sqrt(2.0)
+
+    def I(*ks):  # integral of the product of the listed Gaussians (indices may repeat)
+        return _gauss_product_integral([p] * len(ks), [a[k] for k in ks], [c[k] for k in ks])
+
+    G = np.array([[I(0, 0), I(0, 1)], [I(1, 0), I(1, 1)]])
+    b = np.array([I(i, 0) + I(i, 1) - I(i, 0, 1) for i in range(2)])  # integral of u g_i
+    exact = np.linalg.solve(G, b)
+    fits = np.array([O.cv_fit_weights(ms, [0], seed=s, n=1 << 18, ridge=0.0) for s in range(8)])
+    se = fits.std(0, ddof=1) / np.sqrt(len(fits))
+    assert np.all(np.abs(fits.mean(0) - exact) < 4 * se), (fits.mean(0), exact, se)
+    assert np.all(se < 2e-3 * exact)
+
+
+def test_least_squares_weights_of_isolated_atoms_are_one():
+    ms = MolSet(np.array([[0, 0, 0], [30, 0, 0], [0, 30, 0]], np.float32), np.array([1.7, 1.55, 1.52], np.float32),
+                np.array([0, 3], np.int32), np.zeros(3, np.uint8))
+    np.testing.assert_allclose(O.cv_fit_weights(ms, [0], seed=1, n=1 << 16), 1.0, atol=2e-2)
+
+
+def test_least_squares_weights_beat_attributions_in_the_screen():
+    """The projection weights lower the screen's union variance further than
+    the volume attributions do (drug-size molecules)."""
+    q = synth.principal_axes(synth.generate(21, [20, 32, 12]))
+    d = synth.principal_axes(synth.generate(22, [12, 39, 50, 25]))
+    aq = O.attributions(q, np.arange(q.n_mol), seed=3, M=2048)
+    ad = O.attributions(d, np.arange(d.n_mol), seed=4, M=2048)
+    lq = O.cv_fit_weights(q, np.arange(q.n_mol), seed=5, n=4096)
+    ld = O.cv_fit_weights(d, np.arange(d.n_mol), seed=6, n=4096, stream_base=10)
+    pl = _screen(q, d, seed=7, n=4096)
+    ca = _screen(q, d, seed=7, n=4096, omega_q=aq, omega_d=ad)
+    cl = _screen(q, d, seed=7, n=4096, omega_q=lq, omega_d=ld)
+    ra = (ca["seO"][:, 1] / pl["seO"][:, 1]) ** 2
+    rl = (cl["seO"][:, 1] / pl["seO"][:, 1]) ** 2
+    assert rl.mean() < 0.55 and rl.mean() < 0.75 * ra.mean(), (rl, ra)
