@@ -487,9 +487,10 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
     (18-60, heavy-tailed toward 40), rounds of 256 samples per direction
     until SE(T_union) <= tau or cap. Compared with the plain fixed budget
     that gives the same guarantee (cap samples per direction for every pair),
-    timed on every 64th database molecule. With a trained crowding network,
-    also the adaptive screen with the union slot's control variate (weights
-    predicted per atom for both sets)."""
+    timed on every 64th database molecule. Also the adaptive screen with the
+    union slot's control variate: weights predicted per atom by the trained
+    crowding network (when given), and least-squares projection weights
+    fitted per molecule."""
     from scipy import stats
     from paper_2607_20766_b300 import synth
     q, d = synth.adaptive_screen(n_q=16, n_db=n_db, seed=4242 + 7919 * rank)
@@ -551,16 +552,16 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
                 "coverage_95": float((np.abs(z) <= 1.959964).mean())}
 
     se_ad_sub = se_ad.reshape(q.n_mol, d.n_mol)[:, sub]
-    with_cv = None
-    if net is not None:
+    def cv_arm(weights):
+        """The adaptive screen with the union slot's control variate; the
+        weights (per atom of both sets) come from `weights()`, timed."""
         c0 = torch.cuda.Event(enable_timing=True)
         c1 = torch.cuda.Event(enable_timing=True)
         c0.record(stream)
-        wq = net.predict(shp.cv_features(Sq))
-        wd = net.predict(shp.cv_features(Sd))
+        wq, wd = weights()
         c1.record(stream)
-        best_cv, times_cv = shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=16384, tau=tau, cap=cap,
-                                                     omega_q=wq, omega_db=wd)
+        best_cv, _ = shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=16384, tau=tau, cap=cap,
+                                              omega_q=wq, omega_db=wd)
         g_cv = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, selfq, selfd, seed=77, tau=tau, round=256, min_n=1024,
                              cap=cap, omega_q=wq, omega_db=wd)
         torch.cuda.synchronize()
@@ -576,7 +577,7 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
         T_cv = rcv["T"].cpu().numpy()[:, 1].reshape(q.n_mol, d.n_mol)[:, sub]
         rho_cv = [float(stats.spearmanr(T_cv[i], T_fx[i]).statistic) for i in range(q.n_mol)]
         se_cv = rcv["seT"].cpu().numpy()[:, 1]
-        with_cv = {
+        return {
             "optional_stopping": stopping_effect(T_cv, se_cv.reshape(q.n_mol, d.n_mol)[:, sub]),
             "pairs_per_s": npairs / (t_cv + t_w), "seconds": t_cv, "weights_seconds": t_w,
             "mean_samples_per_direction": float(nu_cv.mean()), "frac_at_cap": float((nu_cv >= cap).mean()),
@@ -586,6 +587,14 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
             "spearman_rho_vs_fixed": {"mean": float(np.mean(rho_cv)), "min": float(np.min(rho_cv))},
             "tuned_variant": int(best_cv),
         }
+
+    # learned crowding weights (the volume network) and least-squares
+    # projection weights fitted from 1024 samples per molecule
+    with_cv = None
+    if net is not None:
+        with_cv = cv_arm(lambda: (net.predict(shp.cv_features(Sq)), net.predict(shp.cv_features(Sd))))
+    with_fit = cv_arm(lambda: (shp.cv_fit_weights(Sq, seed=91, n_samples=1024),
+                               shp.cv_fit_weights(Sd, seed=92, n_samples=1024)))
     return {
         "workload": f"adaptive screen: 16 queries (20-48 atoms) x {n_db} molecules (18-60, heavy-tailed toward 40), "
                     f"rounds of 256 per direction, SE(T_union) <= {tau} or {cap} per direction",
@@ -602,6 +611,7 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
         "optional_stopping": stopping_effect(T_ad, se_ad_sub),
         "tuned_variant": int(best), "variant_ms": [round(float(x), 3) for x in times],
         "with_control_variate": with_cv,
+        "with_fitted_control_variate": with_fit,
     }
 
 

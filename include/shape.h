@@ -337,6 +337,7 @@ int align_rigid(shp_set Q, int32_t iq, shp_set B, const int32_t* ib, int64_t n_p
  */
 
 #define SHP_TAG_ATTR 5u /* samples of the union attributions */
+#define SHP_TAG_FIT 6u  /* samples of the least-squares control-variate fit */
 
 /*
  * Union attributions om*_i = E_{r ~ N(c_i, I/(2 alpha_i))}[u(r)/m(r)] for
@@ -347,6 +348,25 @@ int align_rigid(shp_set Q, int32_t iq, shp_set B, const int32_t* ib, int64_t n_p
  */
 int union_attributions(shp_set S, uint64_t seed, uint64_t stream_base, uint32_t M, float* omega,
                        void* stream);
+
+/*
+ * Least-squares control-variate weights (not in the paper; for the screen's
+ * union slot): for molecule k of the list the weights w minimising the
+ * integral of (u - sum_i w_i g_i)^2, the projection of the union occupancy
+ * onto the molecule's own Gaussians:
+ *   (G + lambda I) w = b,   G_ij = integral g_i g_j (closed form, Eq. fo terms),
+ *   b_i = integral u g_i = Z E_q[(u / m) g_i],   lambda = ridge * trace(G) / N,
+ * b from mc->n_samples (a positive multiple of 256) samples of the molecule's
+ * own mixture (stream mc->stream_base + k, tag SHP_TAG_FIT, the usual sample
+ * layout; mc->flags must be 0), solved by conjugate gradients to a relative
+ * residual of 1e-6 (at most 4 N iterations).
+ *   idx [n] device int32 molecule ids, or NULL for molecules 0 .. n-1
+ *   omega [n_atoms] float device: written for the atoms of the listed
+ *   molecules (set atom order); other entries are left as they are.
+ * Errors: SHP_EINVAL (NULL, bad n_samples, flags or ridge), SHP_ERANGE.
+ */
+int cv_fit_weights(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, float ridge, float* omega,
+                   void* stream);
 
 /*
  * Union volume of molecules S[idx[k]] with the control variate omega (per

@@ -26,7 +26,7 @@ EXPORTS = ("shp_last_error", "shp_version", "shp_fail_next_allocations", "shape_
            "shape_set_tables", "overlap_estimate", "union_volume_estimate", "fo_overlap",
            "tanimoto_screen", "shp_screen_variants", "shp_screen_variant_info", "tanimoto_screen_tune", "align_crn_points",
            "overlap_pose_grad", "align_rigid", "shape_set_frames", "union_attributions", "union_volume_cv",
-           "cv_features", "mlp_forward", "mlp_loss_grad", "mlp_adam", "mlp_loss_grad_noalloc")
+           "cv_features", "mlp_forward", "mlp_loss_grad", "mlp_adam", "mlp_loss_grad_noalloc", "cv_fit_weights")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 33, 64, 6401
 OBJ_FO, OBJ_UNION, OBJ_FO_CLOSED = 0, 1, 2
 
@@ -88,6 +88,7 @@ def load_library():
         "union_attributions": [_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, _P],
         "union_volume_cv": [_P, _P, ctypes.c_int64, _P, _P, ctypes.c_float, ctypes.c_uint32, _P, _P, _P, _P],
         "cv_features": [_P, _P, _P],
+        "cv_fit_weights": [_P, _P, ctypes.c_int64, _P, ctypes.c_float, _P, _P],
         "mlp_forward": [_P, _P, _P, ctypes.c_int64, _P, _P],
         "mlp_loss_grad": [_P, _P, _P, _P, ctypes.c_int64, _P, _P, _P],
         "mlp_loss_grad_noalloc": [_P, _P, _P, _P, ctypes.c_int64, _P, _P, _P],
@@ -445,6 +446,25 @@ def union_volume_cv(S: ShapeSet, idx=None, omega=None, seed: int = 0, n_samples:
     _check(load_library().union_volume_cv(S.handle, _dptr(idx), n, ctypes.byref(mc), _dptr(omega), target_rel_se,
                                           round, _dptr(vol), _dptr(se), _dptr(nu), _stream(stream)))
     return vol, se, nu
+
+
+def cv_fit_weights(S: ShapeSet, seed: int, n_samples: int = 1024, stream_base: int = 0, ridge: float = 1e-6,
+                   idx=None, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """[n_atoms] float32 device tensor: least-squares control-variate weights
+    (the projection of u onto each molecule's Gaussians, the right-hand side
+    from n_samples of its own samples) for the listed molecules (all if idx
+    is None)."""
+    dev = S.device
+    omega = out if out is not None else torch.zeros(S.n_atoms, dtype=torch.float32, device=dev)
+    if idx is None:
+        n, ip = S.n_mol, None
+    else:
+        ip = _device_i32(idx, dev)
+        n = ip.numel()
+    mc = ShpMC(seed, stream_base, n_samples, 0)
+    _check(load_library().cv_fit_weights(S.handle, _dptr(ip), n, ctypes.byref(mc), ridge, _dptr(omega),
+                                         _stream(stream)))
+    return omega
 
 
 def cv_features(S: ShapeSet, stream=None):

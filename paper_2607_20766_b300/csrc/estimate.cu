@@ -1200,6 +1200,127 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_volume_kernel(const CVArg
   }
 }
 
+struct FitArgs {
+  SetView S;
+  const int32_t* idx;
+  int64_t n_items;
+  Key key;
+  uint64_t stream_base;
+  uint32_t nb;    // batches of 256 samples per molecule
+  float ridge;
+  float* omega;
+  unsigned long long* queue;
+};
+
+// Closed-form overlap integral of two atomic Gaussians (Eq. fo term), FP32.
+__device__ __forceinline__ float gauss_overlap(float4 ci, float lpi, float4 cj, float lpj) {
+  const float kLog2e = 1.4426950408889634f, kPi = 3.14159265358979f;
+  const float dx = ci.x - cj.x, dy = ci.y - cj.y, dz = ci.z - cj.z;
+  const float inv = 1.0f / (ci.w + cj.w);
+  const float t = kPi * inv;
+  return t * sqrtf(t) *
+         ex2_approx(fmaf(-kLog2e * ci.w * cj.w * inv, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), lpi + lpj));
+}
+
+// Least-squares control-variate weights, one warp per molecule: the
+// projection of u onto the molecule's own Gaussians, (G + lambda I) w = b
+// with b_j = Z E_q[(u/m) g_j] from nb batches of the molecule's own samples
+// (tag 6) and G_ij the closed-form overlaps, solved by conjugate gradients
+// (lanes own rows j and j + 32; G is recomputed in every product, nothing
+// N x N is stored; at most 4 N iterations, stopping at a relative residual of
+// 1e-6).
+__global__ void __launch_bounds__(kCVWarps * 32, 2) cv_fit_kernel(const FitArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float s_b[kCVWarps][SHP_MAX_ATOMS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpTables& T = reinterpret_cast<WarpTables*>(smem_raw)[warp];
+  float* bsum = s_b[warp];
+  constexpr int SP = 4;
+  unsigned long long next = 0;
+  if (lane == 0) next = atomicAdd(a.queue, 1ull);
+  for (;;) {
+    const unsigned long long item = __shfl_sync(0xffffffffu, next, 0);
+    if (item >= (unsigned long long)a.n_items) break;
+    if (lane == 0) next = atomicAdd(a.queue, 1ull);
+    const int32_t xm = a.idx ? a.idx[item] : (int32_t)item;
+    if (xm < 0 || xm >= a.S.n_mol) continue;
+    const MolRef M = mol_ref(a.S, xm);
+    const uint64_t stream = a.stream_base + item;
+    stage_direction(T, a.S, M, nullptr, nullptr, M, nullptr, lane);
+    for (int j = lane; j < SHP_MAX_ATOMS; j += 32) bsum[j] = 0.f;
+    __syncwarp();
+    for (uint32_t bt = 0; bt < a.nb; ++bt) {
+      float2 rx[SP], ry[SP], rz[SP], rr[SP], m[SP], q[SP], ut[SP], w[SP];
+      draw_batch<SP>(T.samp, T.thr, T.alias, M.n, bt, a.key, (uint32_t)stream, (uint32_t)(stream >> 32), SHP_TAG_FIT,
+                     false, lane, rx, ry, rz, rr);
+#pragma unroll
+      for (int p = 0; p < SP; ++p) {
+        m[p] = make_float2(0.f, 0.f);
+        q[p] = make_float2(1.f, 1.f);
+      }
+      eval_table<SP, 5, false>(T.x, M.n, rx, ry, rz, rr, m, q, ut);
+#pragma unroll
+      for (int p = 0; p < SP; ++p)
+        w[p] = make_float2(__fdividef(1.f - q[p].x, m[p].x), __fdividef(1.f - q[p].y, m[p].y));
+      // b_j += sum over the batch of (u/m) g_j, g_j from the same packed expression
+#pragma unroll 1
+      for (int j = 0; j < M.n; ++j) {
+        const float4 k0 = T.x[j].ac, k1 = T.x[j].bxy, k2 = T.x[j].bzw;
+        float c = 0.f;
+#pragma unroll
+        for (int p = 0; p < SP; ++p) {
+          float2 e = __ffma2_rn(make_float2(k0.x, k0.y), rr[p], make_float2(k0.z, k0.w));
+          e = __ffma2_rn(make_float2(k1.x, k1.y), rx[p], e);
+          e = __ffma2_rn(make_float2(k1.z, k1.w), ry[p], e);
+          e = __ffma2_rn(make_float2(k2.x, k2.y), rz[p], e);
+          c = fmaf(w[p].x, ex2_approx(e.x), fmaf(w[p].y, ex2_approx(e.y), c));
+        }
+        c = warp_sum(c);
+        if (lane == 0) bsum[j] += c;
+      }
+    }
+    __syncwarp();
+    // conjugate gradients on (G + lambda I) x = b; lane owns rows i0, i1
+    const int N = M.n;
+    const int i0 = lane, i1 = lane + 32;
+    const bool h0 = i0 < N, h1 = i1 < N;
+    const float scale = (float)(a.S.Z[xm] / (256.0 * a.nb));
+    const float4 c0 = h0 ? a.S.atom[M.a0 + i0] : make_float4(0.f, 0.f, 0.f, 1.f);
+    const float4 c1 = h1 ? a.S.atom[M.a0 + i1] : make_float4(0.f, 0.f, 0.f, 1.f);
+    const float l0 = h0 ? a.S.aux[M.a0 + i0].y : 0.f, l1 = h1 ? a.S.aux[M.a0 + i1].y : 0.f;
+    const float trace =
+        warp_sum((h0 ? gauss_overlap(c0, l0, c0, l0) : 0.f) + (h1 ? gauss_overlap(c1, l1, c1, l1) : 0.f));
+    const float lambda = a.ridge * trace / (float)N;
+    float x0 = 0.f, x1 = 0.f;
+    float r0 = h0 ? bsum[i0] * scale : 0.f, r1 = h1 ? bsum[i1] * scale : 0.f;
+    float p0 = r0, p1 = r1;
+    float rs = warp_sum(r0 * r0 + r1 * r1);
+    const float tol = 1e-12f * rs;
+    for (int it = 0; it < 4 * N && rs > tol; ++it) {
+      float y0 = lambda * p0, y1 = lambda * p1;
+#pragma unroll 1
+      for (int j = 0; j < N; ++j) {
+        const float pj = __shfl_sync(0xffffffffu, j < 32 ? p0 : p1, j & 31);
+        const float4 cj = a.S.atom[M.a0 + j];
+        const float lj = a.S.aux[M.a0 + j].y;
+        if (h0) y0 = fmaf(gauss_overlap(c0, l0, cj, lj), pj, y0);
+        if (h1) y1 = fmaf(gauss_overlap(c1, l1, cj, lj), pj, y1);
+      }
+      const float pap = warp_sum(p0 * y0 + p1 * y1);
+      const float al = rs / pap;
+      x0 = fmaf(al, p0, x0); x1 = fmaf(al, p1, x1);
+      r0 = fmaf(-al, y0, r0); r1 = fmaf(-al, y1, r1);
+      const float rs_new = warp_sum(r0 * r0 + r1 * r1);
+      const float be = rs_new / rs;
+      p0 = fmaf(be, p0, r0); p1 = fmaf(be, p1, r1);
+      rs = rs_new;
+    }
+    if (h0) a.omega[M.a0 + i0] = x0;
+    if (h1) a.omega[M.a0 + i1] = x1;
+    __syncwarp();
+  }
+}
+
 }  // namespace
 }  // namespace shp
 
@@ -1217,6 +1338,30 @@ extern "C" int union_attributions(shp_set S, uint64_t seed, uint64_t stream_base
   a.omega = omega;
   return launch_persistent(attribution_kernel, a, S->n_mol, kCVWarps, sizeof(WarpTables) * kCVWarps,
                            (cudaStream_t)stream);
+}
+
+extern "C" int cv_fit_weights(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, float ridge, float* omega,
+                              void* stream) {
+  clear_error();
+  if (!S || !mc || !omega) { set_error("cv_fit_weights: NULL argument"); return SHP_EINVAL; }
+  if (mc->n_samples == 0 || mc->n_samples % 256u || mc->flags) {
+    set_error("cv_fit_weights: n_samples must be a positive multiple of 256, no flags");
+    return SHP_EINVAL;
+  }
+  if (!(ridge >= 0.f)) { set_error("cv_fit_weights: ridge must be >= 0"); return SHP_EINVAL; }
+  if (n < 0) { set_error("cv_fit_weights: negative n"); return SHP_EINVAL; }
+  if (!idx && n > S->n_mol) { set_error("cv_fit_weights: n exceeds the set size"); return SHP_ERANGE; }
+  if (n == 0) return SHP_OK;
+  FitArgs a{};
+  a.S = view(S);
+  a.idx = idx;
+  a.n_items = n;
+  a.key = Key{(uint32_t)mc->seed, (uint32_t)(mc->seed >> 32)};
+  a.stream_base = mc->stream_base;
+  a.nb = mc->n_samples / 256u;
+  a.ridge = ridge;
+  a.omega = omega;
+  return launch_persistent(cv_fit_kernel, a, n, kCVWarps, sizeof(WarpTables) * kCVWarps, (cudaStream_t)stream);
 }
 
 extern "C" int union_volume_cv(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, const float* omega,

@@ -122,3 +122,24 @@ def test_trained_network_reduces_variance():
     assert np.median(ratio) < 0.9
     z = ((v_cv - v_pl) / torch.sqrt(s_cv ** 2 + s_pl ** 2)).cpu().numpy()
     assert abs(z.mean()) < 0.2
+
+
+def test_least_squares_weights_match_oracle():
+    """The projection weights of the screen's control variate: GPU (FP32
+    sums, conjugate gradients) against the oracle (FP64, Cholesky) on the same
+    samples; a list of molecules writes only their atoms."""
+    ms = synth.principal_axes(synth.generate(91, [12, 25, 40, 60, 18, 1]))
+    S = shp.shape_set_load(ms)
+    w = shp.cv_fit_weights(S, seed=4, n_samples=1024, stream_base=7).cpu().numpy()
+    ref = O.cv_fit_weights(ms, np.arange(ms.n_mol), seed=4, n=1024, stream_base=7)
+    np.testing.assert_allclose(w, ref, rtol=1e-4, atol=2e-4 * np.abs(ref).max())
+    pick = np.array([3, 0], np.int32)
+    wp = shp.cv_fit_weights(S, seed=5, n_samples=512, idx=pick).cpu().numpy()
+    rp = O.cv_fit_weights(ms, pick, seed=5, n=512)
+    listed = np.zeros(ms.n_atoms, bool)
+    for k in pick:
+        listed[ms.offsets[k]:ms.offsets[k + 1]] = True
+    np.testing.assert_allclose(wp[listed], rp[listed], rtol=1e-4, atol=2e-4 * np.abs(rp).max())
+    assert np.all(wp[~listed] == 0.0)
+    with pytest.raises(shp.ShapeError):
+        shp.cv_fit_weights(S, seed=1, n_samples=1000)  # not a multiple of 256
