@@ -67,6 +67,8 @@ def parse_args():
     p.add_argument("--cv-train", type=int, default=200_000,
                    help="training molecules of the control-variate section (0 skips it)")
     p.add_argument("--cv-held", type=int, default=50_000)
+    p.add_argument("--fit-samples", type=int, default=4096,
+                   help="samples per molecule of the least-squares control-variate fit (multiple of 256)")
     p.add_argument("--align-db", type=int, default=10_000,
                    help="database size of the alignment section (0 skips it)")
     return p.parse_args()
@@ -428,7 +430,7 @@ def main():
         net, cvres = cv_section(shp, torch, args.cv_train, args.cv_held, rank)
     adaptive = None
     if args.adaptive_db > 0:
-        adaptive = adaptive_section(shp, torch, args.adaptive_db, rank, net=net)
+        adaptive = adaptive_section(shp, torch, args.adaptive_db, rank, net=net, fit_samples=args.fit_samples)
     aligned = None
     if args.align_db > 0:
         aligned = align_section(shp, torch, args.align_db, rank)
@@ -482,7 +484,8 @@ def main():
     return 0
 
 
-def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: int = 65536, net=None):
+def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: int = 65536, net=None,
+                     fit_samples: int = 4096):
     """Confidence-bounded screen: 16 queries (20-48 atoms) x n_db molecules
     (18-60, heavy-tailed toward 40), rounds of 256 samples per direction
     until SE(T_union) <= tau or cap. Compared with the plain fixed budget
@@ -589,12 +592,13 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
         }
 
     # learned crowding weights (the volume network) and least-squares
-    # projection weights fitted from 1024 samples per molecule
+    # projection weights fitted from fit_samples samples per molecule
     with_cv = None
     if net is not None:
         with_cv = cv_arm(lambda: (net.predict(shp.cv_features(Sq)), net.predict(shp.cv_features(Sd))))
-    with_fit = cv_arm(lambda: (shp.cv_fit_weights(Sq, seed=91, n_samples=1024),
-                               shp.cv_fit_weights(Sd, seed=92, n_samples=1024)))
+    with_fit = cv_arm(lambda: (shp.cv_fit_weights(Sq, seed=91, n_samples=fit_samples),
+                               shp.cv_fit_weights(Sd, seed=92, n_samples=fit_samples)))
+    with_fit["fit_samples_per_molecule"] = fit_samples
     return {
         "workload": f"adaptive screen: 16 queries (20-48 atoms) x {n_db} molecules (18-60, heavy-tailed toward 40), "
                     f"rounds of 256 per direction, SE(T_union) <= {tau} or {cap} per direction",
