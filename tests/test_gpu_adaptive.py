@@ -256,3 +256,23 @@ def test_graph_captured_control_variate_screen_matches_eager(small_screen):
         torch.cuda.synchronize()
         for k in ("T", "seT", "O", "seO", "n_used"):
             np.testing.assert_array_equal(res[k].cpu().numpy(), eager[k].cpu().numpy())
+
+
+def test_graph_replay_reads_inputs_updated_in_place(small_screen):
+    """A captured screen reads its inputs from the addresses seen at capture:
+    self-overlaps and control-variate weights updated in place (copy_) are
+    picked up by the next replay, which then equals an eager call on the new
+    values."""
+    q, d, Sq, Sd, sq, sd = small_screen
+    tq, td = torch.tensor(sq, device="cuda"), torch.tensor(sd, device="cuda")
+    wq = torch.full((q.n_atoms,), 0.5, dtype=torch.float32, device="cuda")
+    wd = torch.full((d.n_atoms,), 0.5, dtype=torch.float32, device="cuda")
+    g = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, tq, td, seed=9, n_fixed=1024, with_overlaps=True, omega_q=wq,
+                      omega_db=wd)
+    tq.copy_(tq * 1.01)
+    wd.copy_(torch.linspace(0.3, 0.9, d.n_atoms, device="cuda"))
+    res = g.replay()
+    eager = shp.tanimoto_screen(Sq, Sd, tq, td, seed=9, n_fixed=1024, with_overlaps=True, omega_q=wq, omega_db=wd)
+    torch.cuda.synchronize()
+    for k in ("T", "seT", "O", "seO"):
+        np.testing.assert_array_equal(res[k].cpu().numpy(), eager[k].cpu().numpy())
