@@ -276,3 +276,33 @@ def test_graph_replay_reads_inputs_updated_in_place(small_screen):
     torch.cuda.synchronize()
     for k in ("T", "seT", "O", "seO"):
         np.testing.assert_array_equal(res[k].cpu().numpy(), eager[k].cpu().numpy())
+
+
+def test_adaptive_fitted_control_variate_full_size_sampled():
+    """The benchmark's fastest arm at its full size: 16 x 1,000,000 adaptive
+    screen with least-squares weights fitted from 4096 samples per molecule;
+    24 sampled pairs recomputed by the oracle (same weights, same streams) and
+    their stop decisions checked."""
+    q, d = synth.adaptive_screen()
+    Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
+    selfq = shp.self_overlaps(Sq, seed=11, n_samples=4096, stream_base=0)
+    selfd = shp.self_overlaps(Sd, seed=11, n_samples=4096, stream_base=16)
+    wq = shp.cv_fit_weights(Sq, seed=91, n_samples=4096)
+    wd = shp.cv_fit_weights(Sd, seed=92, n_samples=4096)
+    shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=16384, tau=0.005, cap=65536, omega_q=wq,
+                             omega_db=wd)
+    g = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, selfq, selfd, seed=77, tau=0.005, round=256, min_n=1024,
+                      cap=65536, with_overlaps=True, omega_q=wq, omega_db=wd)
+    res = g.replay()
+    torch.cuda.synchronize()
+    nu = res["n_used"].cpu().numpy()
+    rng = np.random.default_rng(5)
+    pairs = np.sort(rng.choice(len(nu), 24, replace=False))
+    sq = np.zeros((q.n_mol, 2))
+    sd = np.zeros((d.n_mol, 2))
+    qs, ds = np.unique(pairs // d.n_mol), np.unique(pairs % d.n_mol)
+    sq[qs] = selfq.cpu().numpy()[qs]  # the screen's T uses the library's self-overlaps
+    sd[ds] = selfd[torch.as_tensor(ds, device=selfd.device)].cpu().numpy()
+    check_adaptive_against_oracle(q, d, res, sq, sd, 77, 0.005, 256, 1024, 65536, pairs, d.n_mol,
+                                  omega_q=wq.cpu().numpy().astype(np.float64),
+                                  omega_d=wd.cpu().numpy().astype(np.float64))
