@@ -67,7 +67,7 @@ _SIGS = {
     "orc_union_overlap_ie": [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, ctypes.c_int],
     "orc_grid": [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_double, ctypes.c_double, _P,
                  ctypes.c_int],
-    "orc_tanimoto_pairs": [_P, _P, _P, _P, _P, ctypes.c_int64, _P, _P, ctypes.c_uint64,
+    "orc_tanimoto_pairs": [_P, _P, _P, _P, _P, ctypes.c_int64, _P, _P, _P, _P, ctypes.c_uint64,
                            ctypes.c_uint32, ctypes.c_uint32, _P, _P, _P, _P, _P, _P, ctypes.c_int],
     "orc_crn_points": [_P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P],
     "orc_pose_objective": [ctypes.c_double, _P, ctypes.c_uint32, _P, ctypes.c_int32, _P, ctypes.c_int, _P],
@@ -80,6 +80,8 @@ _SIGS = {
     "orc_union_volume_cv": [_P, _P, ctypes.c_int64, _P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, _P,
                             ctypes.c_int],
     "orc_cv_features": [_P, _P],
+    "orc_union_self_cv": [_P, _P, ctypes.c_int64, _P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, _P, _P,
+                          _P, ctypes.c_int],
 }
 
 
@@ -276,13 +278,19 @@ def grid(A, ia, B=None, ib=0, h=0.1, pad=6.5, poseB=None, n_threads=0, c_alpha=2
 
 
 def tanimoto_pairs(Q, iq, D, idd, stream_ids, selfQ, selfD, seed, n, flags=0, n_threads=0,
-                   c_alpha=2.41798793, omega_q=None, omega_d=None):
+                   c_alpha=2.41798793, omega_q=None, omega_d=None, selfQ_se=None, selfD_se=None):
     """Fixed-budget symmetric screen of explicit pairs. Returns dict of
     [n_pairs, 2] arrays O, seO, T, seT (slot 0 first order, slot 1 union).
-    omega_q/omega_d (per set atom): control-variate weights of the union slot."""
+    omega_q/omega_d (per set atom): control-variate weights of the union slot.
+    selfQ_se/selfD_se (like selfQ/selfD): standard errors of the
+    self-overlaps; seT is then the full delta-method SE of T."""
     sq, sd = _oset(Q, c_alpha), _oset(D, c_alpha)
     if (omega_q is None) != (omega_d is None):
         raise ValueError("give both omega_q and omega_d or neither")
+    if (selfQ_se is None) != (selfD_se is None):
+        raise ValueError("give both selfQ_se and selfD_se or neither")
+    eq = None if selfQ_se is None else np.ascontiguousarray(selfQ_se, dtype=np.float64)
+    ed = None if selfD_se is None else np.ascontiguousarray(selfD_se, dtype=np.float64)
     wq = None if omega_q is None else np.ascontiguousarray(omega_q, dtype=np.float64)
     wd = None if omega_d is None else np.ascontiguousarray(omega_d, dtype=np.float64)
     iq = np.ascontiguousarray(iq, dtype=np.int32)
@@ -293,7 +301,8 @@ def tanimoto_pairs(Q, iq, D, idd, stream_ids, selfQ, selfD, seed, n, flags=0, n_
     k = len(iq)
     O, sO, T, sT = (np.empty((k, 2)) for _ in range(4))
     _check(lib().orc_tanimoto_pairs(sq.ref, iq.ctypes.data, sd.ref, idd.ctypes.data, st.ctypes.data, k,
-                                    selfQ.ctypes.data, selfD.ctypes.data, seed, n, flags, _ptr(wq), _ptr(wd),
+                                    selfQ.ctypes.data, selfD.ctypes.data, _ptr(eq), _ptr(ed), seed, n, flags,
+                                    _ptr(wq), _ptr(wd),
                                     O.ctypes.data, sO.ctypes.data, T.ctypes.data, sT.ctypes.data, n_threads),
            "tanimoto_pairs")
     return dict(O=O, seO=sO, T=T, seT=sT)
@@ -372,6 +381,20 @@ def union_volume_cv(S, idx, omega, seed, n, stream_base=0, n_threads=0, c_alpha=
     _check(lib().orc_union_volume_cv(s.ref, idx.ctypes.data, len(idx), om.ctypes.data, seed, stream_base, n,
                                      v.ctypes.data, vs.ctypes.data, n_threads), "union_volume_cv")
     return v, vs
+
+
+def union_self_cv(S, idx, omega, seed, n, stream_base=0, n_threads=0, c_alpha=2.41798793):
+    """(vol, vol_se, self_ov, self_se), each [len(idx)]: union volumes and
+    union self-overlaps with the weighted-Gaussian control variate omega (per
+    set atom; None = the plain estimators), n samples per molecule (tag 2)."""
+    s = _oset(S, c_alpha)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    om = None if omega is None else np.ascontiguousarray(omega, dtype=np.float64)
+    k = len(idx)
+    v, vs, so, ss = (np.empty(k) for _ in range(4))
+    _check(lib().orc_union_self_cv(s.ref, idx.ctypes.data, k, _ptr(om), seed, stream_base, n, v.ctypes.data,
+                                   vs.ctypes.data, so.ctypes.data, ss.ctypes.data, n_threads), "union_self_cv")
+    return v, vs, so, ss
 
 
 def cv_fit_weights(S, idx, seed, n, stream_base=0, ridge=1e-6, n_threads=0, c_alpha=2.41798793):

@@ -720,6 +720,16 @@ int orc_grid(const orc_set* A, int32_t ia, const orc_set* B, int32_t ib, const f
  * [slot 0 = first order, slot 1 = union] (indexed by iq[k] / id[k]).
  * Outputs (slot 0 first order, slot 1 union), each [n_pairs][2]:
  * O, seO, T = O / (S - O) with S = O_QQ + O_DD, seT = S / (S - O)^2 seO.
+ *
+ * selfQ_se / selfD_se (same layout as selfQ / selfD, or both NULL): the
+ * standard errors of estimated self-overlaps. The self-overlaps then carry
+ * their own sampling error into T, and seT is the full first-order (delta
+ * method) propagation of all three independent estimates through
+ * T(O, O_QQ, O_DD) = O / (O_QQ + O_DD - O):
+ *   dT/dO = S / (S - O)^2,   dT/dO_QQ = dT/dO_DD = -O / (S - O)^2,
+ *   seT^2 = (dT/dO)^2 seO^2 + (O / (S - O)^2)^2 (seQQ^2 + seDD^2).
+ * The paper's formula (Sec. confidence-bounded screening) keeps only the
+ * first term, i.e. treats the self-overlaps as exact.
  */
 /*
  * omega_q, omega_d: per-atom control-variate weights of each set (set atom
@@ -733,11 +743,13 @@ int orc_grid(const orc_set* A, int32_t ia, const orc_set* B, int32_t ib, const f
  */
 int orc_tanimoto_pairs(const orc_set* Q, const int32_t* iq, const orc_set* D, const int32_t* id,
                        const uint64_t* stream_ids, int64_t n_pairs, const double* selfQ,
-                       const double* selfD, uint64_t seed, uint32_t n, uint32_t flags,
+                       const double* selfD, const double* selfQ_se, const double* selfD_se, uint64_t seed,
+                       uint32_t n, uint32_t flags,
                        const double* omega_q, const double* omega_d, double* O, double* seO, double* T,
                        double* seT, int n_threads) {
   if (n < 2) return ORC_EINVAL;
   if ((omega_q == NULL) != (omega_d == NULL)) return ORC_EINVAL;
+  if ((selfQ_se == NULL) != (selfD_se == NULL)) return ORC_EINVAL;
   nthreads_set(n_threads);
   int err = 0;
   const int anti = (flags & ORC_ANTITHETIC) != 0;
@@ -763,7 +775,13 @@ int orc_tanimoto_pairs(const orc_set* Q, const int32_t* iq, const orc_set* D, co
       O[2 * k + slot] = o;
       seO[2 * k + slot] = so;
       T[2 * k + slot] = o / den;
-      seT[2 * k + slot] = fabs(S / (den * den)) * so;
+      double var_t = (S / (den * den)) * (S / (den * den)) * so * so;
+      if (selfQ_se) {
+        double sq = selfQ_se[2 * (size_t)iq[k] + slot], sd = selfD_se[2 * (size_t)id[k] + slot];
+        double d_self = o / (den * den);
+        var_t += d_self * d_self * (sq * sq + sd * sd);
+      }
+      seT[2 * k + slot] = sqrt(var_t);
     }
   }
   return err ? ORC_EINVAL : ORC_OK;
@@ -1023,6 +1041,60 @@ int orc_union_volume_cv(const orc_set* S, const int32_t* idx, int64_t n_mol, con
     if (var < 0) var = 0;
     vol[k] = closed + m.Z * mean;
     if (vol_se) vol_se[k] = m.Z * sqrt(var / n);
+  }
+  return err ? ORC_EINVAL : ORC_OK;
+}
+
+/*
+ * Union volume and union self-overlap with the weighted-Gaussian control
+ * variate u~(r) = sum_i omega_i g_i(r) (omega NULL: the plain estimators of
+ * orc_union_volume_estimate, same numbers):
+ *   V    = sum_i omega_i v_i                   + Z E_q[(u - u~) / m]
+ *   O_XX = sum_ij omega_i omega_j int g_i g_j  + Z E_q[(u^2 - u~^2) / m]
+ * Both residual identities hold for any omega because E_q[h / m] Z is the
+ * integral of h (Eq. expectation), and the integrals of u~ and u~^2 are the
+ * closed forms of Eq. fo with weights. Same samples as
+ * orc_union_volume_estimate (tag 2, stream stream_base + k); n samples per
+ * molecule. Not in the paper: the self-overlap counterpart of the screen's
+ * union control variate.
+ */
+int orc_union_self_cv(const orc_set* S, const int32_t* idx, int64_t n_mol, const double* omega, uint64_t seed,
+                      uint64_t stream_base, uint32_t n, double* vol, double* vol_se, double* self_ov,
+                      double* self_se, int n_threads) {
+  if (n < 2) return ORC_EINVAL;
+  nthreads_set(n_threads);
+  int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+  for (int64_t k = 0; k < n_mol; ++k) {
+    int32_t mi = idx ? idx[k] : (int32_t)k;
+    orc_mol m;
+    if (load_mol(S, mi, NULL, &m)) { err |= 1; continue; }
+    const double* om = omega ? omega + S->offsets[mi] : NULL;
+    double closed_v = 0.0, closed_s = 0.0;
+    if (om) {
+      for (int i = 0; i < m.n; ++i) closed_v += om[i] * m.v[i];
+      closed_s = fo_closed_w(&m, om, &m, om);
+    }
+    double s[4] = {0, 0, 0, 0};
+    for (uint32_t t = 0; t < n; t += 2) {
+      double r[2][3];
+      int i0, i1;
+      draw_pair(&m, seed, stream_base + (uint64_t)k, ORC_TAG_SELF, t / 2, 0, r[0], r[1], &i0, &i1);
+      for (int j = 0; j < 2 && t + j < n; ++j) {
+        double ms, u;
+        occupancy(&m, r[j], &ms, &u);
+        double ut = om ? weighted_sum(&m, om, r[j]) : 0.0;
+        double fv = (u - ut) / ms, fs = (u * u - ut * ut) / ms;
+        s[0] += fv; s[1] += fv * fv; s[2] += fs; s[3] += fs * fs;
+      }
+    }
+    double e, sd;
+    finish(m.Z, s[0], s[1], (double)n, &e, &sd);
+    if (vol) vol[k] = closed_v + e;
+    if (vol_se) vol_se[k] = sd;
+    finish(m.Z, s[2], s[3], (double)n, &e, &sd);
+    if (self_ov) self_ov[k] = closed_s + e;
+    if (self_se) self_se[k] = sd;
   }
   return err ? ORC_EINVAL : ORC_OK;
 }
