@@ -69,15 +69,27 @@ def parse_args():
     p.add_argument("--cv-held", type=int, default=50_000)
     p.add_argument("--fit-samples", type=int, default=4096,
                    help="samples per molecule of the least-squares control-variate fit (multiple of 256)")
+    p.add_argument("--self-rel-se", type=float, default=3.5e-3,
+                   help="relative SE to which the adaptive screen estimates each database molecule's union "
+                        "self-overlap (the queries: a quarter of it)")
     p.add_argument("--align-db", type=int, default=10_000,
                    help="database size of the alignment section (0 skips it)")
     return p.parse_args()
 
 
-def workload(n_db: int, rank: int):
-    from paper_2607_20766_b300 import synth
-    # each rank screens its own database shard (weak scaling)
-    return synth.fixed_screen(n_db=n_db, n_query_atoms=N_QUERY_ATOMS, seed=SEED_WORKLOAD + 7919 * rank)
+def workload(n_db: int, rank: int, world: int = 1):
+    """The query and this rank's shard of one global database of
+    n_db * world molecules (weak scaling: n_db per rank on average): the
+    shard is a contiguous range [start, end) balanced by screen work, and only
+    its molecules are generated (the generator is keyed by molecule id).
+    Returns (query, shard, start, n_global)."""
+    from paper_2607_20766_b300 import shard, synth
+    n_global = n_db * world
+    counts = synth.counts_uniform(SEED_WORKLOAD + 1, n_global, 18, 60)
+    q = synth.principal_axes(synth.generate(SEED_WORKLOAD, [N_QUERY_ATOMS]))
+    start, end = shard.partition(counts, q.counts, world)[rank]
+    d = synth.principal_axes(synth.generate(SEED_WORKLOAD + 1, counts[start:end], first=start))
+    return q, d, start, n_global
 
 
 def aggregate(t_local: float, work_local, device: str = "cpu"):
@@ -296,7 +308,7 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    q, d = workload(args.n_db, 0)
+    q, d, _, _ = workload(args.n_db, 0)
     total_steps = args.steps + args.warmup
     per_step = args.ref_seconds or max(2.0, min(15.0, 150.0 / max(total_steps, 1)))
     rates, secs, info = [], [], None
@@ -350,7 +362,7 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    q, d = workload(args.n_db, rank)
+    q, d, start, n_global = workload(args.n_db, rank, world)
     n = N_SAMPLES
     screen_evals, self_evals = step_evals(q, d, n)
     Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
@@ -359,16 +371,18 @@ def main():
 
     # project autotuner: time every launch variant on 8192 pairs, keep the fastest
     selfq0 = shp.self_overlaps(Sq, seed=1, n_samples=n, stream_base=0)
-    selfd0 = shp.self_overlaps(Sd, seed=1, n_samples=n, stream_base=1)
+    selfd0 = shp.self_overlaps(Sd, seed=1, n_samples=n, stream_base=1 + start)
     tuned, tune_ms = shp.tanimoto_screen_tune(Sq, Sd, selfq0, selfd0, seed=SEED_WORKLOAD, n_fixed=n,
                                               n_sample=min(8192, q.n_mol * d.n_mol))
 
     # the step as two CUDA graphs (self-overlaps of both sets; the screen), so
-    # the screen kernel can be timed on its own between the replays
+    # the screen kernel can be timed on its own between the replays; a shard
+    # keys its streams by global molecule and pair ids
     g_self = shp.StepGraph(lambda: (shp.self_overlaps(Sq, seed=1, n_samples=n, stream_base=0),
-                                    shp.self_overlaps(Sd, seed=1, n_samples=n, stream_base=1)))
+                                    shp.self_overlaps(Sd, seed=1, n_samples=n, stream_base=1 + start)))
     selfq, selfd = g_self.replay()
-    g_screen = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, selfq, selfd, seed=SEED_WORKLOAD, n_fixed=n)
+    g_screen = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, selfq, selfd, seed=SEED_WORKLOAD, n_fixed=n,
+                             stream_base=start, stream_stride=n_global)
 
     def step():
         g_self.replay()
@@ -421,16 +435,30 @@ def main():
             sm_max = float(json.load(f).get("sm_max_mhz", sm_max))
     peak = sms * 128 * sm_max * 1e6 / FP32_OPS_PER_EVAL / 1e9
 
+    # the whole database's per-query top-k union Tanimotos, merged on rank 0
+    # from every shard (once, after the timed region)
+    from paper_2607_20766_b300 import shard
+    merge = None
+    if dist is not None:
+        m0 = time.perf_counter()
+        top = shard.topk_merge(res["T"][:, 1].contiguous(), start, q.n_mol, 100)
+        torch.cuda.synchronize()
+        if rank == 0:
+            merge = {"k": 100, "seconds": time.perf_counter() - m0, "best_T": float(top[0][0, 0]),
+                     "best_id": int(top[1][0, 0])}
+
     e2e = None
     if not args.no_e2e:
-        e2e = end_to_end(shp, torch, q, d, n, steps=max(2, args.steps), warmup=max(3, args.warmup))
+        e2e = end_to_end(shp, torch, q, d, n, steps=max(2, args.steps), warmup=max(3, args.warmup), start=start,
+                         n_global=n_global)
 
     cvres, net = None, None
     if args.cv_train > 0:
         net, cvres = cv_section(shp, torch, args.cv_train, args.cv_held, rank)
     adaptive = None
     if args.adaptive_db > 0:
-        adaptive = adaptive_section(shp, torch, args.adaptive_db, rank, net=net, fit_samples=args.fit_samples)
+        adaptive = adaptive_section(shp, torch, args.adaptive_db, rank, net=net, fit_samples=args.fit_samples,
+                                    self_rel_se=args.self_rel_se)
     aligned = None
     if args.align_db > 0:
         aligned = align_section(shp, torch, args.align_db, rank)
@@ -447,14 +475,16 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 accumulation)", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 evaluation, f64 per-pair sums", "data": "synthetic",
             "config": {"workload": f"fixed-budget screen: 1 query ({N_QUERY_ATOMS} atoms) x {args.n_db} database "
                                    f"molecules per GPU (18-60 atoms, uniform, principal-axis pre-aligned), "
                                    f"{n} samples per direction per pair, first-order + union Tanimoto with "
                                    f"self-overlaps",
                        "global_batch": n_pairs * world, "l2": "flushed between timed steps (512 MB write)",
                        "launch": "per step two CUDA graph replays: self-overlaps of both sets, then the screen",
-                       "parallelism": f"dp{world} (database shards, no collective)"},
+                       "parallelism": f"dp{world}: one database of {n_global} molecules in balanced contiguous "
+                                      f"shards, pairs keyed by global ids, no collective while screening, "
+                                      f"per-query top-100 merged on rank 0 after the timed region"},
             "pairs_per_s": pairs_per_s,
             "evals_per_step": evals_rank,
             "wall_s": wall,
@@ -470,6 +500,8 @@ def main():
         }
         if e2e is not None:
             line["e2e"] = e2e
+        if merge is not None:
+            line["topk_merge"] = merge
         if adaptive is not None:
             line["adaptive"] = adaptive
         if cvres is not None:
@@ -485,61 +517,96 @@ def main():
 
 
 def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: int = 65536, net=None,
-                     fit_samples: int = 4096):
+                     fit_samples: int = 4096, self_rel_se: float = 3.5e-3):
     """Confidence-bounded screen: 16 queries (20-48 atoms) x n_db molecules
     (18-60, heavy-tailed toward 40), rounds of 256 samples per direction
-    until SE(T_union) <= tau or cap. Compared with the plain fixed budget
-    that gives the same guarantee (cap samples per direction for every pair),
-    timed on every 64th database molecule. Also the adaptive screen with the
-    union slot's control variate: weights predicted per atom by the trained
-    crowding network (when given), and least-squares projection weights
-    fitted per molecule."""
+    until the full delta-method SE(T_union) <= tau or cap. The union
+    self-overlaps are estimated first, each to a stated relative SE (rounds
+    of 256 until SE/O <= self_rel_se for the database, a quarter of it for
+    the queries), and their SEs enter SE(T) and the stop rule; their time
+    counts in every arm's pairs/s. Compared with the plain fixed budget at
+    the cap and at the smallest budget that meets the full SE(T) <= tau for
+    99% of pairs, both timed on every 64th database molecule. Also the
+    adaptive screen with the union slot's control variate: weights predicted
+    per atom by the trained crowding network (when given), and least-squares
+    projection weights fitted per molecule."""
     from scipy import stats
     from paper_2607_20766_b300 import synth
     q, d = synth.adaptive_screen(n_q=16, n_db=n_db, seed=4242 + 7919 * rank)
     Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
     stream = torch.cuda.current_stream()
-    # self-overlaps and the adaptive screen, each captured as a CUDA graph
-    g_self = shp.StepGraph(lambda: (shp.self_overlaps(Sq, seed=11, n_samples=4096, stream_base=0),
-                                    shp.self_overlaps(Sd, seed=11, n_samples=4096, stream_base=16)))
-    selfq, selfd = g_self.replay()
-    best, times = shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=16384, tau=tau, cap=cap)
-    g_ad = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, selfq, selfd, seed=77, tau=tau, round=256, min_n=1024,
-                         cap=cap)
-    torch.cuda.synchronize()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    g_self.replay()
-    t1.record(stream)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    res = g_ad.replay()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_self = t0.elapsed_time(t1) / 1e3
-    t_ad = e0.elapsed_time(e1) / 1e3
-    nu = res["n_used"].cpu().numpy().astype(np.int64)
-    npairs = len(nu)
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    # union self-overlaps to a stated precision (closed-form first order beside them)
+    rel_q = self_rel_se / 4
+
+    def self_step():
+        sq, sq_se, nq = shp.self_overlaps(Sq, seed=11, n_samples=1 << 24, stream_base=0, target_rel_se=rel_q,
+                                          round=4096, with_se=True)
+        sd, sd_se, nd = shp.self_overlaps(Sd, seed=11, n_samples=1 << 22, stream_base=16, target_rel_se=self_rel_se,
+                                          round=256, with_se=True)
+        return sq, sq_se, nq, sd, sd_se, nd
+
+    self_step()  # warm-up
+    (selfq, selfq_se, nq_self, selfd, selfd_se, nd_self), t_self = timed(self_step)
+    nd_self = nd_self.cpu().numpy().astype(np.int64)
     nq_c = q.counts.astype(np.int64)
     nd_c = d.counts.astype(np.int64)
+    self_evals = int((nq_self.cpu().numpy().astype(np.int64) * nq_c).sum() + (nd_self * nd_c).sum())
+    se_kw = dict(self_se_q=selfq_se, self_se_db=selfd_se)
+    best, times = shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=16384, tau=tau, cap=cap, **se_kw)
+    g_ad = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, selfq, selfd, seed=77, tau=tau, round=256, min_n=1024,
+                         cap=cap, **se_kw)
+    torch.cuda.synchronize()
+    res, t_ad = timed(g_ad.replay)
+    nu = res["n_used"].cpu().numpy().astype(np.int64)
+    npairs = len(nu)
     pair_atoms = (nq_c[:, None] + nd_c[None, :]).reshape(-1)
     evals = int(2 * (nu * pair_atoms).sum())
-    # fixed budget at the same guarantee on a strided subsample
+
+    # plain fixed budgets on a strided subsample (same self-overlaps and SEs)
     sub = np.arange(0, d.n_mol, 64)
     dsub = d.subset(sub)
     Ss = shp.shape_set_load(dsub)
-    self_sub = selfd[torch.as_tensor(sub, device=selfd.device)]
-    shp.tanimoto_screen(Sq, Ss, selfq, self_sub, seed=77, n_fixed=cap, variant=-1)  # warm-up
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    fix = shp.tanimoto_screen(Sq, Ss, selfq, self_sub, seed=77, n_fixed=cap)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    t_fix = f0.elapsed_time(f1) / 1e3
+    sub_t = torch.as_tensor(sub, device=selfd.device)
+    self_sub, self_se_sub = selfd[sub_t], selfd_se[sub_t]
+    sub_kw = dict(self_se_q=selfq_se, self_se_db=self_se_sub)
     fixed_pairs = q.n_mol * len(sub)
+
+    def fixed_run(n_fixed):
+        shp.tanimoto_screen(Sq, Ss, selfq, self_sub, seed=77, n_fixed=n_fixed, **sub_kw)  # warm-up
+        return timed(lambda: shp.tanimoto_screen(Sq, Ss, selfq, self_sub, seed=77, n_fixed=n_fixed,
+                                                 with_overlaps=True, **sub_kw))
+
+    def fixed_pairs_per_s(t_sub):
+        # the subsample's screen time scaled to every pair, plus the self-overlaps
+        return npairs / (t_sub * npairs / fixed_pairs + t_self)
+
+    fix, t_fix = fixed_run(cap)
+    # smallest fixed n (multiple of 256) whose full SE(T) meets tau for 99% of
+    # pairs: the pair term scales as n^-1/2 from its value at the cap
+    Sfx = (selfq[:, 1].cpu().numpy()[:, None] + self_sub[:, 1].cpu().numpy()[None, :]).reshape(-1)
+    Ofx = fix["O"][:, 1].cpu().numpy()
+    den = Sfx - Ofx
+    pair_var_cap = (Sfx / den ** 2 * fix["seO"][:, 1].cpu().numpy()) ** 2
+    sq_se = selfq_se[:, 1].cpu().numpy()[:, None]
+    sd_se = self_se_sub[:, 1].cpu().numpy()[None, :]
+    self_var = ((Ofx / den ** 2) ** 2 * (sq_se ** 2 + sd_se ** 2).reshape(-1))
+    room = tau ** 2 - self_var
+    n_need = np.where(room > 0, cap * pair_var_cap / np.maximum(room, 1e-300), np.inf)
+    n99 = int(min(cap, max(256, 256 * np.ceil(np.quantile(n_need, 0.99) / 256))))
+    fix99, t_fix99 = fixed_run(n99)
+    se99 = fix99["seT"][:, 1].cpu().numpy()
+    fixed_pps, fixed99_pps = fixed_pairs_per_s(t_fix), fixed_pairs_per_s(t_fix99)
+
     T_ad = res["T"].cpu().numpy()[:, 1].reshape(q.n_mol, d.n_mol)[:, sub]
     T_fx = fix["T"].cpu().numpy()[:, 1].reshape(q.n_mol, len(sub))
     rho = [float(stats.spearmanr(T_ad[i], T_fx[i]).statistic) for i in range(q.n_mol)]
@@ -547,46 +614,43 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
 
     def stopping_effect(T_a, se_a):
         """Optional stopping: mean of T_adaptive - T_fixed and the share of
-        pairs whose nominal 95% interval (both SEs) covers the difference."""
+        pairs whose nominal 95% interval covers the difference. Both arms
+        share the self-overlaps, so only the pair terms of the two SEs are
+        independent: the interval uses those."""
         se_f = fix["seT"].cpu().numpy()[:, 1].reshape(q.n_mol, len(sub))
+        sv = self_var.reshape(q.n_mol, len(sub))
+        pa = np.maximum(se_a ** 2 - sv, 0.0)
+        pf = np.maximum(se_f ** 2 - sv, 0.0)
         diff = T_a - T_fx
-        z = diff / np.sqrt(se_a ** 2 + se_f ** 2)
+        z = diff / np.sqrt(pa + pf)
         return {"mean_T_minus_fixed": float(diff.mean()), "mean_z": float(z.mean()),
                 "coverage_95": float((np.abs(z) <= 1.959964).mean())}
 
     se_ad_sub = se_ad.reshape(q.n_mol, d.n_mol)[:, sub]
+    self_term = np.sqrt(self_var)
+
     def cv_arm(weights):
         """The adaptive screen with the union slot's control variate; the
         weights (per atom of both sets) come from `weights()`, timed."""
-        c0 = torch.cuda.Event(enable_timing=True)
-        c1 = torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        wq, wd = weights()
-        c1.record(stream)
+        (wq, wd), t_w = timed(weights)
         best_cv, _ = shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=16384, tau=tau, cap=cap,
-                                              omega_q=wq, omega_db=wd)
+                                              omega_q=wq, omega_db=wd, **se_kw)
         g_cv = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, selfq, selfd, seed=77, tau=tau, round=256, min_n=1024,
-                             cap=cap, omega_q=wq, omega_db=wd)
+                             cap=cap, omega_q=wq, omega_db=wd, **se_kw)
         torch.cuda.synchronize()
-        v0 = torch.cuda.Event(enable_timing=True)
-        v1 = torch.cuda.Event(enable_timing=True)
-        v0.record(stream)
-        rcv = g_cv.replay()
-        v1.record(stream)
-        torch.cuda.synchronize()
-        t_cv = v0.elapsed_time(v1) / 1e3
-        t_w = c0.elapsed_time(c1) / 1e3
+        rcv, t_cv = timed(g_cv.replay)
         nu_cv = rcv["n_used"].cpu().numpy().astype(np.int64)
         T_cv = rcv["T"].cpu().numpy()[:, 1].reshape(q.n_mol, d.n_mol)[:, sub]
         rho_cv = [float(stats.spearmanr(T_cv[i], T_fx[i]).statistic) for i in range(q.n_mol)]
         se_cv = rcv["seT"].cpu().numpy()[:, 1]
+        pps = npairs / (t_cv + t_w + t_self)
         return {
             "optional_stopping": stopping_effect(T_cv, se_cv.reshape(q.n_mol, d.n_mol)[:, sub]),
-            "pairs_per_s": npairs / (t_cv + t_w), "seconds": t_cv, "weights_seconds": t_w,
+            "pairs_per_s": pps, "seconds": t_cv, "weights_seconds": t_w,
             "mean_samples_per_direction": float(nu_cv.mean()), "frac_at_cap": float((nu_cv >= cap).mean()),
             "frac_se_met": float((se_cv <= tau * (1 + 1e-6)).mean()),
-            "speedup_vs_fixed": (npairs / (t_cv + t_w)) / (fixed_pairs / t_fix),
-            "speedup_vs_adaptive": t_ad / (t_cv + t_w),
+            "speedup_vs_fixed": pps / fixed_pps, "speedup_vs_p99_fixed": pps / fixed99_pps,
+            "speedup_vs_adaptive": (t_ad + t_self) / (t_cv + t_w + t_self),
             "spearman_rho_vs_fixed": {"mean": float(np.mean(rho_cv)), "min": float(np.min(rho_cv))},
             "tuned_variant": int(best_cv),
         }
@@ -599,18 +663,26 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
     with_fit = cv_arm(lambda: (shp.cv_fit_weights(Sq, seed=91, n_samples=fit_samples),
                                shp.cv_fit_weights(Sd, seed=92, n_samples=fit_samples)))
     with_fit["fit_samples_per_molecule"] = fit_samples
+    pps = npairs / (t_ad + t_self)
     return {
         "workload": f"adaptive screen: 16 queries (20-48 atoms) x {n_db} molecules (18-60, heavy-tailed toward 40), "
-                    f"rounds of 256 per direction, SE(T_union) <= {tau} or {cap} per direction",
-        "launch": "CUDA graph replay (self-overlaps graph, then the persistent adaptive screen graph)",
-        "pairs": npairs, "pairs_per_s": npairs / t_ad, "evals_per_s": evals / t_ad, "seconds": t_ad,
-        "self_overlap_seconds": t_self,
+                    f"rounds of 256 per direction, full SE(T_union) <= {tau} or {cap} per direction",
+        "launch": "self-overlaps (two persistent launches), then the persistent adaptive screen as a CUDA graph",
+        "se": "full delta-method SE(T): pair overlap and both union self-overlaps (stop rule and frac_se_met)",
+        "self_overlaps": {"target_rel_se_db": self_rel_se, "target_rel_se_query": rel_q, "seconds": t_self,
+                          "mean_samples_db": float(nd_self.mean()), "evals": self_evals,
+                          "se_t_term_median": float(np.median(self_term)),
+                          "se_t_term_p99": float(np.quantile(self_term, 0.99))},
+        "pairs": npairs, "pairs_per_s": pps, "evals_per_s": (evals + self_evals) / (t_ad + t_self),
+        "seconds": t_ad,
         "mean_samples_per_direction": float(nu.mean()), "median_samples_per_direction": float(np.median(nu)),
         "frac_at_cap": float((nu >= cap).mean()), "frac_se_met": float((se_ad <= tau * (1 + 1e-6)).mean()),
         "sample_reduction_vs_fixed": 1.0 - float(nu.mean()) / cap,
         "fixed_budget": {"samples_per_direction": cap, "pairs_timed": fixed_pairs,
-                         "pairs_per_s": fixed_pairs / t_fix, "seconds": t_fix},
-        "speedup_pairs_per_s": (npairs / t_ad) / (fixed_pairs / t_fix),
+                         "pairs_per_s": fixed_pps, "seconds": t_fix},
+        "fixed_budget_p99": {"samples_per_direction": n99, "pairs_timed": fixed_pairs, "pairs_per_s": fixed99_pps,
+                             "seconds": t_fix99, "frac_se_met": float((se99 <= tau * (1 + 1e-6)).mean())},
+        "speedup_pairs_per_s": pps / fixed_pps, "speedup_vs_p99_fixed": pps / fixed99_pps,
         "spearman_rho_vs_fixed": {"mean": float(np.mean(rho)), "min": float(np.min(rho))},
         "optional_stopping": stopping_effect(T_ad, se_ad_sub),
         "tuned_variant": int(best), "variant_ms": [round(float(x), 3) for x in times],
@@ -698,7 +770,7 @@ def align_section(shp, torch, n_db: int, rank: int):
             "mean_T_aligned": float(T1.mean()), "frac_improved": float((T1 >= T0 - 0.005).mean())}
 
 
-def end_to_end(shp, torch, q, d, n, steps: int, warmup: int):
+def end_to_end(shp, torch, q, d, n, steps: int, warmup: int, start: int = 0, n_global: int = 0):
     """The same metric through the public API from host arrays: every step
     uploads both molecule sets (shape_set_load), computes self-overlaps and
     the screen, and reads T and SE(T) back to pinned host memory. Steps are
@@ -713,8 +785,9 @@ def end_to_end(shp, torch, q, d, n, steps: int, warmup: int):
     def issue(i):
         Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
         selfq = shp.self_overlaps(Sq, seed=1, n_samples=n, stream_base=0)
-        selfd = shp.self_overlaps(Sd, seed=1, n_samples=n, stream_base=1)
-        res = shp.tanimoto_screen(Sq, Sd, selfq, selfd, seed=SEED_WORKLOAD, n_fixed=n)
+        selfd = shp.self_overlaps(Sd, seed=1, n_samples=n, stream_base=1 + start)
+        res = shp.tanimoto_screen(Sq, Sd, selfq, selfd, seed=SEED_WORKLOAD, n_fixed=n, stream_base=start,
+                                  stream_stride=n_global)
         host_T, host_seT = host[i % 2]
         host_T.copy_(res["T"], non_blocking=True)
         host_seT.copy_(res["seT"], non_blocking=True)

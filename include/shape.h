@@ -47,7 +47,9 @@ extern "C" {
 #define SHP_ENOMEM (-2)   /* device or host allocation failed               */
 #define SHP_ECUDA (-3)    /* a CUDA runtime call failed                      */
 #define SHP_ERANGE (-4)   /* atom count outside 1..SHP_MAX_ATOMS, index out of range */
-#define SHP_ETIMEOUT (-5) /* a bounded device-side wait gave up              */
+#define SHP_ETIMEOUT (-5) /* reserved for a bounded device-side wait that gives
+                             up; no entry point returns it: no kernel of the
+                             library waits on another block or on the host   */
 
 #define SHP_MAX_ATOMS 64
 
@@ -180,7 +182,7 @@ int fo_overlap(shp_set A, const int32_t* ia, shp_set B, const int32_t* ib, int64
 /* Screening settings (Sec. confidence-bounded screening). */
 typedef struct {
   uint64_t seed;        /* Philox key                                              */
-  uint64_t stream_base; /* pair (q, d) uses stream stream_base + q * n_db + d       */
+  uint64_t stream_base; /* pair (q, d) uses stream stream_base + q * stride + d     */
   uint32_t n_fixed;     /* > 0: fixed budget, samples per direction (>= 2);
                            0: adaptive (fields below)                              */
   uint32_t flags;       /* SHP_ANTITHETIC (fixed budget only; both directions are
@@ -200,6 +202,15 @@ typedef struct {
                            Q and of D (device, set atom order), both or neither;
                            NULL = plain estimator                                  */
   const float* omega_db;
+  const double* self_se_q;  /* standard errors of self_q / self_db ([n][2] device,
+                               same layout), both or neither; NULL = the
+                               self-overlaps are exact                             */
+  const double* self_se_db;
+  uint64_t stream_stride;   /* the stride above; 0 = n_db. A database shard
+                               [start, end) of a global database of n_global
+                               molecules uses stream_base = start and stride =
+                               n_global, and reproduces the global screen's
+                               numbers for its pairs                        */
 } shp_screen;
 
 /*
@@ -211,6 +222,11 @@ typedef struct {
  * p = q * n_db + d and slot s:
  *   T[p][s]   = O / (S_Q + S_D - O)
  *   seT[p][s] = (S_Q + S_D) / (S_Q + S_D - O)^2 * SE(O)   (delta method)
+ * and, when the self-overlaps are estimates with standard errors
+ * cfg->self_se_q, cfg->self_se_db (e.g. union_self_estimate's self_se), the
+ * full delta-method SE of T(O, S_Q, S_D), whose terms are independent:
+ *   seT^2 = ((S_Q + S_D) / den^2 SE(O))^2 + (O / den^2)^2 (se_Q^2 + se_D^2),
+ *   den = S_Q + S_D - O
  *   O_out[p][s], seO_out[p][s] (double, may be NULL)
  *   n_used[p] samples drawn per direction (may be NULL)
  * Control variate (omega_q, omega_db given): the union overlap is estimated
@@ -219,9 +235,10 @@ typedef struct {
  * weights): unbiased for any weights; the first-order slot is unchanged.
  * Fixed budget: n_fixed samples per direction. Adaptive (n_fixed == 0):
  * rounds of `round` samples per direction are drawn until, after at least
- * min_n, the watched SE(T) (computed in FP32 from the running sums) is
- * <= tau, or cap is reached; the samples are the first n_used of the same
- * streams a fixed budget would draw.
+ * min_n, the watched SE(T) (computed in FP32 from the running sums, and
+ * the full SE when self-overlap SEs are given) is <= tau, or cap is reached;
+ * the samples are the first n_used of the same streams a fixed budget would
+ * draw.
  *   self_q [n_q][2], self_db [n_db][2] double device
  *   T, seT [n_q * n_db][2] float device
  * Work is balanced by a persistent kernel that takes pairs largest-first
@@ -362,7 +379,12 @@ int union_attributions(shp_set S, uint64_t seed, uint64_t stream_base, uint32_t 
  * residual of 1e-6 (at most 4 N iterations).
  *   idx [n] device int32 molecule ids, or NULL for molecules 0 .. n-1
  *   omega [n_atoms] float device: written for the atoms of the listed
- *   molecules (set atom order); other entries are left as they are.
+ *   molecules (set atom order); other entries are left as they are. An id
+ *   outside 0 .. n_mol-1 (not checked on the host: idx is device memory)
+ *   is skipped and writes nothing.
+ * The conjugate-gradient iteration stops early, keeping its last finite
+ * iterate, if a step becomes non-finite or the curvature p.Gp is not
+ * positive (possible for ridge = 0 and nearly coincident atoms).
  * Errors: SHP_EINVAL (NULL, bad n_samples, flags or ridge), SHP_ERANGE.
  */
 int cv_fit_weights(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, float ridge, float* omega,
@@ -380,6 +402,29 @@ int cv_fit_weights(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, f
 int union_volume_cv(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, const float* omega,
                     float target_rel_se, uint32_t round, double* vol, double* vol_se, uint32_t* n_used,
                     void* stream);
+
+/*
+ * Union volumes and union self-overlaps of molecules S[idx[k]] to a stated
+ * precision (Eq. expectation with f = u/m and Eq. union-is with B = A; the
+ * self-overlaps are the O_AA of the Tanimoto, Sec. union). Same samples as
+ * union_volume_estimate (tag SHP_TAG_SELF, stream mc->stream_base + k, no
+ * flags). With omega (per set atom, float device; NULL = plain) both carry
+ * the weighted-Gaussian control variate u~ = sum_i omega_i g_i:
+ *   V    = sum_i omega_i v_i                  + Z E_q[(u - u~) / m]
+ *   O_AA = sum_ij omega_i omega_j int g_i g_j + Z E_q[(u^2 - u~^2) / m]
+ * (not in the paper; unbiased for any omega). target_rel_se <= 0:
+ * mc->n_samples samples. target_rel_se > 0: rounds of `round` samples (a
+ * multiple of 256 dividing mc->n_samples, which is then the cap) until the
+ * watched estimate (watch 0: volume, 1: self-overlap) has SE / estimate <=
+ * target_rel_se, checked in FP32 after each round.
+ *   idx [n] int32 device or NULL (= 0..n-1); vol, vol_se, self_ov, self_se
+ *   [n] double and n_used [n] uint32 device, each may be NULL (not both vol
+ *   and self_ov).
+ * Errors: SHP_EINVAL, SHP_ERANGE, SHP_ENOMEM, SHP_ECUDA.
+ */
+int union_self_estimate(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, const float* omega,
+                        float target_rel_se, uint32_t round, uint32_t watch, double* vol, double* vol_se,
+                        double* self_ov, double* self_se, uint32_t* n_used, void* stream);
 
 #define SHP_MLP_IN 33
 #define SHP_MLP_HIDDEN 64
@@ -427,6 +472,9 @@ int mlp_loss_grad(const float* params, const float* x, const float* target, cons
  * device address (make that first call before any stream capture). A call
  * overwrites the part of the array it uses, so nothing carries over between
  * calls; calls that overlap on the GPU (e.g. on two streams) race on it.
+ * The looked-up address is kept for the life of the process: after a
+ * cudaDeviceReset of that device the library must not be called on it again
+ * (the cached address would then be stale).
  */
 int mlp_loss_grad_noalloc(const float* params, const float* x, const float* target,
                           const int32_t* rows, int64_t n, float* grad, double* loss, void* stream);

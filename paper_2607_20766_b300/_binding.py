@@ -26,7 +26,8 @@ EXPORTS = ("shp_last_error", "shp_version", "shp_fail_next_allocations", "shape_
            "shape_set_tables", "overlap_estimate", "union_volume_estimate", "fo_overlap",
            "tanimoto_screen", "shp_screen_variants", "shp_screen_variant_info", "tanimoto_screen_tune", "align_crn_points",
            "overlap_pose_grad", "align_rigid", "shape_set_frames", "union_attributions", "union_volume_cv",
-           "cv_features", "mlp_forward", "mlp_loss_grad", "mlp_adam", "mlp_loss_grad_noalloc", "cv_fit_weights")
+           "cv_features", "mlp_forward", "mlp_loss_grad", "mlp_adam", "mlp_loss_grad_noalloc", "cv_fit_weights",
+           "union_self_estimate")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 33, 64, 6401
 OBJ_FO, OBJ_UNION, OBJ_FO_CLOSED = 0, 1, 2
 
@@ -42,7 +43,8 @@ class ShpScreen(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("stream_base", ctypes.c_uint64), ("n_fixed", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("tau", ctypes.c_float), ("round", ctypes.c_uint32),
                 ("min_n", ctypes.c_uint32), ("cap", ctypes.c_uint32), ("watch", ctypes.c_uint32),
-                ("variant", ctypes.c_int32), ("omega_q", ctypes.c_void_p), ("omega_db", ctypes.c_void_p)]
+                ("variant", ctypes.c_int32), ("omega_q", ctypes.c_void_p), ("omega_db", ctypes.c_void_p),
+                ("self_se_q", ctypes.c_void_p), ("self_se_db", ctypes.c_void_p), ("stream_stride", ctypes.c_uint64)]
 
 
 class ShpAlign(ctypes.Structure):
@@ -88,6 +90,8 @@ def load_library():
         "union_attributions": [_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, _P],
         "union_volume_cv": [_P, _P, ctypes.c_int64, _P, _P, ctypes.c_float, ctypes.c_uint32, _P, _P, _P, _P],
         "cv_features": [_P, _P, _P],
+        "union_self_estimate": [_P, _P, ctypes.c_int64, _P, _P, ctypes.c_float, ctypes.c_uint32, ctypes.c_uint32, _P,
+                                _P, _P, _P, _P, _P],
         "cv_fit_weights": [_P, _P, ctypes.c_int64, _P, ctypes.c_float, _P, _P],
         "mlp_forward": [_P, _P, _P, ctypes.c_int64, _P, _P],
         "mlp_loss_grad": [_P, _P, _P, _P, ctypes.c_int64, _P, _P, _P],
@@ -246,11 +250,20 @@ def fo_overlap(A: ShapeSet, ia, B: ShapeSet, ib, pose=None, stream=None, out=Non
 def screen_config(seed: int, n_fixed: int = 0, tau: float = 0.005, round: int = 256, min_n: int = 1024,
                   cap: int = 65536, watch: int = 1, flags: int = 0, stream_base: int = 0,
                   variant: int = -1, omega_q: torch.Tensor | None = None,
-                  omega_db: torch.Tensor | None = None) -> ShpScreen:
+                  omega_db: torch.Tensor | None = None, self_se_q: torch.Tensor | None = None,
+                  self_se_db: torch.Tensor | None = None, stream_stride: int = 0) -> ShpScreen:
     """A shp_screen: fixed budget when n_fixed > 0, else adaptive (tau, round, min_n, cap, watch);
-    omega_q/omega_db (float32 device, per set atom): control variate of the union slot."""
+    omega_q/omega_db (float32 device, per set atom): control variate of the union slot;
+    self_se_q/self_se_db (float64 device, [n, 2]): SEs of the self-overlaps (full delta-method SE(T));
+    pair (q, d) uses Philox stream stream_base + q * stream_stride + d (stride 0 = n_db)."""
     return ShpScreen(seed, stream_base, n_fixed, flags, tau, round, min_n, cap, watch, variant,
-                     _dptr(omega_q), _dptr(omega_db))
+                     _dptr(omega_q), _dptr(omega_db), _dptr(self_se_q), _dptr(self_se_db), stream_stride)
+
+
+def _self_se(t, S: "ShapeSet"):
+    if t is None:
+        return None
+    return t.to(device=S.device, dtype=torch.float64).contiguous()
 
 
 def _weights(omega, S: "ShapeSet"):
@@ -263,13 +276,18 @@ def tanimoto_screen(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: tor
                     n_fixed: int = 0, flags: int = 0, stream_base: int = 0, stream=None, with_overlaps: bool = False,
                     out=None, tau: float = 0.005, round: int = 256, min_n: int = 1024, cap: int = 65536,
                     watch: int = 1, variant: int = -1, omega_q: torch.Tensor | None = None,
-                    omega_db: torch.Tensor | None = None):
+                    omega_db: torch.Tensor | None = None, self_se_q: torch.Tensor | None = None,
+                    self_se_db: torch.Tensor | None = None, stream_stride: int = 0):
     """Screen every query against every database molecule (fixed budget when
     n_fixed > 0, else adaptive). Returns dict T, seT ([n_q * n_db, 2]
     float32), n_used ([n_q * n_db] int32 view of uint32) and, with
     with_overlaps, O, seO ([n_q * n_db, 2] float64). omega_q, omega_db
     (per-atom weights of each set) turn on the union slot's control
-    variate."""
+    variate; self_se_q, self_se_db (SEs of self_q, self_db) make seT, and
+    the adaptive stop rule, the full delta-method SE. Pair (q, d) draws from
+    stream stream_base + q * stream_stride + d (stream_stride 0 = n_db): a
+    database shard [start, end) of n_global molecules passes start and
+    n_global to reproduce the whole screen's numbers."""
     dev = Q.device
     npairs = Q.n_mol * D.n_mol
     if out is None:
@@ -280,7 +298,9 @@ def tanimoto_screen(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: tor
             out["O"] = torch.empty((npairs, 2), dtype=torch.float64, device=dev)
             out["seO"] = torch.empty((npairs, 2), dtype=torch.float64, device=dev)
     omega_q, omega_db = _weights(omega_q, Q), _weights(omega_db, D)
-    cfg = screen_config(seed, n_fixed, tau, round, min_n, cap, watch, flags, stream_base, variant, omega_q, omega_db)
+    self_se_q, self_se_db = _self_se(self_se_q, Q), _self_se(self_se_db, D)
+    cfg = screen_config(seed, n_fixed, tau, round, min_n, cap, watch, flags, stream_base, variant, omega_q, omega_db,
+                        self_se_q, self_se_db, stream_stride)
     self_q = self_q.to(device=dev, dtype=torch.float64).contiguous()
     self_db = self_db.to(device=dev, dtype=torch.float64).contiguous()
     _check(load_library().tanimoto_screen(Q.handle, D.handle, ctypes.byref(cfg), _dptr(self_q), _dptr(self_db),
@@ -310,7 +330,8 @@ def screen_variant_info(v: int) -> dict:
 def tanimoto_screen_tune(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: torch.Tensor, seed: int,
                          n_fixed: int = 0, n_sample: int = 4096, stream=None, tau: float = 0.005, round: int = 256,
                          min_n: int = 1024, cap: int = 65536, watch: int = 1, omega_q: torch.Tensor | None = None,
-                         omega_db: torch.Tensor | None = None):
+                         omega_db: torch.Tensor | None = None, self_se_q: torch.Tensor | None = None,
+                         self_se_db: torch.Tensor | None = None):
     """Autotune the screen's launch variant on n_sample pairs (with the
     control variate when omega_q/omega_db are given); returns (best variant,
     per-variant milliseconds, -1 where not valid)."""
@@ -320,7 +341,9 @@ def tanimoto_screen_tune(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db
     seT = torch.empty((npairs, 2), dtype=torch.float32, device=dev)
     nu = torch.empty(npairs, dtype=torch.int32, device=dev)
     omega_q, omega_db = _weights(omega_q, Q), _weights(omega_db, D)
-    cfg = screen_config(seed, n_fixed, tau, round, min_n, cap, watch, omega_q=omega_q, omega_db=omega_db)
+    self_se_q, self_se_db = _self_se(self_se_q, Q), _self_se(self_se_db, D)
+    cfg = screen_config(seed, n_fixed, tau, round, min_n, cap, watch, omega_q=omega_q, omega_db=omega_db,
+                        self_se_q=self_se_q, self_se_db=self_se_db)
     nv = screen_variants()
     times = np.empty(nv, np.float32)
     best = ctypes.c_int32(-1)
@@ -332,18 +355,33 @@ def tanimoto_screen_tune(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db
     return best.value, times
 
 
-def self_overlaps(S: ShapeSet, seed: int, n_samples: int, stream_base: int = 0, stream=None):
+def self_overlaps(S: ShapeSet, seed: int, n_samples: int, stream_base: int = 0, stream=None,
+                  target_rel_se: float = 0.0, round: int = 256, omega=None, with_se: bool = False):
     """[n_mol, 2] float64 device tensor: slot 0 closed-form first-order
-    self-overlap, slot 1 union self-overlap estimate (n_samples draws)."""
+    self-overlap, slot 1 union self-overlap estimate (n_samples draws, or
+    rounds of `round` up to the cap n_samples until its relative SE is
+    <= target_rel_se; omega: control-variate weights per set atom). With
+    with_se, returns (self, se, n_used): se [n_mol, 2] (slot 0 zero, the
+    closed form is exact) and the samples per molecule."""
     dev = S.device
     idx = torch.arange(S.n_mol, dtype=torch.int32, device=dev)
     out = torch.empty((S.n_mol, 2), dtype=torch.float64, device=dev)
     fo = fo_overlap(S, idx, S, idx, stream=stream)
-    vol, vse, so, sse = union_volume_estimate(S, idx, seed=seed, n_samples=n_samples, stream_base=stream_base,
-                                              stream=stream)
+    if target_rel_se <= 0 and omega is None and not with_se:
+        vol, vse, so, sse = union_volume_estimate(S, idx, seed=seed, n_samples=n_samples, stream_base=stream_base,
+                                                  stream=stream)
+        nu = None
+    else:
+        _, _, so, sse, nu = union_self_estimate(S, None, omega=omega, seed=seed, n_samples=n_samples,
+                                                target_rel_se=target_rel_se, round=round, watch=1,
+                                                stream_base=stream_base, stream=stream)
     out[:, 0] = fo
     out[:, 1] = so
-    return out
+    if not with_se:
+        return out
+    se = torch.zeros((S.n_mol, 2), dtype=torch.float64, device=dev)
+    se[:, 1] = sse
+    return out, se, nu
 
 
 # ---------------------------------------------------------------- alignment
@@ -446,6 +484,29 @@ def union_volume_cv(S: ShapeSet, idx=None, omega=None, seed: int = 0, n_samples:
     _check(load_library().union_volume_cv(S.handle, _dptr(idx), n, ctypes.byref(mc), _dptr(omega), target_rel_se,
                                           round, _dptr(vol), _dptr(se), _dptr(nu), _stream(stream)))
     return vol, se, nu
+
+
+def union_self_estimate(S: ShapeSet, idx=None, omega=None, seed: int = 0, n_samples: int = 4096,
+                        target_rel_se: float = 0.0, round: int = 256, watch: int = 1, stream_base: int = 0,
+                        stream=None):
+    """(vol, vol_se, self_ov, self_se, n_used): union volumes and union
+    self-overlaps, plain or with the control variate omega, fixed n_samples
+    or rounds until the watched estimate (0 volume, 1 self-overlap) reaches
+    target_rel_se (n_samples is then the cap)."""
+    dev = S.device
+    if idx is not None:
+        idx = _device_i32(idx, dev)
+        n = idx.numel()
+    else:
+        n = S.n_mol
+    if omega is not None:
+        omega = torch.as_tensor(omega, dtype=torch.float32, device=dev).contiguous()
+    outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4)]
+    nu = torch.empty(n, dtype=torch.int32, device=dev)
+    mc = ShpMC(seed, stream_base, n_samples, 0)
+    _check(load_library().union_self_estimate(S.handle, _dptr(idx), n, ctypes.byref(mc), _dptr(omega), target_rel_se,
+                                              round, watch, *(_dptr(t) for t in outs), _dptr(nu), _stream(stream)))
+    return (*outs, nu)
 
 
 def cv_fit_weights(S: ShapeSet, seed: int, n_samples: int = 1024, stream_base: int = 0, ridge: float = 1e-6,

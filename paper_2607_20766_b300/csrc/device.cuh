@@ -102,15 +102,4 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Error-free-ish accumulation of FP32 batch partials: hi + lo carries about
-// 48 significant bits (Fast2Sum, valid while |hi| >= |x|, i.e. for sums of
-// non-negative terms and for any term small against the running sum).
-__device__ __forceinline__ void acc2(float& hi, float& lo, float x) {
-  const float t = hi + x;
-  const float big = fabsf(hi) >= fabsf(x) ? hi : x;
-  const float sml = fabsf(hi) >= fabsf(x) ? x : hi;
-  lo += (big - t) + sml;
-  hi = t;
-}
-
 }  // namespace shp

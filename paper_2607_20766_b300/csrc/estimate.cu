@@ -12,9 +12,9 @@
 // Each lane then draws SP sample pairs per batch (64 SP samples per warp)
 // and evaluates every atom of both molecules: four FP32 FMAs for the
 // exponent, one SFU exp2, a packed FP32x2 add for the first-order sum and an
-// FMA for the union product. FP32 batch partials of values shifted by a
-// warp-uniform constant are folded into a hi/lo pair per lane and reduced
-// over the warp with compensated FP32 sums; the epilogue runs in FP64.
+// FMA for the union product. FP32 batch partials (the lane's 2 SP samples) of
+// values shifted by a warp-uniform constant are added to FP64 running sums
+// per lane, reduced over the warp in FP64; the epilogue runs in FP64.
 //
 // Launch variants (SP, exponent form, warps per CTA, CTAs per SM) are
 // template instances; tanimoto_screen_tune times them and keeps the fastest.
@@ -38,10 +38,11 @@ struct __align__(16) CoefT {
   float4 bzw;  // bz, bz, om, om
 };
 
-// Running per-lane sums of one proposal direction: shifted sums
-// {fa, fa^2, fb, fb^2} as hi + lo pairs, and the warp-uniform shifts.
+// Running per-lane sums of one proposal direction: FP64 sums of the shifted
+// values {fa, fa^2, fb, fb^2} (each batch adds its FP32 partial over the
+// lane's 2 SP samples), and the warp-uniform shifts.
 struct DirState {
-  float hi[4], lo[4];
+  double s[4];
   float K[2];
 };
 
@@ -221,7 +222,7 @@ __device__ __forceinline__ void eval_table(const CoefT* __restrict__ tab, int n,
 
 __device__ __forceinline__ void dir_init(DirState& s) {
 #pragma unroll
-  for (int t = 0; t < 4; ++t) { s.hi[t] = 0.f; s.lo[t] = 0.f; }
+  for (int t = 0; t < 4; ++t) s.s[t] = 0.0;
   s.K[0] = s.K[1] = 0.f;
 }
 
@@ -265,7 +266,7 @@ __device__ __forceinline__ void draw_batch(const float4* __restrict__ samp, cons
 //   cross: fa = m_Y (first order), fb = (u_X / m_X) u_Y (union), with kCV
 //          fb = (u_X u_Y - ut_X ut_Y) / m_X (union residual, ut = sum om g)
 //   self:  fa = u_X / m_X (volume), with kCV (u_X - ut_X) / m_X,
-//          fb = u_X^2 / m_X (self-overlap)
+//          fb = u_X^2 / m_X (self-overlap), with kCV (u_X^2 - ut_X^2) / m_X
 // With antithetic pairs the unit is the mean of a sample and its
 // reflection. The first batch sets the shifts from sample 0.
 template <bool kSelf, int SP, int kForm, bool kCV = false>
@@ -284,13 +285,15 @@ __device__ __forceinline__ void eval_batch(const CoefT* __restrict__ tx, const C
   }
   eval_table<SP, kForm, kCV>(tx, nx, rx, ry, rz, rr, m, q, ut);
   if (kSelf) {
-    // volume: fa = u/m (or (u - ut)/m with the control variate), fb = u^2/m
+    // volume: fa = u/m (or (u - ut)/m with the control variate), self-overlap:
+    // fb = u^2/m (or (u^2 - ut^2)/m)
 #pragma unroll
     for (int p = 0; p < SP; ++p) {
       const float ux = 1.f - q[p].x, uy = 1.f - q[p].y;
       const float ix = __fdividef(1.f, m[p].x), iy = __fdividef(1.f, m[p].y);
       fa[p] = kCV ? make_float2((ux - ut[p].x) * ix, (uy - ut[p].y) * iy) : make_float2(ux * ix, uy * iy);
-      fb[p] = make_float2(ux * ux * ix, uy * uy * iy);
+      fb[p] = kCV ? make_float2(fmaf(ux, ux, -ut[p].x * ut[p].x) * ix, fmaf(uy, uy, -ut[p].y * ut[p].y) * iy)
+                  : make_float2(ux * ux * ix, uy * uy * iy);
     }
   } else {
     float2 w[SP], wt[SP];
@@ -343,7 +346,7 @@ __device__ __forceinline__ void eval_batch(const CoefT* __restrict__ tx, const C
     }
   }
 #pragma unroll
-  for (int t = 0; t < 4; ++t) acc2(st.hi[t], st.lo[t], acc[t]);
+  for (int t = 0; t < 4; ++t) st.s[t] += (double)acc[t];
 }
 
 // One batch of one direction (draw, evaluate, accumulate) by a single warp;
@@ -358,20 +361,6 @@ __device__ __forceinline__ void run_batch(WarpTables& T, int nx, int ny, uint32_
   eval_batch<kSelf, SP, kForm, kCV>(tx ? tx : T.x, ty ? ty : T.y, nx, ny, b, n, anti, lane, st, rx, ry, rz, rr);
 }
 
-// Compensated FP32 warp sum of hi + lo; lane 0's (hi, lo) carries the total.
-__device__ __forceinline__ void warp_sum2(float& hi, float& lo) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-    const float s = hi + h2;
-    const float bb = s - hi;
-    const float e = (hi - (s - bb)) + (h2 - bb);
-    hi = s;
-    lo = lo + l2 + e;
-  }
-}
-
 // est = Z mean, se = Z sqrt(s^2 / n) (n-1 sample variance, Eq. var) from
 // sums s, s2 of the values shifted by K.
 __device__ __forceinline__ void finish(double Z, double s, double s2, double K, double n, double& est,
@@ -383,14 +372,10 @@ __device__ __forceinline__ void finish(double Z, double s, double s2, double K, 
   se = Z * sqrt(var / n);
 }
 
-// Warp totals of a direction (valid in lane 0): sums[4] in FP64.
+// Warp totals of a direction (in every lane): sums[4] in FP64.
 __device__ __forceinline__ void dir_totals(const DirState& st, double sums[4]) {
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    float h = st.hi[t], l = st.lo[t];
-    warp_sum2(h, l);
-    sums[t] = (double)h + (double)l;
-  }
+  for (int t = 0; t < 4; ++t) sums[t] = warp_sum(st.s[t]);
 }
 
 enum Mode { kPairs = 0, kScreen = 1, kAdaptive = 2 };
@@ -406,8 +391,11 @@ struct CrossArgs {
   // screen modes
   const int32_t* order_b;
   int32_t n_q, n_db;
+  uint64_t stream_stride;  // pair (q, d) uses stream stream_base + q * stream_stride + d
   const double* self_q;
   const double* self_db;
+  const double* self_se_q;   // standard errors of self_q / self_db, or NULL (exact)
+  const double* self_se_db;
   float* T;
   float* seT;
   double* O;
@@ -483,23 +471,32 @@ __device__ void pair_epilogue(const CrossArgs& args, int32_t xa, int32_t xb, int
       const double S = args.self_q[2 * (int64_t)xa + slot] + args.self_db[2 * (int64_t)xb + slot];
       const double den = S - e[slot];
       args.T[2 * out_idx + slot] = (float)(e[slot] / den);
-      args.seT[2 * out_idx + slot] = (float)(fabs(S / (den * den)) * sd[slot]);
+      // delta method: dT/dO = S / den^2 (the paper's term) and, for
+      // estimated self-overlaps, dT/dO_QQ = dT/dO_DD = -O / den^2
+      const double dO = S / (den * den);
+      double var_t = dO * dO * sd[slot] * sd[slot];
+      if (args.self_se_q) {
+        const double sq = args.self_se_q[2 * (int64_t)xa + slot], sdb = args.self_se_db[2 * (int64_t)xb + slot];
+        const double dS = e[slot] / (den * den);
+        var_t += dS * dS * (sq * sq + sdb * sdb);
+      }
+      args.seT[2 * out_idx + slot] = (float)sqrt(var_t);
       if (args.O) args.O[2 * out_idx + slot] = e[slot];
       if (args.seO) args.seO[2 * out_idx + slot] = sd[slot];
     }
   }
 }
 
-// FP32 SE(T) of the watched slot from the running sums (adaptive stop rule).
+// FP32 SE(T) of the watched slot from the running sums (adaptive stop rule),
+// with the self-overlaps' own errors when their SEs are given.
 __device__ __forceinline__ float watched_se_t(const CrossArgs& args, const DirState& sa, const DirState& sb, int32_t xa,
                                               int32_t xb, float n, float C = 0.f) {
   const bool w = args.watch != 0;
-  float h[4] = {w ? sa.hi[2] : sa.hi[0], w ? sa.hi[3] : sa.hi[1], w ? sb.hi[2] : sb.hi[0], w ? sb.hi[3] : sb.hi[1]};
-  float l[4] = {w ? sa.lo[2] : sa.lo[0], w ? sa.lo[3] : sa.lo[1], w ? sb.lo[2] : sb.lo[0], w ? sb.lo[3] : sb.lo[1]};
+  double h[4] = {w ? sa.s[2] : sa.s[0], w ? sa.s[3] : sa.s[1], w ? sb.s[2] : sb.s[0], w ? sb.s[3] : sb.s[1]};
 #pragma unroll
-  for (int i = 0; i < 4; ++i) warp_sum2(h[i], l[i]);
+  for (int i = 0; i < 4; ++i) h[i] = warp_sum(h[i]);
   const float ZA = (float)args.A.Z[xa], ZB = (float)args.B.Z[xb];
-  const float s1a = h[0] + l[0], s2a = h[1] + l[1], s1b = h[2] + l[2], s2b = h[3] + l[3];
+  const float s1a = (float)h[0], s2a = (float)h[1], s1b = (float)h[2], s2b = (float)h[3];
   const float va = fmaxf((s2a - s1a * s1a / n) / (n - 1.f), 0.f);
   const float vb = fmaxf((s2b - s1b * s1b / n) / (n - 1.f), 0.f);
   const float ea = ZA * ((w ? sa.K[1] : sa.K[0]) + s1a / n), eb = ZB * ((w ? sb.K[1] : sb.K[0]) + s1b / n);
@@ -507,7 +504,15 @@ __device__ __forceinline__ float watched_se_t(const CrossArgs& args, const DirSt
   const float seO = 0.5f * sqrtf((ZA * ZA * va + ZB * ZB * vb) / n);
   const float S = (float)(args.self_q[2 * (int64_t)xa + args.watch] + args.self_db[2 * (int64_t)xb + args.watch]);
   const float den = S - O;
-  return fabsf(S / (den * den)) * seO;
+  const float dO = S / (den * den);
+  float var_t = dO * dO * seO * seO;
+  if (args.self_se_q) {
+    const float sq = (float)args.self_se_q[2 * (int64_t)xa + args.watch];
+    const float sdb = (float)args.self_se_db[2 * (int64_t)xb + args.watch];
+    const float dS = O / (den * den);
+    var_t = fmaf(dS * dS, fmaf(sq, sq, sdb * sdb), var_t);
+  }
+  return sqrtf(var_t);
 }
 
 // Stages direction dir of a pair (0: A sampled and B evaluated, 1: the
@@ -574,8 +579,9 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) cross_kernel(const Cr
       }
       continue;
     }
-    const uint32_t slo = (uint32_t)(args.stream_base + (uint64_t)out_idx);
-    const uint32_t shi = (uint32_t)((args.stream_base + (uint64_t)out_idx) >> 32);
+    const uint64_t sid = args.stream_base + (MODE == kPairs ? (uint64_t)out_idx
+                                                            : (uint64_t)xa * args.stream_stride + (uint64_t)xb);
+    const uint32_t slo = (uint32_t)sid, shi = (uint32_t)(sid >> 32);
     const MolRef MA = mol_ref(args.A, xa), MB = mol_ref(args.B, xb);
     DirState& sa = T.st[0][lane];
     DirState& sb = T.st[1][lane];
@@ -888,6 +894,7 @@ int screen_args(shp_set Q, shp_set D, const shp_screen* cfg, const double* self_
   a.item_stride = 1;
   a.key = Key{(uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32)};
   a.stream_base = cfg->stream_base;
+  a.stream_stride = cfg->stream_stride ? cfg->stream_stride : (uint64_t)D->n_mol;
   a.anti = (cfg->flags & SHP_ANTITHETIC) != 0;
   a.symmetric = true;
   if ((cfg->omega_q == nullptr) != (cfg->omega_db == nullptr)) {
@@ -896,6 +903,12 @@ int screen_args(shp_set Q, shp_set D, const shp_screen* cfg, const double* self_
   }
   a.omega_a = cfg->omega_q;
   a.omega_b = cfg->omega_db;
+  if ((cfg->self_se_q == nullptr) != (cfg->self_se_db == nullptr)) {
+    set_error("%s: give both self-overlap SE arrays or neither", who);
+    return SHP_EINVAL;
+  }
+  a.self_se_q = cfg->self_se_q;
+  a.self_se_db = cfg->self_se_db;
   return SHP_OK;
 }
 
@@ -1112,16 +1125,24 @@ struct CVArgs {
   Key key;
   uint64_t stream_base;
   uint32_t n;          // fixed budget (samples), or the cap when adaptive
-  float target;        // > 0: stop once SE / V <= target (checked every round_b batches)
+  float target;        // > 0: stop once SE / estimate <= target for the watched
+                       // estimand (checked every round_b batches)
   uint32_t round_b;
+  int watch;           // 0: volume, 1: self-overlap
   double* vol;
   double* vol_se;
+  double* self_ov;
+  double* self_se;
   uint32_t* n_used;
   unsigned long long* queue;
 };
 
-// Union volume with the weighted-Gaussian control variate: V = sum_i om_i v_i
-// + Z mean((u - sum_i om_i g_i) / m), same samples as union_volume_estimate.
+// Union volume and union self-overlap, optionally with the weighted-Gaussian
+// control variate ut = sum_i om_i g_i:
+//   V    = sum_i om_i v_i                   + Z mean((u - ut) / m)
+//   O_XX = sum_ij om_i om_j integral g_i g_j + Z mean((u^2 - ut^2) / m)
+// same samples as union_volume_estimate; fixed budget or rounds until the
+// watched estimate reaches a relative SE.
 template <bool kCV>
 __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_volume_kernel(const CVArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1137,22 +1158,27 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_volume_kernel(const CVArg
     const int32_t xm = a.idx ? a.idx[item] : (int32_t)item;
     if (xm < 0 || xm >= a.S.n_mol) {
       if (lane == 0) {
-        a.vol[item] = __longlong_as_double(0x7ff8000000000000ll);
-        if (a.vol_se) a.vol_se[item] = __longlong_as_double(0x7ff8000000000000ll);
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        if (a.vol) a.vol[item] = nan;
+        if (a.vol_se) a.vol_se[item] = nan;
+        if (a.self_ov) a.self_ov[item] = nan;
+        if (a.self_se) a.self_se[item] = nan;
         if (a.n_used) a.n_used[item] = 0;
       }
       continue;
     }
     const MolRef M = mol_ref(a.S, xm);
     stage_direction(T, a.S, M, nullptr, nullptr, M, nullptr, lane, kCV ? a.omega : nullptr);
-    // closed-form part sum_i om_i v_i, v_i = p_i (pi / alpha_i)^{3/2}, in FP64
-    double closed = 0.0;
+    // closed-form parts: sum_i om_i v_i, v_i = p_i (pi / alpha_i)^{3/2}, in
+    // FP64, and sum_ij om_i om_j integral g_i g_j (Eq. fo with weights)
+    double closed = 0.0, closed_s = 0.0;
     if (kCV) {
       for (int i = lane; i < M.n; i += 32) {
         const double t = 3.141592653589793 / (double)a.S.atom[M.a0 + i].w;
         closed += (double)a.omega[M.a0 + i] * exp2((double)a.S.aux[M.a0 + i].y) * t * sqrt(t);
       }
       closed = warp_sum(closed);
+      closed_s = weighted_fo(a.S, M, a.omega, a.S, M, a.omega, lane);
     }
     const double Z = a.S.Z[xm];
     DirState& st = T.st[0][lane];
@@ -1175,12 +1201,10 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_volume_kernel(const CVArg
           run_batch<true, SP, 5, kCV>(T, M.n, 0, k, n_now, a.key, slo, shi, SHP_TAG_SELF, false, lane, st);
         b = nxt;
         if (b >= cap_b) break;
-        float h1 = st.hi[0], l1 = st.lo[0], h2 = st.hi[1], l2 = st.lo[1];
-        warp_sum2(h1, l1);
-        warp_sum2(h2, l2);
-        const float nf = (float)n_now, s1 = h1 + l1, s2 = h2 + l2;
+        const int w = a.watch;
+        const float nf = (float)n_now, s1 = (float)warp_sum(st.s[2 * w]), s2 = (float)warp_sum(st.s[2 * w + 1]);
         const float var = fmaxf((s2 - s1 * s1 / nf) / (nf - 1.f), 0.f);
-        const float V = (float)closed + (float)Z * (st.K[0] + s1 / nf);
+        const float V = (float)(w ? closed_s : closed) + (float)Z * (st.K[w] + s1 / nf);
         const float se = (float)Z * sqrtf(var / nf);
         const int stop = __shfl_sync(0xffffffffu, (int)(se <= a.target * fabsf(V)), 0);
         if (stop) break;
@@ -1192,8 +1216,11 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_volume_kernel(const CVArg
     if (lane == 0) {
       double e, sd;
       finish(Z, s[0], s[1], st.K[0], (double)n_done, e, sd);
-      a.vol[item] = closed + e;
+      if (a.vol) a.vol[item] = closed + e;
       if (a.vol_se) a.vol_se[item] = sd;
+      finish(Z, s[2], s[3], st.K[1], (double)n_done, e, sd);
+      if (a.self_ov) a.self_ov[item] = closed_s + e;
+      if (a.self_se) a.self_se[item] = sd;
       if (a.n_used) a.n_used[item] = n_done;
     }
     __syncwarp();
@@ -1243,7 +1270,7 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_fit_kernel(const FitArgs 
     if (item >= (unsigned long long)a.n_items) break;
     if (lane == 0) next = atomicAdd(a.queue, 1ull);
     const int32_t xm = a.idx ? a.idx[item] : (int32_t)item;
-    if (xm < 0 || xm >= a.S.n_mol) continue;
+    if (xm < 0 || xm >= a.S.n_mol) continue;  // an id outside the set has no atoms to write
     const MolRef M = mol_ref(a.S, xm);
     const uint64_t stream = a.stream_base + item;
     stage_direction(T, a.S, M, nullptr, nullptr, M, nullptr, lane);
@@ -1306,9 +1333,16 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_fit_kernel(const FitArgs 
         if (h0) y0 = fmaf(gauss_overlap(c0, l0, cj, lj), pj, y0);
         if (h1) y1 = fmaf(gauss_overlap(c1, l1, cj, lj), pj, y1);
       }
+      // warp_sum leaves the same bits in every lane, so these exits are
+      // warp-uniform
       const float pap = warp_sum(p0 * y0 + p1 * y1);
       const float al = rs / pap;
-      x0 = fmaf(al, p0, x0); x1 = fmaf(al, p1, x1);
+      // a non-positive curvature or a non-finite step (possible with ridge 0
+      // and nearly coincident atoms) ends the iteration at the last finite x
+      if (!(pap > 0.f) || !isfinite(al)) break;
+      const float nx0 = fmaf(al, p0, x0), nx1 = fmaf(al, p1, x1);
+      if (!__all_sync(0xffffffffu, isfinite(nx0) && isfinite(nx1))) break;
+      x0 = nx0; x1 = nx1;
       r0 = fmaf(-al, y0, r0); r1 = fmaf(-al, y1, r1);
       const float rs_new = warp_sum(r0 * r0 + r1 * r1);
       const float be = rs_new / rs;
@@ -1364,20 +1398,23 @@ extern "C" int cv_fit_weights(shp_set S, const int32_t* idx, int64_t n, const sh
   return launch_persistent(cv_fit_kernel, a, n, kCVWarps, sizeof(WarpTables) * kCVWarps, (cudaStream_t)stream);
 }
 
-extern "C" int union_volume_cv(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, const float* omega,
-                               float target_rel_se, uint32_t round, double* vol, double* vol_se, uint32_t* n_used,
-                               void* stream) {
-  clear_error();
-  if (!S || !mc) { set_error("union_volume_cv: NULL argument"); return SHP_EINVAL; }
-  if (mc->n_samples < 2 || mc->flags) { set_error("union_volume_cv: n_samples >= 2 and no flags"); return SHP_EINVAL; }
-  if (n < 0) { set_error("union_volume_cv: negative n"); return SHP_EINVAL; }
+namespace shp {
+namespace {
+
+int self_estimate(const char* who, shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, const float* omega,
+                  float target_rel_se, uint32_t round, int watch, double* vol, double* vol_se, double* self_ov,
+                  double* self_se, uint32_t* n_used, cudaStream_t stream) {
+  if (!S || !mc) { set_error("%s: NULL argument", who); return SHP_EINVAL; }
+  if (mc->n_samples < 2 || mc->flags) { set_error("%s: n_samples >= 2 and no flags", who); return SHP_EINVAL; }
+  if (n < 0) { set_error("%s: negative n", who); return SHP_EINVAL; }
+  if (watch != 0 && watch != 1) { set_error("%s: watch must be 0 (volume) or 1 (self-overlap)", who); return SHP_EINVAL; }
   if (n == 0) return SHP_OK;
-  if (!vol) { set_error("union_volume_cv: NULL vol"); return SHP_EINVAL; }
-  if (!idx && n > S->n_mol) { set_error("union_volume_cv: n exceeds the set size"); return SHP_ERANGE; }
+  if (!vol && !self_ov) { set_error("%s: NULL outputs", who); return SHP_EINVAL; }
+  if (!idx && n > S->n_mol) { set_error("%s: n exceeds the set size", who); return SHP_ERANGE; }
   CVArgs a{};
   if (target_rel_se > 0.f) {
     if (round == 0 || round % 256u || mc->n_samples % round) {
-      set_error("union_volume_cv: round must be a multiple of 256 dividing n_samples (the cap)");
+      set_error("%s: round must be a multiple of 256 dividing n_samples (the cap)", who);
       return SHP_EINVAL;
     }
     a.round_b = round / 256u;
@@ -1390,10 +1427,33 @@ extern "C" int union_volume_cv(shp_set S, const int32_t* idx, int64_t n, const s
   a.stream_base = mc->stream_base;
   a.n = mc->n_samples;
   a.target = target_rel_se;
+  a.watch = watch;
   a.vol = vol;
   a.vol_se = vol_se;
+  a.self_ov = self_ov;
+  a.self_se = self_se;
   a.n_used = n_used;
   const size_t smem = sizeof(WarpTables) * kCVWarps;
-  return omega ? launch_persistent(cv_volume_kernel<true>, a, n, kCVWarps, smem, (cudaStream_t)stream)
-               : launch_persistent(cv_volume_kernel<false>, a, n, kCVWarps, smem, (cudaStream_t)stream);
+  return omega ? launch_persistent(cv_volume_kernel<true>, a, n, kCVWarps, smem, stream)
+               : launch_persistent(cv_volume_kernel<false>, a, n, kCVWarps, smem, stream);
+}
+
+}  // namespace
+}  // namespace shp
+
+extern "C" int union_volume_cv(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, const float* omega,
+                               float target_rel_se, uint32_t round, double* vol, double* vol_se, uint32_t* n_used,
+                               void* stream) {
+  clear_error();
+  if (n > 0 && !vol) { set_error("union_volume_cv: NULL vol"); return SHP_EINVAL; }
+  return self_estimate("union_volume_cv", S, idx, n, mc, omega, target_rel_se, round, 0, vol, vol_se, nullptr,
+                       nullptr, n_used, (cudaStream_t)stream);
+}
+
+extern "C" int union_self_estimate(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, const float* omega,
+                                   float target_rel_se, uint32_t round, uint32_t watch, double* vol, double* vol_se,
+                                   double* self_ov, double* self_se, uint32_t* n_used, void* stream) {
+  clear_error();
+  return self_estimate("union_self_estimate", S, idx, n, mc, omega, target_rel_se, round, (int)watch, vol, vol_se,
+                       self_ov, self_se, n_used, (cudaStream_t)stream);
 }

@@ -1,6 +1,6 @@
 """Host-side logic of the benchmark: the multi-rank aggregation (world size
-2 over gloo on CPU), per-rank database shards, and the reference arm's JSON
-line (the FP64 oracle on the host cores)."""
+2 over gloo on CPU), the per-rank shards of one global database, and the
+reference arm's JSON line (the FP64 oracle on the host cores)."""
 import json
 import os
 import subprocess
@@ -44,15 +44,21 @@ def test_single_process_aggregate_is_identity():
     assert bench.aggregate(2.5, [7, 8]) == (2.5, [7.0, 8.0])
 
 
-def test_rank_shards_differ_and_repeat():
+def test_rank_shards_partition_one_global_database():
+    """Under N ranks each rank generates only its balanced contiguous range of
+    one global database; the ranges put together are the one-rank database."""
     sys.path.insert(0, ROOT)
     import bench
-    q0, d0 = bench.workload(200, 0)
-    q1, d1 = bench.workload(200, 1)
-    q0b, d0b = bench.workload(200, 0)
-    np.testing.assert_array_equal(d0.xyz, d0b.xyz)
-    assert d0.n_mol == d1.n_mol == 200
-    assert not np.array_equal(d0.counts, d1.counts) or not np.allclose(d0.xyz[:10], d1.xyz[:10])
+    q, whole, s0, n_glob = bench.workload(400, 0, 1)
+    assert s0 == 0 and n_glob == 400 and whole.n_mol == 400
+    parts = [bench.workload(200, r, 2) for r in range(2)]
+    assert parts[0][2] == 0 and parts[1][2] == parts[0][1].n_mol and parts[1][3] == 400
+    np.testing.assert_array_equal(parts[0][0].xyz, q.xyz)
+    xyz = np.concatenate([p[1].xyz for p in parts])
+    np.testing.assert_array_equal(xyz, whole.xyz)
+    cnt = np.concatenate([p[1].counts for p in parts])
+    np.testing.assert_array_equal(cnt, whole.counts)
+    assert abs(parts[0][1].n_mol - parts[1][1].n_mol) < 20  # balanced by work
 
 
 def test_reference_arm_json_line():

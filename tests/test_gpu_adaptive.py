@@ -43,7 +43,7 @@ def small_screen():
 
 
 def check_adaptive_against_oracle(q, d, res, sq, sd, seed, tau, rnd, min_n, cap, pairs, n_db, stream_base=0,
-                                  omega_q=None, omega_d=None):
+                                  omega_q=None, omega_d=None, sq_se=None, sd_se=None):
     nu = res["n_used"].cpu().numpy().astype(np.int64)[pairs]
     iq, idd = pairs // n_db, pairs % n_db
     assert np.all(nu % rnd == 0) and np.all(nu >= min_n) and np.all(nu <= cap)
@@ -54,7 +54,7 @@ def check_adaptive_against_oracle(q, d, res, sq, sd, seed, tau, rnd, min_n, cap,
     for n in np.unique(nu):
         sel = nu == n
         ref = O.tanimoto_pairs(q, iq[sel], d, idd[sel], (stream_base + pairs[sel]).astype(np.uint64), sq, sd,
-                               seed=seed, n=int(n), omega_q=omega_q, omega_d=omega_d)
+                               seed=seed, n=int(n), omega_q=omega_q, omega_d=omega_d, selfQ_se=sq_se, selfD_se=sd_se)
         assert_close(O_[sel], ref["O"], what=f"O at n={n}")
         assert_close(seO[sel], ref["seO"], what=f"seO at n={n}")
         assert_close(T[sel], ref["T"], what=f"T at n={n}")
@@ -64,7 +64,8 @@ def check_adaptive_against_oracle(q, d, res, sq, sd, seed, tau, rnd, min_n, cap,
             assert np.all(ref["seT"][:, 1] <= tau * (1 + 1e-4)), "stopped before SE(T) <= tau"
         if n > min_n:
             prev = O.tanimoto_pairs(q, iq[sel], d, idd[sel], (stream_base + pairs[sel]).astype(np.uint64), sq, sd,
-                                    seed=seed, n=int(n - rnd), omega_q=omega_q, omega_d=omega_d)
+                                    seed=seed, n=int(n - rnd), omega_q=omega_q, omega_d=omega_d, selfQ_se=sq_se,
+                                    selfD_se=sd_se)
             assert np.all(prev["seT"][:, 1] > tau * (1 - 1e-4)), "did not stop when SE(T) <= tau"
     return nu
 

@@ -280,23 +280,32 @@ def test_allocation_failure_is_reported_and_recoverable():
     np.testing.assert_array_equal(S2.tables()[1], S.tables()[1])
 
 
-def test_chunked_screen_reproduces_the_full_screen():
-    """Pairs are keyed by their global index, so a database screened in two
-    chunks (stream bases offset by the first chunk's size) reproduces the
-    one-launch screen bit for bit -- fixed budget and adaptive: a screen can
-    be sharded over devices or resumed from its last finished chunk."""
-    q = synth.principal_axes(synth.generate(71, [28]))
+def test_sharded_screen_reproduces_the_full_screen():
+    """Pairs are keyed by their global index (stream = base + q * stride + d),
+    so a database screened as contiguous shards -- stream_base = the shard's
+    first molecule, stream_stride = the global size, self-overlap streams
+    offset the same way -- reproduces the one-launch screen bit for bit, for
+    several queries, fixed budget and adaptive: a screen can be sharded over
+    devices or resumed from its last finished shard."""
+    from paper_2607_20766_b300 import shard
+    q = synth.principal_axes(synth.generate(71, [28, 40]))
     d = synth.principal_axes(synth.generate(72, synth.counts_uniform(72, 600, 18, 60)))
     Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
-    sq = shp.self_overlaps(Sq, seed=1, n_samples=2048)
-    sd = shp.self_overlaps(Sd, seed=2, n_samples=2048)
-    halves = [np.arange(0, 250), np.arange(250, 600)]
+    sq, sq_se, _ = shp.self_overlaps(Sq, seed=1, n_samples=2048, with_se=True)
+    sd, sd_se, _ = shp.self_overlaps(Sd, seed=2, n_samples=2048, with_se=True)
+    parts = shard.partition(d.counts, q.counts, 3)
+    assert all(e > s for s, e in parts)
     for kw in (dict(n_fixed=1024), dict(tau=0.01, min_n=512, cap=8192)):
-        full = shp.tanimoto_screen(Sq, Sd, sq, sd, seed=3, with_overlaps=True, **kw)
-        parts = []
-        for h in halves:
-            Sh = shp.shape_set_load(d.subset(h))
-            sh = shp.self_overlaps(Sh, seed=2, n_samples=2048, stream_base=int(h[0]))
-            parts.append(shp.tanimoto_screen(Sq, Sh, sq, sh, seed=3, stream_base=int(h[0]), with_overlaps=True, **kw))
-        for k in ("T", "seT", "O", "n_used"):
-            np.testing.assert_array_equal(np.concatenate([p[k].cpu().numpy() for p in parts]), full[k].cpu().numpy())
+        full = shp.tanimoto_screen(Sq, Sd, sq, sd, seed=3, with_overlaps=True, self_se_q=sq_se, self_se_db=sd_se,
+                                   **kw)
+        got = {k: [] for k in ("T", "seT", "O", "n_used")}
+        for s, e in parts:
+            Sh = shp.shape_set_load(d.subset(np.arange(s, e)))
+            sh, sh_se, _ = shp.self_overlaps(Sh, seed=2, n_samples=2048, stream_base=s, with_se=True)
+            r = shp.tanimoto_screen(Sq, Sh, sq, sh, seed=3, stream_base=s, stream_stride=d.n_mol, with_overlaps=True,
+                                    self_se_q=sq_se, self_se_db=sh_se, **kw)
+            for k in got:
+                a = r[k].cpu().numpy()
+                got[k].append(a.reshape(q.n_mol, e - s, *a.shape[1:]))
+        for k, v in got.items():
+            np.testing.assert_array_equal(np.concatenate(v, axis=1).reshape(full[k].shape), full[k].cpu().numpy())

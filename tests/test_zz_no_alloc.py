@@ -1,8 +1,8 @@
 """The allocation-free loss/gradient entry point (for callers that cannot
 allocate device memory while they run, e.g. inside a host framework that
 owns the allocator) gives the same loss and gradient as the regular one, on
-two calls in a row through the C ABI, and refuses batches beyond its fixed
-scratch. Collected last on purpose: it must pass alone in a fresh process
+two calls in a row through the C ABI, while the library's allocation hook
+would fail any allocation, and refuses batches beyond its fixed scratch. Collected last on purpose: it must pass alone in a fresh process
 and after every other test."""
 import ctypes
 
@@ -36,7 +36,14 @@ def test_noalloc_matches_regular_entry_point():
         g_new = torch.full((B.MLP_PARAMS,), float("nan"), dtype=torch.float32, device=dev)
         l_new = torch.full((1,), float("nan"), dtype=torch.float64, device=dev)
         assert _call(lib.mlp_loss_grad, p, x, t, rows, n_rows, g_ref, l_ref) == 0
-        assert _call(lib.mlp_loss_grad_noalloc, p, x, t, rows, n_rows, g_new, l_new) == 0, lib.shp_last_error()
+        # arm the library's allocation hook: any allocation on this path would
+        # now fail with SHP_ENOMEM, so success shows that the call allocates nothing
+        assert lib.shp_fail_next_allocations(1000) == 0
+        try:
+            rc = _call(lib.mlp_loss_grad_noalloc, p, x, t, rows, n_rows, g_new, l_new)
+        finally:
+            assert lib.shp_fail_next_allocations(0) == 0
+        assert rc == 0, lib.shp_last_error()
         torch.cuda.synchronize()
         # same kernels, same fixed-order reduction: the results agree to the
         # tolerance the other network tests use (they are in fact identical)
