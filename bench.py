@@ -434,6 +434,7 @@ def main():
         with open(peaks_path) as f:
             sm_max = float(json.load(f).get("sm_max_mhz", sm_max))
     peak = sms * 128 * sm_max * 1e6 / FP32_OPS_PER_EVAL / 1e9
+    ceiling = loop_ceiling(shp, torch, Sq, Sd, d, tuned, peak, achieved)
 
     # the whole database's per-query top-k union Tanimotos, merged on rank 0
     # from every shard (once, after the timed region)
@@ -493,7 +494,8 @@ def main():
                          "traffic_basis": "ncu dram bytes of a 20,000-pair capture scaled by pairs",
                          "kernel": "cross_kernel<screen>",
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz / {FP32_OPS_PER_EVAL} "
-                                       f"FP32 ops per sample-atom evaluation"},
+                                       f"FP32 ops per sample-atom evaluation",
+                         "loop_ceiling": ceiling},
             "clocks": clk.summary(),
             "tuned_variant": int(tuned), "variant_ms": [round(float(x), 3) for x in tune_ms],
             "gpu_launches": 5 * args.steps,
@@ -514,6 +516,32 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def loop_ceiling(shp, torch, Sq, Sd, d, variant: int, peak: float, achieved: float, batches: int = 256):
+    """What the screen's per-sample work reaches on this chip without the
+    per-pair work around it: the tuned variant's evaluation loop and
+    accumulation on one typical pair (the query and a database molecule of
+    the mean atom count), on every resident warp, without (eval) and with
+    (sample path) the Philox/alias/Box-Muller draw of the samples."""
+    stream = torch.cuda.current_stream()
+    mean = int(round(float(d.counts.mean())))
+    idd = int(np.flatnonzero(d.counts == mean)[0]) if np.any(d.counts == mean) else 0
+    out = {"pair_atoms": [int(Sq.counts[0]), int(d.counts[idd])], "batches_per_warp_per_direction": batches}
+    for name, draw in (("eval_only", False), ("sample_path", True)):
+        shp.eval_probe(Sq, 0, Sd, idd, variant, draw, batches)  # warm-up
+        ms = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ev = shp.eval_probe(Sq, 0, Sd, idd, variant, draw, batches)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        rate = ev / (statistics.median(ms) / 1e3) / 1e9
+        out[name] = {"achieved": rate, "frac": rate / peak, "kernel_frac_of_it": achieved / rate}
+    return out
 
 
 def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: int = 65536, net=None,

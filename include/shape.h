@@ -248,6 +248,24 @@ int tanimoto_screen(shp_set Q, shp_set D, const shp_screen* cfg, const double* s
                     const double* self_db, float* T, float* seT, double* O_out, double* seO_out,
                     uint32_t* n_used, void* stream);
 
+/*
+ * Roofline calibration (a measurement aid; the paper has none): runs the
+ * per-sample work of screen launch variant `variant` (-1 = the tuned
+ * default) on the pair (Q[iq], D[id]) -- every atom of both molecules
+ * evaluated at each sample and the per-lane accumulation, both directions --
+ * on as many warps as the variant keeps resident, `batches` batches of 64 SP
+ * samples per direction per warp, with no pair queue and no per-pair
+ * epilogue. draw = 1: the samples are drawn as in the screen (Philox words,
+ * alias pick, Box-Muller normals); draw = 0: they are placed at the staged
+ * component centres moved by a per-batch offset, i.e. the same position
+ * arithmetic without the random draw. *evals_host receives the sample x atom
+ * evaluations one call performs; time it with events on `stream`.
+ *   sink [1] double device: a checksum is added to it (keeps the work live).
+ * Errors: SHP_EINVAL, SHP_ERANGE (indices, variant), SHP_ECUDA.
+ */
+int shp_eval_probe(shp_set Q, int32_t iq, shp_set D, int32_t id, int32_t variant, int32_t draw,
+                   uint32_t batches, double* sink, int64_t* evals_host, void* stream);
+
 /* Number of compiled launch variants of the screen kernel. */
 int shp_screen_variants(void);
 

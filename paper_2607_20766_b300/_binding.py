@@ -27,7 +27,7 @@ EXPORTS = ("shp_last_error", "shp_version", "shp_fail_next_allocations", "shape_
            "tanimoto_screen", "shp_screen_variants", "shp_screen_variant_info", "tanimoto_screen_tune", "align_crn_points",
            "overlap_pose_grad", "align_rigid", "shape_set_frames", "union_attributions", "union_volume_cv",
            "cv_features", "mlp_forward", "mlp_loss_grad", "mlp_adam", "mlp_loss_grad_noalloc", "cv_fit_weights",
-           "union_self_estimate")
+           "union_self_estimate", "shp_eval_probe")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 33, 64, 6401
 OBJ_FO, OBJ_UNION, OBJ_FO_CLOSED = 0, 1, 2
 
@@ -90,6 +90,8 @@ def load_library():
         "union_attributions": [_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, _P],
         "union_volume_cv": [_P, _P, ctypes.c_int64, _P, _P, ctypes.c_float, ctypes.c_uint32, _P, _P, _P, _P],
         "cv_features": [_P, _P, _P],
+        "shp_eval_probe": [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, _P,
+                           _P, _P],
         "union_self_estimate": [_P, _P, ctypes.c_int64, _P, _P, ctypes.c_float, ctypes.c_uint32, ctypes.c_uint32, _P,
                                 _P, _P, _P, _P, _P],
         "cv_fit_weights": [_P, _P, ctypes.c_int64, _P, ctypes.c_float, _P, _P],
@@ -313,6 +315,18 @@ def fail_next_allocations(count: int) -> None:
     """Test hook: the next `count` device allocations of library calls fail
     as out of memory (0 clears)."""
     _check(load_library().shp_fail_next_allocations(count))
+
+
+def eval_probe(Q: ShapeSet, iq: int, D: ShapeSet, id_: int, variant: int = -1, draw: bool = False,
+               batches: int = 256, stream=None) -> int:
+    """Roofline calibration: the screen variant's per-sample work on the pair
+    (Q[iq], D[id_]) with or without the random draw (see shp_eval_probe);
+    returns the sample x atom evaluations of the call (time it with events)."""
+    sink = torch.zeros(1, dtype=torch.float64, device=Q.device)
+    ev = ctypes.c_int64()
+    _check(load_library().shp_eval_probe(Q.handle, iq, D.handle, id_, variant, int(draw), batches, _dptr(sink),
+                                         ctypes.byref(ev), _stream(stream)))
+    return ev.value
 
 
 def screen_variants() -> int:

@@ -702,6 +702,86 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) self_kernel(const Sel
   }
 }
 
+// ------------------------------------------------------------ roofline calibration
+
+struct ProbeArgs {
+  SetView A, B;
+  int32_t xa, xb;
+  uint32_t batches;  // per direction per warp
+  int draw;
+  Key key;
+  double* sink;
+};
+
+// Synthetic sample pairs for the calibration without draws: slot p of a lane
+// sits at staged component centres k0[p], k1[p] (advanced through the table
+// by one per batch) moved by sigma times a warp-uniform offset of the batch:
+// the position arithmetic of a drawn sample, without its Philox words, alias
+// picks and normals.
+template <int SP>
+__device__ __forceinline__ void synth_batch(const float4* __restrict__ samp, int nx, uint32_t b, int (&k0)[SP],
+                                            int (&k1)[SP], float2 (&rx)[SP], float2 (&ry)[SP], float2 (&rz)[SP],
+                                            float2 (&rr)[SP]) {
+  const float ox = 0.31f * (float)(b % 13u) - 1.9f, oy = 0.23f * (float)(b % 17u) - 1.8f;
+  const float oz = 0.17f * (float)(b % 19u) - 1.5f;
+#pragma unroll
+  for (int p = 0; p < SP; ++p) {
+    k0[p] = k0[p] + 1 < nx ? k0[p] + 1 : 0;
+    k1[p] = k1[p] + 1 < nx ? k1[p] + 1 : 0;
+    const float4 c0 = samp[k0[p]], c1 = samp[k1[p]];
+    const float ax = fmaf(c0.w, ox, c0.x), ay = fmaf(c0.w, oy, c0.y), az = fmaf(c0.w, oz, c0.z);
+    const float bx = fmaf(c1.w, oy, c1.x), by = fmaf(c1.w, oz, c1.y), bz = fmaf(c1.w, ox, c1.z);
+    rx[p] = make_float2(ax, bx);
+    ry[p] = make_float2(ay, by);
+    rz[p] = make_float2(az, bz);
+    rr[p] = make_float2(fmaf(ax, ax, fmaf(ay, ay, az * az)), fmaf(bx, bx, fmaf(by, by, bz * bz)));
+  }
+}
+
+// The screen variant's per-sample work on one pair, both directions, a fixed
+// number of batches per warp: no queue, no per-pair staging beyond the
+// first, no epilogue.
+template <int SP, int kForm, int kWarps, int kMinBlocks>
+__global__ void __launch_bounds__(kWarps * 32, kMinBlocks) probe_kernel(const ProbeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpTables& T = reinterpret_cast<WarpTables*>(smem_raw)[warp];
+  const MolRef MA = mol_ref(a.A, a.xa), MB = mol_ref(a.B, a.xb);
+  const uint32_t gw = blockIdx.x * kWarps + warp;  // stream of this warp
+  DirState& st = T.st[0][lane];
+  double check = 0.0;
+#pragma unroll 1
+  for (int dir = 0; dir < 2; ++dir) {
+    const SetView& SX = dir ? a.B : a.A;
+    const SetView& SY = dir ? a.A : a.B;
+    const MolRef MX = dir ? MB : MA, MY = dir ? MA : MB;
+    stage_direction(T, SX, MX, nullptr, &SY, MY, nullptr, lane);
+    dir_init(st);
+    const uint32_t n = a.batches * 64u * SP;
+    if (a.draw) {
+      for (uint32_t b = 0; b < a.batches; ++b)
+        run_batch<false, SP, kForm>(T, MX.n, MY.n, b, n, a.key, gw, 0u, (uint32_t)dir, false, lane, st);
+    } else {
+      int k0[SP], k1[SP];
+#pragma unroll
+      for (int p = 0; p < SP; ++p) {
+        k0[p] = (lane + 32 * p) % MX.n;
+        k1[p] = (lane + 32 * p + 7) % MX.n;
+      }
+      for (uint32_t b = 0; b < a.batches; ++b) {
+        float2 rx[SP], ry[SP], rz[SP], rr[SP];
+        synth_batch<SP>(T.samp, MX.n, b, k0, k1, rx, ry, rz, rr);
+        eval_batch<false, SP, kForm>(T.x, T.y, MX.n, MY.n, b, n, false, lane, st, rx, ry, rz, rr);
+      }
+    }
+    double sums[4];
+    dir_totals(st, sums);
+    check += sums[0] + sums[2];
+    __syncwarp();
+  }
+  if (lane == 0) atomicAdd(a.sink, check);
+}
+
 // ------------------------------------------------------------ variants
 
 // sample pairs per lane, exponent form, warps per CTA, CTAs per SM (the
@@ -788,6 +868,32 @@ int launch_cross(int v, const CrossArgs& a, int64_t n_items, cudaStream_t st) {
     return v == V ? launch_cross_v<MODE, V, kCV>(a, n_items, st) : launch_cross<MODE, kCV, V + 1>(v, a, n_items, st);
   } else {
     return launch_cross_v<MODE, V, kCV>(a, n_items, st);
+  }
+}
+
+template <int V>
+int launch_probe_v(const ProbeArgs& a, cudaStream_t st, int64_t* warps) {
+  using Tr = VariantTraits<V>;
+  auto k = probe_kernel<Tr::sp, Tr::form, Tr::warps, Tr::min_blocks>;
+  int sms = 0;
+  int rc = sm_count(&sms);
+  if (rc) return rc;
+  SHP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tr::smem));
+  int per_sm = 0;
+  SHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Tr::warps * 32, Tr::smem));
+  if (per_sm < 1) per_sm = 1;
+  *warps = (int64_t)sms * per_sm * Tr::warps;
+  k<<<sms * per_sm, Tr::warps * 32, Tr::smem, st>>>(a);
+  SHP_CUDA(cudaGetLastError());
+  return SHP_OK;
+}
+
+template <int V = 0>
+int launch_probe(int v, const ProbeArgs& a, cudaStream_t st, int64_t* warps) {
+  if constexpr (V + 1 < kNumVariants) {
+    return v == V ? launch_probe_v<V>(a, st, warps) : launch_probe<V + 1>(v, a, st, warps);
+  } else {
+    return launch_probe_v<V>(a, st, warps);
   }
 }
 
@@ -1456,4 +1562,29 @@ extern "C" int union_self_estimate(shp_set S, const int32_t* idx, int64_t n, con
   clear_error();
   return self_estimate("union_self_estimate", S, idx, n, mc, omega, target_rel_se, round, (int)watch, vol, vol_se,
                        self_ov, self_se, n_used, (cudaStream_t)stream);
+}
+
+extern "C" int shp_eval_probe(shp_set Q, int32_t iq, shp_set D, int32_t id, int32_t variant, int32_t draw,
+                              uint32_t batches, double* sink, int64_t* evals, void* stream) {
+  clear_error();
+  if (!Q || !D || !sink || !evals) { set_error("shp_eval_probe: NULL argument"); return SHP_EINVAL; }
+  if (iq < 0 || iq >= Q->n_mol || id < 0 || id >= D->n_mol) { set_error("shp_eval_probe: molecule index out of range"); return SHP_ERANGE; }
+  if (variant < 0) variant = default_variant(kScreen);
+  if (variant >= kNumVariants) { set_error("shp_eval_probe: no variant %d", variant); return SHP_ERANGE; }
+  if (batches == 0 || batches > (1u << 20)) { set_error("shp_eval_probe: batches must be in 1 .. 2^20"); return SHP_EINVAL; }
+  ProbeArgs a{};
+  a.A = view(Q);
+  a.B = view(D);
+  a.xa = iq;
+  a.xb = id;
+  a.batches = batches;
+  a.draw = draw != 0;
+  a.key = Key{0x5A17u, 0x0C0FFEEu};
+  a.sink = sink;
+  int64_t warps = 0;
+  const int rc = launch_probe(variant, a, (cudaStream_t)stream, &warps);
+  if (rc) return rc;
+  const int64_t na = Q->h_off_count(iq), nb = D->h_off_count(id);
+  *evals = warps * 2 * (int64_t)batches * 64 * kVariants[variant].sp * (na + nb);
+  return SHP_OK;
 }

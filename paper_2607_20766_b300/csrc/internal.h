@@ -31,8 +31,11 @@ struct shp_set_s {
   bool frames_ready = false;
   cudaEvent_t frames_done = nullptr;
   std::mutex frames_mu;
-  // host mirror of Z (alignment scales its estimates on the host)
+  // host mirrors of Z (alignment scales its estimates on the host) and of
+  // the atom counts
   std::vector<double> h_Z;
+  std::vector<uint8_t> h_count;
+  int32_t h_off_count(int32_t m) const { return h_count[m]; }
 };
 
 namespace shp {

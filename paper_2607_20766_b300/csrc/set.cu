@@ -317,6 +317,8 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
   s->n_atoms = n_atoms;
   s->max_atoms = max_atoms;
   s->h_Z.assign(n_mol, 0.0);
+  s->h_count.resize(n_mol);
+  for (int32_t m = 0; m < n_mol; ++m) s->h_count[m] = (uint8_t)(offsets[m + 1] - offsets[m]);
   const SetLayout L = set_layout(n_atoms, n_mol);
   std::lock_guard<std::mutex> stage_lock(g_stage_mu);
   StageBuf* sb = nullptr;

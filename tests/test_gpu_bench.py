@@ -13,6 +13,27 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 pytestmark = pytest.mark.gpu
 
 
+def a_ok(a):
+    return a["pairs_per_s"] > 0 and "speedup_vs_p99_fixed" in a["with_fitted_control_variate"]
+
+
+def test_eval_probe_calibration():
+    import torch
+    import paper_2607_20766_b300 as shp
+    from paper_2607_20766_b300 import synth
+    q = synth.principal_axes(synth.generate(3, [32]))
+    d = synth.principal_axes(synth.generate(4, [39, 20]))
+    Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
+    for draw in (False, True):
+        ev = shp.eval_probe(Sq, 0, Sd, 0, -1, draw, 8)
+        torch.cuda.synchronize()
+        assert ev > 0 and ev % (2 * 8 * 71) == 0
+    with pytest.raises(shp.ShapeError):
+        shp.eval_probe(Sq, 0, Sd, 5, -1, False, 8)
+    with pytest.raises(shp.ShapeError):
+        shp.eval_probe(Sq, 0, Sd, 0, 99, False, 8)
+
+
 def test_bench_json_line_small():
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--n-db", "3000", "--steps", "3", "--warmup", "3",
            "--adaptive-db", "3000", "--cv-train", "3000", "--cv-held", "500", "--align-db", "200",
@@ -30,7 +51,14 @@ def test_bench_json_line_small():
     assert line["e2e"]["h2d_bytes_per_step"] > 0 and line["e2e"]["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["gpu_launches"] == 5 * line["steps"]
+    c = r["loop_ceiling"]
+    # the calibration loops do the screen's per-sample work without its per-pair work: at least as fast
+    assert 0 < c["sample_path"]["frac"] <= c["eval_only"]["frac"] < 1.2
+    assert c["sample_path"]["kernel_frac_of_it"] < 1.05
+    assert a_ok(line["adaptive"])
     a = line["adaptive"]
     assert a["frac_se_met"] + a["frac_at_cap"] >= 0.999
+    assert a["fixed_budget_p99"]["samples_per_direction"] <= a["fixed_budget"]["samples_per_direction"]
+    assert a["self_overlaps"]["seconds"] > 0
     assert a["with_control_variate"]["pairs_per_s"] > 0 and a["with_fitted_control_variate"]["pairs_per_s"] > 0
     assert line["alignment"]["frac_improved"] > 0.5
