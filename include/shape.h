@@ -348,17 +348,20 @@ typedef struct {
  * ascent steps on the CRN objective (step sizes decayed by
  * (1 + cos(pi step / steps)) / 2), then each final pose is scored by the
  * symmetrised union Tanimoto (overlap_estimate with n_score samples and the
- * union self-overlaps self_q[iq][1], self_db[ib[k]][1]) and the best start
- * is kept.
+ * union self-overlaps self_q[iq][1], self_db[ib[k]][1]; every start of pair
+ * k on the same random numbers, stream cfg->stream + k, seed cfg->seed ^
+ * 0x5DEECE66D, so that starts are compared on common random numbers) and
+ * the best start is kept.
  *   self_q [n_q][2], self_db [n_db][2] double device (slot 1 = union)
  *   pose_out [n_pairs][7], T_out [n_pairs], T_starts [n_pairs][starts]
- *   (may be NULL) float device.
+ *   (may be NULL), pose_starts [n_pairs][starts][7] (the final raw pose of
+ *   every start, may be NULL) float device.
  * Scratch (CRN points, per-start poses, scores) is stream-ordered library
  * memory.
  */
 int align_rigid(shp_set Q, int32_t iq, shp_set B, const int32_t* ib, int64_t n_pairs,
                 const shp_align* cfg, const double* self_q, const double* self_db, float* pose_out,
-                float* T_out, float* T_starts, void* stream);
+                float* T_out, float* T_starts, float* pose_starts, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Learned control variate for union volumes                               */

@@ -85,7 +85,7 @@ def load_library():
         "align_crn_points": [_P, ctypes.c_int32, _P, _P, _P],
         "overlap_pose_grad": [_P, ctypes.c_int32, _P, ctypes.c_uint32, _P, _P, ctypes.c_int64, _P, ctypes.c_uint32,
                               _P, _P, _P],
-        "align_rigid": [_P, ctypes.c_int32, _P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P],
+        "align_rigid": [_P, ctypes.c_int32, _P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P],
         "shape_set_frames": [_P, _P],
         "union_attributions": [_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, _P],
         "union_volume_cv": [_P, _P, ctypes.c_int64, _P, _P, ctypes.c_float, ctypes.c_uint32, _P, _P, _P, _P],
@@ -453,7 +453,8 @@ def align_rigid(Q: ShapeSet, iq: int, B: ShapeSet, ib, self_q: torch.Tensor, sel
                 lr_t: float = 0.05, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, n_score: int = 4096,
                 stream_base: int = 0, with_starts: bool = False, stream=None):
     """Multi-start Adam alignment of B[ib[k]] onto Q[iq]. Returns dict pose
-    ([n, 7]), T ([n]) and, with with_starts, T_starts ([n, starts])."""
+    ([n, 7]), T ([n]) and, with with_starts, T_starts ([n, starts]) and
+    pose_starts ([n, starts, 7], every start's final raw pose)."""
     dev = Q.device
     ib = _device_i32(ib, dev)
     n = ib.numel()
@@ -462,11 +463,12 @@ def align_rigid(Q: ShapeSet, iq: int, B: ShapeSet, ib, self_q: torch.Tensor, sel
                T=torch.empty(n, dtype=torch.float32, device=dev))
     if with_starts:
         out["T_starts"] = torch.empty((n, starts), dtype=torch.float32, device=dev)
+        out["pose_starts"] = torch.empty((n, starts, 7), dtype=torch.float32, device=dev)
     self_q = self_q.to(device=dev, dtype=torch.float64).contiguous()
     self_db = self_db.to(device=dev, dtype=torch.float64).contiguous()
     _check(load_library().align_rigid(Q.handle, iq, B.handle, _dptr(ib), n, ctypes.byref(cfg), _dptr(self_q),
                                       _dptr(self_db), _dptr(out["pose"]), _dptr(out["T"]), _dptr(out.get("T_starts")),
-                                      _stream(stream)))
+                                      _dptr(out.get("pose_starts")), _stream(stream)))
     return out
 
 

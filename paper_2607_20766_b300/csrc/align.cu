@@ -499,7 +499,7 @@ extern "C" int overlap_pose_grad(shp_set Q, int32_t iq, const float* points, uin
 
 extern "C" int align_rigid(shp_set Q, int32_t iq, shp_set B, const int32_t* ib, int64_t n_pairs,
                            const shp_align* cfg, const double* self_q, const double* self_db, float* pose_out,
-                           float* T_out, float* T_starts, void* stream) {
+                           float* T_out, float* T_starts, float* pose_starts, void* stream) {
   clear_error();
   int rc = check_points_args(Q, iq, "align_rigid");
   if (rc) return rc;
@@ -577,10 +577,15 @@ extern "C" int align_rigid(shp_set Q, int32_t iq, shp_set B, const int32_t* ib, 
   if (need < grid) grid = need;
   align_adam_kernel<<<(unsigned)grid, kAlignThreads, kAlignSmem, st>>>(a);
   e = cudaGetLastError();
+  if (e == cudaSuccess && pose_starts)
+    e = cudaMemcpyAsync(pose_starts, poses, sizeof(float) * 7 * n_items, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) { release(); return cuda_fail(e, "align_rigid: optimiser launch"); }
   pair_index_kernel<<<(unsigned)((n_items + 255) / 256), 256, 0, st>>>(n_pairs, (int)cfg->starts, iq, ib, ia2, ib2);
   shp_mc score{cfg->seed ^ 0x5DEECE66Dull, cfg->stream, cfg->n_score, SHP_SYMMETRIC};
-  rc = overlap_estimate(Q, ia2, B, ib2, n_items, poses, &score, est, se, stream);
+  // every start of a pair is scored on the same random numbers (stream base
+  // + pair), so that the choice between starts is not decided by
+  // independent sampling noise
+  rc = overlap_estimate_grouped(Q, ia2, B, ib2, n_items, poses, &score, est, se, cfg->starts, st);
   if (rc) { release(); return rc; }
   select_best_kernel<<<(unsigned)((n_pairs + 255) / 256), 256, 0, st>>>(n_pairs, (int)cfg->starts, est, self_q, iq,
                                                                          self_db, B->n_mol, ib, poses, pose_out,

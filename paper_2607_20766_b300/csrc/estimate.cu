@@ -411,6 +411,7 @@ struct CrossArgs {
   // common
   int64_t n_items;
   int64_t item_stride;
+  int64_t stream_group;  // pair mode: item k uses stream stream_base + k / stream_group
   Key key;
   uint64_t stream_base;
   uint32_t n;
@@ -579,7 +580,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) cross_kernel(const Cr
       }
       continue;
     }
-    const uint64_t sid = args.stream_base + (MODE == kPairs ? (uint64_t)out_idx
+    const uint64_t sid = args.stream_base + (MODE == kPairs ? (uint64_t)(out_idx / args.stream_group)
                                                             : (uint64_t)xa * args.stream_stride + (uint64_t)xb);
     const uint32_t slo = (uint32_t)sid, shi = (uint32_t)(sid >> 32);
     const MolRef MA = mol_ref(args.A, xa), MB = mol_ref(args.B, xb);
@@ -1030,9 +1031,11 @@ int launch_screen(int mode, int v, const CrossArgs& a, int64_t n_items, cudaStre
 
 using namespace shp;
 
-extern "C" int overlap_estimate(shp_set A, const int32_t* ia, shp_set B, const int32_t* ib, int64_t n_pairs,
-                                const float* poseB, const shp_mc* mc, double* est, double* se, void* stream) {
-  clear_error();
+namespace shp {
+
+int overlap_estimate_grouped(shp_set A, const int32_t* ia, shp_set B, const int32_t* ib, int64_t n_pairs,
+                             const float* poseB, const shp_mc* mc, double* est, double* se, int64_t group,
+                             cudaStream_t stream) {
   if (!A || !B) { set_error("overlap_estimate: NULL set"); return SHP_EINVAL; }
   int rc = check_mc(mc, "overlap_estimate");
   if (rc) return rc;
@@ -1049,12 +1052,21 @@ extern "C" int overlap_estimate(shp_set A, const int32_t* ia, shp_set B, const i
   a.se = se;
   a.n_items = n_pairs;
   a.item_stride = 1;
+  a.stream_group = group < 1 ? 1 : group;
   a.key = Key{(uint32_t)mc->seed, (uint32_t)(mc->seed >> 32)};
   a.stream_base = mc->stream_base;
   a.n = mc->n_samples;
   a.anti = (mc->flags & SHP_ANTITHETIC) != 0;
   a.symmetric = (mc->flags & SHP_SYMMETRIC) != 0;
-  return launch_cross<kPairs>(default_variant(kPairs), a, n_pairs, (cudaStream_t)stream);
+  return launch_cross<kPairs>(default_variant(kPairs), a, n_pairs, stream);
+}
+
+}  // namespace shp
+
+extern "C" int overlap_estimate(shp_set A, const int32_t* ia, shp_set B, const int32_t* ib, int64_t n_pairs,
+                                const float* poseB, const shp_mc* mc, double* est, double* se, void* stream) {
+  clear_error();
+  return overlap_estimate_grouped(A, ia, B, ib, n_pairs, poseB, mc, est, se, 1, (cudaStream_t)stream);
 }
 
 extern "C" int union_volume_estimate(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, double* vol,

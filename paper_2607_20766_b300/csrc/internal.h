@@ -66,6 +66,12 @@ inline SetView view(const shp_set_s* s) {
   return SetView{s->atom, s->aux, s->thr, s->alias, s->off, s->Z, s->frame, s->radius, s->n_mol};
 }
 
+// overlap_estimate with item k drawing from stream mc->stream_base + k / group
+// (group consecutive items share their random numbers).
+int overlap_estimate_grouped(shp_set A, const int32_t* ia, shp_set B, const int32_t* ib, int64_t n_pairs,
+                             const float* poseB, const shp_mc* mc, double* est, double* se, int64_t group,
+                             cudaStream_t stream);
+
 int mlp_loss_grad_into(const float* params, const float* x, const float* target, const int32_t* rows, int64_t n,
                        float* part, float* grad, double* loss, cudaStream_t st);
 

@@ -10,6 +10,7 @@ import torch
 from scipy.spatial.transform import Rotation
 
 import oracle as O
+from oracle import align as OA
 import paper_2607_20766_b300 as shp
 from paper_2607_20766_b300 import synth
 from paper_2607_20766_b300.synth import MolSet
@@ -164,6 +165,58 @@ def test_align_starts_and_first_adam_step(mols):
     np.testing.assert_allclose(p1[:, :4], qraw / np.linalg.norm(qraw, axis=1, keepdims=True), atol=2e-6)
 
 
+def _rot(p):
+    return OA.quat_to_rot(np.asarray(p[:4], np.float64))
+
+
+def test_starts_match_the_oracle(mols):
+    """All starts (four principal-axis sign patterns, then random rotations)
+    against the oracle's own frames (numpy eigensolver) and Shoemake
+    rotations (its own Philox)."""
+    q, b, Sq, Sb = mols
+    ib = np.array([2, 3, 4], np.int32)
+    sq, sb = _self(Sq), _self(Sb)
+    r0 = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=4, starts=7, steps=0, n_score=256, with_starts=True)
+    P0 = r0["pose_starts"].cpu().numpy()
+    FQ = OA.principal_frame(q, 0)
+    for k, i in enumerate(ib):
+        FB = OA.principal_frame(b, int(i))
+        for s in range(7):
+            ref = OA.start_pose(FQ, FB, s, seed=4, pair=k)
+            np.testing.assert_allclose(_rot(P0[k, s]), _rot(ref), atol=2e-4, err_msg=f"pair {k} start {s}")
+            np.testing.assert_allclose(P0[k, s, 4:], ref[4:], atol=2e-4, err_msg=f"pair {k} start {s}")
+    # the starts of a pair are scored on common random numbers: stream = pair
+    T = r0["T_starts"].cpu().numpy()
+    S = sq.cpu().numpy()[0, 1] + sb.cpu().numpy()[ib, 1]
+    for s in range(7):
+        est, _ = O.overlap_estimate(q, np.zeros(3, np.int32), b, ib, seed=4 ^ 0x5DEECE66D, n=256, flags=O.SYMMETRIC,
+                                    poses=P0[:, s])
+        np.testing.assert_allclose(T[:, s], est[:, 1] / (S - est[:, 1]), rtol=1e-5, err_msg=f"start {s}")
+
+
+@pytest.mark.parametrize("objective", [shp.OBJ_FO_CLOSED, shp.OBJ_UNION])
+def test_adam_trajectories_match_the_oracle(mols, objective):
+    """k = 1, 3, 10 Adam steps (cosine decay over k) from every start: the
+    GPU's final poses against the oracle's FP64 Adam (central-difference
+    gradients of the FP64 CRN objective on the oracle's own CRN points, or
+    the analytic first-order gradient) started from the same poses."""
+    q, b, Sq, Sb = mols
+    ib = np.array([2, 3], np.int32)
+    sq, sb = _self(Sq), _self(Sb)
+    starts = 6
+    P0 = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=4, starts=starts, steps=0, n_score=256,
+                         with_starts=True)["pose_starts"].cpu().numpy().astype(np.float64)
+    pts = OA.crn(q, 0, seed=4, stream=0, n=1024)
+    for K, tol in ((1, 1e-4), (3, 3e-4), (10, 1e-3)):
+        PK = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=4, starts=starts, steps=K, n_crn=1024, objective=objective,
+                             n_score=256, with_starts=True)["pose_starts"].cpu().numpy()
+        for k, i in enumerate(ib):
+            for s in range(starts):
+                ref = OA.adam(q, 0, b, int(i), P0[k, s], steps=K, objective=objective, points=pts)[-1]
+                np.testing.assert_allclose(_rot(PK[k, s]), _rot(ref), atol=tol, err_msg=f"K={K} pair {k} start {s}")
+                np.testing.assert_allclose(PK[k, s, 4:], ref[4:], atol=tol, err_msg=f"K={K} pair {k} start {s}")
+
+
 def test_recovers_known_superpositions():
     """Rigidly displaced copies (15 A away, random rotation: disjoint, T = 0)
     are superposed back to a Tanimoto of at least 0.99."""
@@ -185,9 +238,9 @@ def test_recovers_known_superpositions():
     # The returned Tanimotos are noisy scores (for a perfect overlap T ~ 1 + 2
     # eps with eps the relative error of O, ~1% at 8192 samples), so the
     # poses are judged directly: RMSD to the exact superposition and a
-    # Tanimoto of 2^16 samples per direction.
-    sq_hi = shp.self_overlaps(Sq, seed=21, n_samples=1 << 16)
-    sb_hi = shp.self_overlaps(Sb, seed=21, n_samples=1 << 16, stream_base=1)
+    # Tanimoto of 2^18 samples per direction, with the self-overlaps of the
+    # copies (equal to the query's) from 2^20 samples: SE(T) ~0.002 near 1.
+    S_hi = 2.0 * shp.self_overlaps(Sq, seed=21, n_samples=1 << 20)[0, 1].item()
 
     def judged(res):
         pose = res["pose"].cpu().numpy()[:6]
@@ -197,10 +250,9 @@ def test_recovers_known_superpositions():
             R = Rotation.from_quat([p[1], p[2], p[3], p[0]]).as_matrix()
             moved = copies[k].astype(np.float64) @ R.T + p[4:]
             rmsd.append(np.sqrt(((moved - q.xyz) ** 2).sum(1).mean()))
-        est, _ = shp.overlap_estimate(Sq, np.zeros(6), Sb, ib[:6], seed=22, n_samples=1 << 16, pose=pose)
+        est, _ = shp.overlap_estimate(Sq, np.zeros(6), Sb, ib[:6], seed=22, n_samples=1 << 18, pose=pose)
         O_ = est.cpu().numpy()[:, 1]
-        S = sq_hi.cpu().numpy()[0, 1] + sb_hi.cpu().numpy()[:6, 1]
-        return np.array(rmsd), O_ / (S - O_)
+        return np.array(rmsd), O_ / (S_hi - O_)
 
     # the hybrid pipeline (align on the exact first-order overlap, score on
     # the union) recovers the copies exactly
@@ -209,12 +261,21 @@ def test_recovers_known_superpositions():
     rmsd, T_hi = judged(hyb)
     assert np.all(rmsd < 0.05), rmsd
     assert np.all(T_hi >= 0.99), T_hi
-    # the union CRN objective with 1024 points has its maximum ~0.1 A RMSD
-    # off the exact superposition (true union Tanimoto ~0.992 there)
+    # The union CRN objective with 1024 points is a Monte-Carlo estimate of
+    # the overlap: its maximum lies off the exact superposition by the CRN
+    # noise (0.06-0.14 A RMSD over six point sets for this query, FP64
+    # oracle with an exact optimiser), where the true union Tanimoto is
+    # 0.98-0.995. The gap is the estimator's, not the optimiser's: it
+    # shrinks as n^-1/2, and with 8192 points the same optimiser recovers
+    # every copy to T >= 0.99.
     res = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=12, starts=8, steps=100, n_crn=1024, n_score=8192)
     rmsd, T_hi = judged(res)
     assert np.all(rmsd < 0.3), rmsd
     assert np.all(T_hi >= 0.98) and np.median(T_hi) >= 0.985, T_hi
+    res8 = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=12, starts=8, steps=100, n_crn=8192, n_score=8192)
+    rmsd8, T8 = judged(res8)
+    assert np.all(rmsd8 < 0.1) and np.median(rmsd8) < 0.6 * np.median(rmsd), (rmsd8, rmsd)
+    assert np.all(T8 >= 0.99), T8
     T = res["T"].cpu().numpy()
     # the unaligned copies do not overlap at all
     est, _ = shp.overlap_estimate(Sq, np.zeros(6), Sb, ib[:6], seed=1, n_samples=1024)
