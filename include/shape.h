@@ -179,6 +179,22 @@ int union_volume_estimate(shp_set S, const int32_t* idx, int64_t n, const shp_mc
 int fo_overlap(shp_set A, const int32_t* ia, shp_set B, const int32_t* ib, int64_t n_pairs,
                const float* poseB, double* out, void* stream);
 
+/*
+ * First-order Tanimoto of every pair (Q[q], D[d]) in closed form (Eq. fo
+ * with heights; Sec. union for the Tanimoto):
+ *   T_fo[q * n_db + d] = O / (S_q + S_d - O),
+ *   O = sum_{i in Q[q], j in D[d]} p_i p_j (pi/(a_i+a_j))^{3/2}
+ *       exp(-a_i a_j / (a_i+a_j) |c_i - c_j|^2)
+ * with S the same closed form of a molecule with itself (fo_overlap of the
+ * molecule with itself). The cheap first stage of the paper's hybrid
+ * pipeline, used to drop clear misses before the union screen. Terms and the
+ * per-pair sum in FP32 (SFU reciprocal, reciprocal square root and exp2).
+ *   fo_self_q [n_q], fo_self_db [n_db] double device; T_fo [n_q * n_db]
+ *   float device. At most 65535 queries per call (SHP_ERANGE).
+ */
+int fo_tanimoto_screen(shp_set Q, shp_set D, const double* fo_self_q, const double* fo_self_db, float* T_fo,
+                       void* stream);
+
 /* Screening settings (Sec. confidence-bounded screening). */
 typedef struct {
   uint64_t seed;        /* Philox key                                              */
@@ -211,6 +227,15 @@ typedef struct {
                                molecules uses stream_base = start and stride =
                                n_global, and reproduces the global screen's
                                numbers for its pairs                        */
+  const int32_t* pairs_q;   /* optional explicit pair list (device int32
+                               [n_pairs], both or neither): only the pairs
+                               (pairs_q[k], pairs_db[k]) are screened and the
+                               outputs are indexed by k; streams stay keyed by
+                               (q, d), so each listed pair gets the numbers
+                               the full screen would give it. NULL = every
+                               pair of Q x D                                  */
+  const int32_t* pairs_db;
+  int64_t n_pairs;
 } shp_screen;
 
 /*
@@ -240,9 +265,11 @@ typedef struct {
  * the samples are the first n_used of the same streams a fixed budget would
  * draw.
  *   self_q [n_q][2], self_db [n_db][2] double device
- *   T, seT [n_q * n_db][2] float device
+ *   T, seT [n_q * n_db][2] (or [n_pairs][2] with a pair list) float device
  * Work is balanced by a persistent kernel that takes pairs largest-first
- * from a device queue (library-allocated, stream-ordered scratch).
+ * from a device queue (library-allocated, stream-ordered scratch); a pair
+ * list is taken in its own order (list large molecules first). Indices of a
+ * pair list outside the sets are skipped (their outputs are not written).
  */
 int tanimoto_screen(shp_set Q, shp_set D, const shp_screen* cfg, const double* self_q,
                     const double* self_db, float* T, float* seT, double* O_out, double* seO_out,

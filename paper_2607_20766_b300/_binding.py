@@ -27,7 +27,7 @@ EXPORTS = ("shp_last_error", "shp_version", "shp_fail_next_allocations", "shape_
            "tanimoto_screen", "shp_screen_variants", "shp_screen_variant_info", "tanimoto_screen_tune", "align_crn_points",
            "overlap_pose_grad", "align_rigid", "shape_set_frames", "union_attributions", "union_volume_cv",
            "cv_features", "mlp_forward", "mlp_loss_grad", "mlp_adam", "mlp_loss_grad_noalloc", "cv_fit_weights",
-           "union_self_estimate", "shp_eval_probe")
+           "union_self_estimate", "shp_eval_probe", "fo_tanimoto_screen")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 33, 64, 6401
 OBJ_FO, OBJ_UNION, OBJ_FO_CLOSED = 0, 1, 2
 
@@ -44,7 +44,8 @@ class ShpScreen(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("tau", ctypes.c_float), ("round", ctypes.c_uint32),
                 ("min_n", ctypes.c_uint32), ("cap", ctypes.c_uint32), ("watch", ctypes.c_uint32),
                 ("variant", ctypes.c_int32), ("omega_q", ctypes.c_void_p), ("omega_db", ctypes.c_void_p),
-                ("self_se_q", ctypes.c_void_p), ("self_se_db", ctypes.c_void_p), ("stream_stride", ctypes.c_uint64)]
+                ("self_se_q", ctypes.c_void_p), ("self_se_db", ctypes.c_void_p), ("stream_stride", ctypes.c_uint64),
+                ("pairs_q", ctypes.c_void_p), ("pairs_db", ctypes.c_void_p), ("n_pairs", ctypes.c_int64)]
 
 
 class ShpAlign(ctypes.Structure):
@@ -90,6 +91,7 @@ def load_library():
         "union_attributions": [_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, _P],
         "union_volume_cv": [_P, _P, ctypes.c_int64, _P, _P, ctypes.c_float, ctypes.c_uint32, _P, _P, _P, _P],
         "cv_features": [_P, _P, _P],
+        "fo_tanimoto_screen": [_P, _P, _P, _P, _P, _P],
         "shp_eval_probe": [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, _P,
                            _P, _P],
         "union_self_estimate": [_P, _P, ctypes.c_int64, _P, _P, ctypes.c_float, ctypes.c_uint32, ctypes.c_uint32, _P,
@@ -253,13 +255,16 @@ def screen_config(seed: int, n_fixed: int = 0, tau: float = 0.005, round: int = 
                   cap: int = 65536, watch: int = 1, flags: int = 0, stream_base: int = 0,
                   variant: int = -1, omega_q: torch.Tensor | None = None,
                   omega_db: torch.Tensor | None = None, self_se_q: torch.Tensor | None = None,
-                  self_se_db: torch.Tensor | None = None, stream_stride: int = 0) -> ShpScreen:
+                  self_se_db: torch.Tensor | None = None, stream_stride: int = 0,
+                  pairs_q: torch.Tensor | None = None, pairs_db: torch.Tensor | None = None) -> ShpScreen:
     """A shp_screen: fixed budget when n_fixed > 0, else adaptive (tau, round, min_n, cap, watch);
     omega_q/omega_db (float32 device, per set atom): control variate of the union slot;
     self_se_q/self_se_db (float64 device, [n, 2]): SEs of the self-overlaps (full delta-method SE(T));
     pair (q, d) uses Philox stream stream_base + q * stream_stride + d (stride 0 = n_db)."""
+    n_list = 0 if pairs_q is None else pairs_q.numel()
     return ShpScreen(seed, stream_base, n_fixed, flags, tau, round, min_n, cap, watch, variant,
-                     _dptr(omega_q), _dptr(omega_db), _dptr(self_se_q), _dptr(self_se_db), stream_stride)
+                     _dptr(omega_q), _dptr(omega_db), _dptr(self_se_q), _dptr(self_se_db), stream_stride,
+                     _dptr(pairs_q), _dptr(pairs_db), n_list)
 
 
 def _self_se(t, S: "ShapeSet"):
@@ -279,7 +284,7 @@ def tanimoto_screen(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: tor
                     out=None, tau: float = 0.005, round: int = 256, min_n: int = 1024, cap: int = 65536,
                     watch: int = 1, variant: int = -1, omega_q: torch.Tensor | None = None,
                     omega_db: torch.Tensor | None = None, self_se_q: torch.Tensor | None = None,
-                    self_se_db: torch.Tensor | None = None, stream_stride: int = 0):
+                    self_se_db: torch.Tensor | None = None, stream_stride: int = 0, pairs=None):
     """Screen every query against every database molecule (fixed budget when
     n_fixed > 0, else adaptive). Returns dict T, seT ([n_q * n_db, 2]
     float32), n_used ([n_q * n_db] int32 view of uint32) and, with
@@ -289,9 +294,18 @@ def tanimoto_screen(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: tor
     the adaptive stop rule, the full delta-method SE. Pair (q, d) draws from
     stream stream_base + q * stream_stride + d (stream_stride 0 = n_db): a
     database shard [start, end) of n_global molecules passes start and
-    n_global to reproduce the whole screen's numbers."""
+    n_global to reproduce the whole screen's numbers. pairs = (q ids, d
+    ids) screens only those pairs (outputs indexed by list position, the
+    same numbers the full screen gives them)."""
     dev = Q.device
-    npairs = Q.n_mol * D.n_mol
+    pq = pd = None
+    if pairs is not None:
+        if pairs[0] is None or pairs[1] is None:
+            raise ShapeError(-1, "tanimoto_screen: a pair list needs both query and database ids")
+        pq, pd = _device_i32(pairs[0], dev), _device_i32(pairs[1], dev)
+        if pq.numel() != pd.numel():
+            raise ValueError("pair lists differ in length")
+    npairs = Q.n_mol * D.n_mol if pq is None else pq.numel()
     if out is None:
         out = dict(T=torch.empty((npairs, 2), dtype=torch.float32, device=dev),
                    seT=torch.empty((npairs, 2), dtype=torch.float32, device=dev),
@@ -302,13 +316,25 @@ def tanimoto_screen(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: tor
     omega_q, omega_db = _weights(omega_q, Q), _weights(omega_db, D)
     self_se_q, self_se_db = _self_se(self_se_q, Q), _self_se(self_se_db, D)
     cfg = screen_config(seed, n_fixed, tau, round, min_n, cap, watch, flags, stream_base, variant, omega_q, omega_db,
-                        self_se_q, self_se_db, stream_stride)
+                        self_se_q, self_se_db, stream_stride, pq, pd)
     self_q = self_q.to(device=dev, dtype=torch.float64).contiguous()
     self_db = self_db.to(device=dev, dtype=torch.float64).contiguous()
     _check(load_library().tanimoto_screen(Q.handle, D.handle, ctypes.byref(cfg), _dptr(self_q), _dptr(self_db),
                                           _dptr(out["T"]), _dptr(out["seT"]), _dptr(out.get("O")),
                                           _dptr(out.get("seO")), _dptr(out.get("n_used")), _stream(stream)))
     return out
+
+
+def fo_tanimoto_screen(Q: ShapeSet, D: ShapeSet, fo_self_q: torch.Tensor, fo_self_db: torch.Tensor, stream=None,
+                       out: torch.Tensor | None = None) -> torch.Tensor:
+    """Closed-form first-order Tanimoto of every pair, [n_q * n_db] float32
+    (pair q * n_db + d); fo_self_*: the closed-form self-overlaps [n]."""
+    dev = Q.device
+    T = out if out is not None else torch.empty(Q.n_mol * D.n_mol, dtype=torch.float32, device=dev)
+    sq = fo_self_q.to(device=dev, dtype=torch.float64).contiguous()
+    sd = fo_self_db.to(device=dev, dtype=torch.float64).contiguous()
+    _check(load_library().fo_tanimoto_screen(Q.handle, D.handle, _dptr(sq), _dptr(sd), _dptr(T), _stream(stream)))
+    return T
 
 
 def fail_next_allocations(count: int) -> None:

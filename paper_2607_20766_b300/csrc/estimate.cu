@@ -390,6 +390,8 @@ struct CrossArgs {
   double* se;
   // screen modes
   const int32_t* order_b;
+  const int32_t* list_q;   // explicit pair list (screen modes), or NULL
+  const int32_t* list_b;
   int32_t n_q, n_db;
   uint64_t stream_stride;  // pair (q, d) uses stream stream_base + q * stream_stride + d
   const double* self_q;
@@ -564,6 +566,11 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) cross_kernel(const Cr
       xb = args.ib[item];
       out_idx = (int64_t)item;
       if (args.pose) pose = args.pose + 7 * (int64_t)item;
+    } else if (args.list_q) {
+      const int64_t t = (int64_t)item * args.item_stride;
+      xa = args.list_q[t];
+      xb = args.list_b[t];
+      out_idx = t;
     } else {
       const int64_t t = (int64_t)item * args.item_stride;
       const int64_t rank = t / args.n_q;
@@ -1016,6 +1023,16 @@ int screen_args(shp_set Q, shp_set D, const shp_screen* cfg, const double* self_
   }
   a.self_se_q = cfg->self_se_q;
   a.self_se_db = cfg->self_se_db;
+  if ((cfg->pairs_q == nullptr) != (cfg->pairs_db == nullptr) || cfg->n_pairs < 0 ||
+      (cfg->pairs_q == nullptr && cfg->n_pairs != 0)) {
+    set_error("%s: give both pair-list arrays with n_pairs >= 0, or neither (n_pairs 0)", who);
+    return SHP_EINVAL;
+  }
+  if (cfg->pairs_q) {
+    a.list_q = cfg->pairs_q;
+    a.list_b = cfg->pairs_db;
+    a.n_items = cfg->n_pairs;
+  }
   return SHP_OK;
 }
 

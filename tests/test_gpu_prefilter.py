@@ -1,0 +1,56 @@
+"""The first-order prefilter of the screen (the cheap stage of the paper's
+hybrid pipeline, Sec. first-order overlap): the closed-form first-order
+Tanimoto of every pair against the FP64 oracle, and the screen of an
+explicit pair list, whose pairs get exactly the numbers the full screen
+gives them (streams keyed by (query, database) ids)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2607_20766_b300 as shp
+from paper_2607_20766_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sets():
+    q = synth.principal_axes(synth.generate(31, [20, 33, 48]))
+    d = synth.principal_axes(synth.generate(32, synth.counts_heavy(32, 300)))
+    return q, d, shp.shape_set_load(q), shp.shape_set_load(d)
+
+
+def test_fo_tanimoto_matches_oracle(sets):
+    q, d, Sq, Sd = sets
+    kq, kd = np.arange(q.n_mol), np.arange(d.n_mol)
+    fq, fd = O.fo_overlap(q, kq, q, kq), O.fo_overlap(d, kd, d, kd)
+    T = shp.fo_tanimoto_screen(Sq, Sd, torch.tensor(fq), torch.tensor(fd)).cpu().numpy()
+    iq, idd = np.meshgrid(kq, kd, indexing="ij")
+    O_ = O.fo_overlap(q, iq.ravel(), d, idd.ravel())
+    ref = O_ / (fq[iq.ravel()] + fd[idd.ravel()] - O_)
+    np.testing.assert_allclose(T, ref, rtol=2e-5)
+    # the library's own closed-form self-overlaps serve as well
+    sq, sd = shp.self_overlaps(Sq, seed=1, n_samples=256), shp.self_overlaps(Sd, seed=1, n_samples=256)
+    T2 = shp.fo_tanimoto_screen(Sq, Sd, sq[:, 0], sd[:, 0]).cpu().numpy()
+    np.testing.assert_allclose(T2, ref, rtol=2e-5)
+
+
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_pair_list_screen_equals_the_full_screen(sets, adaptive):
+    q, d, Sq, Sd = sets
+    sq, sq_se, _ = shp.self_overlaps(Sq, seed=2, n_samples=4096, with_se=True)
+    sd, sd_se, _ = shp.self_overlaps(Sd, seed=2, n_samples=4096, stream_base=5, with_se=True)
+    kw = dict(tau=0.01, min_n=512, cap=8192) if adaptive else dict(n_fixed=1024)
+    full = shp.tanimoto_screen(Sq, Sd, sq, sd, seed=8, with_overlaps=True, self_se_q=sq_se, self_se_db=sd_se, **kw)
+    rng = np.random.default_rng(1)
+    pick = rng.choice(q.n_mol * d.n_mol, 200, replace=False)
+    # largest database molecules first, as a caller should list them
+    pick = pick[np.argsort(-d.counts[pick % d.n_mol], kind="stable")]
+    lst = shp.tanimoto_screen(Sq, Sd, sq, sd, seed=8, with_overlaps=True, self_se_q=sq_se, self_se_db=sd_se,
+                              pairs=(pick // d.n_mol, pick % d.n_mol), **kw)
+    for k in ("T", "seT", "O", "seO", "n_used"):
+        np.testing.assert_array_equal(lst[k].cpu().numpy(), full[k].cpu().numpy()[pick], err_msg=k)
+    with pytest.raises(shp.ShapeError):
+        shp.tanimoto_screen(Sq, Sd, sq, sd, seed=8, n_fixed=256,
+                            pairs=(torch.zeros(3, dtype=torch.int32, device="cuda"), None))
