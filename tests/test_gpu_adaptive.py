@@ -139,33 +139,60 @@ def test_tuner_picks_a_valid_variant(small_screen):
     assert sp4[best_a] and np.all(times_a[~sp4] == -1) and np.all(times_a[sp4] > 0)
 
 
+def oracle_self_at(ms, ids, n_used, seed, stream_base, target, rnd):
+    """The oracle's union self-overlaps and SEs of molecules `ids` at the
+    library's sample counts (same streams), and the check of each adaptive
+    stop decision: SE/O <= target at n unless capped, > target one round
+    earlier unless at the first round."""
+    so, se = np.zeros(len(ids)), np.zeros(len(ids))
+    for j, (k, n) in enumerate(zip(ids, n_used)):
+        _, _, a, b = O.union_volume_estimate(ms, [k], seed=seed, n=int(n), stream_base=stream_base + int(k))
+        so[j], se[j] = a[0], b[0]
+        assert se[j] <= target * so[j] * (1 + 1e-4)
+        if n > rnd:
+            _, _, a0, b0 = O.union_volume_estimate(ms, [k], seed=seed, n=int(n - rnd), stream_base=stream_base + int(k))
+            assert b0[0] > target * a0[0] * (1 - 1e-4)
+    return so, se
+
+
 def test_adaptive_full_size_sampled():
     """16 queries (20-48 atoms) x 1,000,000 molecules (18-60, heavy-tailed
-    toward 40), rounds of 256, SE(T) <= 0.005 or 65,536 per direction: the
-    launch the benchmark times (autotuned variant, replayed CUDA graph); 24
-    sampled pairs checked by the oracle."""
+    toward 40), rounds of 256, full SE(T) <= 0.005 or 65,536 per direction:
+    the launch the benchmark times (self-overlaps to relative SE 3.5e-3,
+    queries 8.75e-4, their SEs in SE(T) and the stop rule; autotuned
+    variant, replayed CUDA graph); 24 sampled pairs and their molecules'
+    self-overlaps checked by the oracle."""
     q, d = synth.adaptive_screen()
     Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
-    selfq = shp.self_overlaps(Sq, seed=11, n_samples=4096, stream_base=0)
-    selfd = shp.self_overlaps(Sd, seed=11, n_samples=4096, stream_base=16)
-    shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=16384, tau=0.005, cap=65536)
+    selfq, seq, nq = shp.self_overlaps(Sq, seed=11, n_samples=1 << 24, stream_base=0, target_rel_se=8.75e-4,
+                                       round=4096, with_se=True)
+    selfd, sed, nd = shp.self_overlaps(Sd, seed=11, n_samples=1 << 22, stream_base=16, target_rel_se=3.5e-3,
+                                       round=256, with_se=True)
+    kw = dict(self_se_q=seq, self_se_db=sed)
+    shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=16384, tau=0.005, cap=65536, **kw)
     g = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, selfq, selfd, seed=77, tau=0.005, round=256, min_n=1024,
-                      cap=65536, with_overlaps=True)
+                      cap=65536, with_overlaps=True, **kw)
     res = g.replay()
     torch.cuda.synchronize()
     nu = res["n_used"].cpu().numpy()
     assert np.all(nu % 256 == 0) and nu.min() >= 1024 and nu.max() <= 65536
     rng = np.random.default_rng(3)
-    pairs = np.sort(rng.choice(len(nu), 24, replace=False))
-    # the oracle's self-overlaps for the sampled molecules (same streams as the library call)
-    sq = np.zeros((q.n_mol, 2))
-    sd = np.zeros((d.n_mol, 2))
+    # 24 pairs of two queries (the oracle's query self-overlaps take ~10^6 samples each)
+    pairs = np.sort(np.concatenate([qq * d.n_mol + rng.choice(d.n_mol, 12, replace=False)
+                                    for qq in rng.choice(q.n_mol, 2, replace=False)]))
     qs, ds = np.unique(pairs // d.n_mol), np.unique(pairs % d.n_mol)
+    sq, sd = np.zeros((q.n_mol, 2)), np.zeros((d.n_mol, 2))
+    eq, ed = np.zeros((q.n_mol, 2)), np.zeros((d.n_mol, 2))
     sq[qs, 0] = O.fo_overlap(q, qs, q, qs)
-    sq[qs, 1] = [O.union_volume_estimate(q, [k], seed=11, n=4096, stream_base=int(k))[2][0] for k in qs]
     sd[ds, 0] = O.fo_overlap(d, ds, d, ds)
-    sd[ds, 1] = [O.union_volume_estimate(d, [k], seed=11, n=4096, stream_base=16 + int(k))[2][0] for k in ds]
-    check_adaptive_against_oracle(q, d, res, sq, sd, 77, 0.005, 256, 1024, 65536, pairs, d.n_mol)
+    sq[qs, 1], eq[qs, 1] = oracle_self_at(q, qs, nq.cpu().numpy()[qs], 11, 0, 8.75e-4, 4096)
+    sd[ds, 1], ed[ds, 1] = oracle_self_at(d, ds, nd.cpu().numpy()[ds], 11, 16, 3.5e-3, 256)
+    for got, ref, what in ((selfq.cpu().numpy()[qs], sq[qs], "query self-overlaps"),
+                           (selfd.cpu().numpy()[ds], sd[ds], "database self-overlaps")):
+        assert_close(got, ref, what=what)
+    assert_close(sed.cpu().numpy()[ds, 1], ed[ds, 1], rtol=1e-4, what="their SEs")
+    check_adaptive_against_oracle(q, d, res, sq, sd, 77, 0.005, 256, 1024, 65536, pairs, d.n_mol, sq_se=eq,
+                                  sd_se=ed)
 
 
 def test_graph_captured_adaptive_step_matches_eager(small_screen):
@@ -280,20 +307,23 @@ def test_graph_replay_reads_inputs_updated_in_place(small_screen):
 
 
 def test_adaptive_fitted_control_variate_full_size_sampled():
-    """The benchmark's fastest arm at its full size: 16 x 1,000,000 adaptive
-    screen with least-squares weights fitted from 4096 samples per molecule;
-    24 sampled pairs recomputed by the oracle (same weights, same streams) and
+    """The benchmark's control-variate arm at its full size: 16 x 1,000,000
+    adaptive screen with least-squares weights fitted from 4096 samples per
+    molecule and the full SE(T); 24 sampled pairs recomputed by the oracle
+    (same weights, same streams, the library's self-overlaps and SEs) and
     their stop decisions checked."""
     q, d = synth.adaptive_screen()
     Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
-    selfq = shp.self_overlaps(Sq, seed=11, n_samples=4096, stream_base=0)
-    selfd = shp.self_overlaps(Sd, seed=11, n_samples=4096, stream_base=16)
+    selfq, seq, _ = shp.self_overlaps(Sq, seed=11, n_samples=1 << 24, stream_base=0, target_rel_se=8.75e-4,
+                                      round=4096, with_se=True)
+    selfd, sed, _ = shp.self_overlaps(Sd, seed=11, n_samples=1 << 22, stream_base=16, target_rel_se=3.5e-3,
+                                      round=256, with_se=True)
     wq = shp.cv_fit_weights(Sq, seed=91, n_samples=4096)
     wd = shp.cv_fit_weights(Sd, seed=92, n_samples=4096)
-    shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=16384, tau=0.005, cap=65536, omega_q=wq,
-                             omega_db=wd)
+    kw = dict(omega_q=wq, omega_db=wd, self_se_q=seq, self_se_db=sed)
+    shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=16384, tau=0.005, cap=65536, **kw)
     g = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, selfq, selfd, seed=77, tau=0.005, round=256, min_n=1024,
-                      cap=65536, with_overlaps=True, omega_q=wq, omega_db=wd)
+                      cap=65536, with_overlaps=True, **kw)
     res = g.replay()
     torch.cuda.synchronize()
     nu = res["n_used"].cpu().numpy()
@@ -302,8 +332,9 @@ def test_adaptive_fitted_control_variate_full_size_sampled():
     sq = np.zeros((q.n_mol, 2))
     sd = np.zeros((d.n_mol, 2))
     qs, ds = np.unique(pairs // d.n_mol), np.unique(pairs % d.n_mol)
-    sq[qs] = selfq.cpu().numpy()[qs]  # the screen's T uses the library's self-overlaps
+    sq[qs] = selfq.cpu().numpy()[qs]  # the screen's T uses the library's self-overlaps and their SEs
     sd[ds] = selfd[torch.as_tensor(ds, device=selfd.device)].cpu().numpy()
     check_adaptive_against_oracle(q, d, res, sq, sd, 77, 0.005, 256, 1024, 65536, pairs, d.n_mol,
                                   omega_q=wq.cpu().numpy().astype(np.float64),
-                                  omega_d=wd.cpu().numpy().astype(np.float64))
+                                  omega_d=wd.cpu().numpy().astype(np.float64), sq_se=seq.cpu().numpy(),
+                                  sd_se=sed.cpu().numpy())
