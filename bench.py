@@ -369,11 +369,12 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 126 MB L2
 
-    # project autotuner: time every launch variant on 8192 pairs, keep the fastest
+    # project autotuner: time every launch variant on 65,536 pairs (~28 per resident warp: with
+    # fewer, the tail of the persistent launch decides the ranking), keep the fastest
     selfq0 = shp.self_overlaps(Sq, seed=1, n_samples=n, stream_base=0)
     selfd0 = shp.self_overlaps(Sd, seed=1, n_samples=n, stream_base=1 + start)
     tuned, tune_ms = shp.tanimoto_screen_tune(Sq, Sd, selfq0, selfd0, seed=SEED_WORKLOAD, n_fixed=n,
-                                              n_sample=min(8192, q.n_mol * d.n_mol))
+                                              n_sample=min(65536, q.n_mol * d.n_mol))
 
     # the step as two CUDA graphs (self-overlaps of both sets; the screen), so
     # the screen kernel can be timed on its own between the replays; a shard
@@ -590,7 +591,7 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
     nd_c = d.counts.astype(np.int64)
     self_evals = int((nq_self.cpu().numpy().astype(np.int64) * nq_c).sum() + (nd_self * nd_c).sum())
     se_kw = dict(self_se_q=selfq_se, self_se_db=selfd_se)
-    best, times = shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=16384, tau=tau, cap=cap, **se_kw)
+    best, times = shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=65536, tau=tau, cap=cap, **se_kw)
     g_ad = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, selfq, selfd, seed=77, tau=tau, round=256, min_n=1024,
                          cap=cap, **se_kw)
     torch.cuda.synchronize()
@@ -664,7 +665,7 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
         weights (per atom of both sets) come from `weights()`, timed."""
         (wq, wd), t_w = timed(weights)
         kept.update(wq=wq, wd=wd, t_w=t_w)
-        best_cv, _ = shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=16384, tau=tau, cap=cap,
+        best_cv, _ = shp.tanimoto_screen_tune(Sq, Sd, selfq, selfd, seed=77, n_sample=65536, tau=tau, cap=cap,
                                               omega_q=wq, omega_db=wd, **se_kw)
         g_cv = shp.StepGraph(shp.tanimoto_screen, Sq, Sd, selfq, selfd, seed=77, tau=tau, round=256, min_n=1024,
                              cap=cap, omega_q=wq, omega_db=wd, **se_kw)
