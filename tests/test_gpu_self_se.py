@@ -173,3 +173,33 @@ def test_least_squares_fit_skips_an_id_outside_the_set():
     for ref, k in ((ref2, 2), (ref0, 0)):
         lo, hi = ms.offsets[k], ms.offsets[k + 1]
         np.testing.assert_allclose(om[lo:hi], ref[lo:hi], rtol=1e-4, atol=2e-4 * np.abs(ref[lo:hi]).max())
+
+
+def test_full_se_matches_the_spread_of_T_over_replicates():
+    """End to end on the GPU: 400 independent replicates of one pair (copies
+    of both molecules, so every replicate has its own self-overlap and pair
+    streams) with noisy self-overlaps (256 samples): the spread of the union T
+    is what the screen's full SE(T) predicts, and several times what the
+    paper's pair-only SE predicts."""
+    a, b = synth.single_pair(n_a=8, n_b=10, seed_a=3, seed_b=4, separation=0.8)
+    K = 400
+
+    def copies(ms):
+        n = ms.n_atoms
+        return MolSet(np.tile(ms.xyz, (K, 1)), np.tile(ms.radius, K), np.arange(K + 1, dtype=np.int32) * n,
+                      np.tile(ms.elem, K))
+
+    Sa, Sb = shp.shape_set_load(copies(a)), shp.shape_set_load(copies(b))
+    sa, sa_se, _ = shp.self_overlaps(Sa, seed=101, n_samples=256, with_se=True)
+    sb, sb_se, _ = shp.self_overlaps(Sb, seed=101, n_samples=256, stream_base=10 * K, with_se=True)
+    k = torch.arange(K, dtype=torch.int32, device="cuda")
+    full = shp.tanimoto_screen(Sa, Sb, sa, sb, seed=202, n_fixed=4096, pairs=(k, k), self_se_q=sa_se,
+                               self_se_db=sb_se)
+    pair_only = shp.tanimoto_screen(Sa, Sb, sa, sb, seed=202, n_fixed=4096, pairs=(k, k))
+    T = full["T"][:, 1].cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(T, pair_only["T"][:, 1].cpu().numpy())
+    var_T = T.var(ddof=1)
+    r_full = var_T / np.mean(full["seT"][:, 1].cpu().numpy().astype(np.float64) ** 2)
+    r_pair = var_T / np.mean(pair_only["seT"][:, 1].cpu().numpy().astype(np.float64) ** 2)
+    assert 0.72 < r_full < 1.30, (r_full, r_pair)
+    assert r_pair > 4.0, (r_full, r_pair)
