@@ -702,20 +702,18 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
         to screening: the closed-form first-order Tanimoto of every pair ranks
         each query's database; only its best `keep` fraction goes through
         the adaptive union screen (fitted control variate, the weights and
-        self-overlaps of the arm above). A listed pair gets exactly the
+        self-overlaps of the arm above); both stages are library kernels
+        (closed-form first order, exact per-query top-k). A listed pair gets exactly the
         numbers of the unfiltered screen, so recall@k (the share of each
         query's union top-k of the unfiltered screen that survives) measures
         the prefilter alone."""
         wq, wd, T_full = kept["wq"], kept["wd"], kept["T"]
 
+        fo_q, fo_d = selfq[:, 0].contiguous(), selfd[:, 0].contiguous()
+
         def stage1():
-            T_fo = shp.fo_tanimoto_screen(Sq, Sd, selfq[:, 0], selfd[:, 0]).view(q.n_mol, d.n_mol)
-            k = max(k_top, int(keep * d.n_mol))
-            ids = torch.topk(T_fo, k, dim=1).indices  # [n_q, k] database ids
-            qid = torch.arange(q.n_mol, device=ids.device).repeat_interleave(k)
-            did = ids.reshape(-1)
-            order = torch.argsort(torch.as_tensor(d.counts, device=ids.device)[did], descending=True, stable=True)
-            return qid[order].int().contiguous(), did[order].int().contiguous()
+            T_fo = shp.fo_tanimoto_screen(Sq, Sd, fo_q, fo_d)
+            return shp.fo_prefilter_select(Sq, Sd, T_fo, max(k_top, int(keep * d.n_mol)))
 
         stage1()  # warm-up
         (pq, pd), t_fo = timed(stage1)

@@ -195,6 +195,23 @@ int fo_overlap(shp_set A, const int32_t* ia, shp_set B, const int32_t* ib, int64
 int fo_tanimoto_screen(shp_set Q, shp_set D, const double* fo_self_q, const double* fo_self_db, float* T_fo,
                        void* stream);
 
+/*
+ * Selection step of the first-order prefilter: for every query q the k
+ * database molecules with the largest scores T[q * n_db + d] (e.g.
+ * fo_tanimoto_screen's output), exactly: every score above the k-th largest
+ * is kept, and of the scores equal to it the lowest database ids until k.
+ * Writes the pair list of tanimoto_screen, per query in ascending database
+ * id: pairs_q[q * k + j] = q, pairs_db[q * k + j] = d. Deterministic (a
+ * radix select on the FP32 scores' order-preserving 32-bit keys, three
+ * passes of 12, 12 and 8 bits). Scores must not be NaN.
+ *   T [n_q * n_db] float device; pairs_q, pairs_db [n_q * k] int32 device;
+ *   1 <= k <= n_db (else SHP_ERANGE), at most 65535 queries.
+ * Scratch (per-query histograms and per-chunk counts) is stream-ordered
+ * library memory.
+ */
+int fo_prefilter_select(shp_set Q, shp_set D, const float* T, int64_t k, int32_t* pairs_q, int32_t* pairs_db,
+                        void* stream);
+
 /* Screening settings (Sec. confidence-bounded screening). */
 typedef struct {
   uint64_t seed;        /* Philox key                                              */

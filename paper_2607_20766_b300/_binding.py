@@ -27,7 +27,8 @@ EXPORTS = ("shp_last_error", "shp_version", "shp_fail_next_allocations", "shape_
            "tanimoto_screen", "shp_screen_variants", "shp_screen_variant_info", "tanimoto_screen_tune", "align_crn_points",
            "overlap_pose_grad", "align_rigid", "shape_set_frames", "union_attributions", "union_volume_cv",
            "cv_features", "mlp_forward", "mlp_loss_grad", "mlp_adam", "mlp_loss_grad_noalloc", "cv_fit_weights",
-           "union_self_estimate", "shp_eval_probe", "fo_tanimoto_screen")
+           "union_self_estimate", "shp_eval_probe", "fo_tanimoto_screen",
+           "fo_prefilter_select")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 33, 64, 6401
 OBJ_FO, OBJ_UNION, OBJ_FO_CLOSED = 0, 1, 2
 
@@ -92,6 +93,7 @@ def load_library():
         "union_volume_cv": [_P, _P, ctypes.c_int64, _P, _P, ctypes.c_float, ctypes.c_uint32, _P, _P, _P, _P],
         "cv_features": [_P, _P, _P],
         "fo_tanimoto_screen": [_P, _P, _P, _P, _P, _P],
+        "fo_prefilter_select": [_P, _P, _P, ctypes.c_int64, _P, _P, _P],
         "shp_eval_probe": [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, _P,
                            _P, _P],
         "union_self_estimate": [_P, _P, ctypes.c_int64, _P, _P, ctypes.c_float, ctypes.c_uint32, ctypes.c_uint32, _P,
@@ -335,6 +337,18 @@ def fo_tanimoto_screen(Q: ShapeSet, D: ShapeSet, fo_self_q: torch.Tensor, fo_sel
     sd = fo_self_db.to(device=dev, dtype=torch.float64).contiguous()
     _check(load_library().fo_tanimoto_screen(Q.handle, D.handle, _dptr(sq), _dptr(sd), _dptr(T), _stream(stream)))
     return T
+
+
+def fo_prefilter_select(Q: ShapeSet, D: ShapeSet, T: torch.Tensor, k: int, stream=None):
+    """(pairs_q, pairs_db) int32 device tensors [n_q * k]: for every query the
+    k database molecules with the largest scores T ([n_q * n_db] float32),
+    ties at the k-th score by lowest id, each query's pairs in ascending id."""
+    dev = Q.device
+    T = T.to(device=dev, dtype=torch.float32).contiguous()
+    pq = torch.empty(Q.n_mol * k, dtype=torch.int32, device=dev)
+    pd = torch.empty(Q.n_mol * k, dtype=torch.int32, device=dev)
+    _check(load_library().fo_prefilter_select(Q.handle, D.handle, _dptr(T), k, _dptr(pq), _dptr(pd), _stream(stream)))
+    return pq, pd
 
 
 def fail_next_allocations(count: int) -> None:

@@ -54,3 +54,31 @@ def test_pair_list_screen_equals_the_full_screen(sets, adaptive):
     with pytest.raises(shp.ShapeError):
         shp.tanimoto_screen(Sq, Sd, sq, sd, seed=8, n_fixed=256,
                             pairs=(torch.zeros(3, dtype=torch.int32, device="cuda"), None))
+
+
+@pytest.mark.parametrize("k", [1, 7, 100, 299, 300])
+def test_prefilter_selection_is_the_exact_top_k(sets, k):
+    """Per query the k largest scores, ties at the k-th by the lowest id,
+    each query's pairs in ascending id: against numpy on scores with many
+    ties (quantised) and negative values, and on the first-order Tanimoto."""
+    q, d, Sq, Sd = sets
+    rng = np.random.default_rng(k)
+    scores = np.round(rng.normal(0.3, 0.4, (q.n_mol, d.n_mol)), 2).astype(np.float32)
+    sq = shp.self_overlaps(Sq, seed=1, n_samples=256)
+    sd = shp.self_overlaps(Sd, seed=1, n_samples=256)
+    T_fo = shp.fo_tanimoto_screen(Sq, Sd, sq[:, 0], sd[:, 0]).cpu().numpy().reshape(q.n_mol, d.n_mol)
+    for S in (scores, T_fo):
+        pq, pd = shp.fo_prefilter_select(Sq, Sd, torch.tensor(S.reshape(-1)), k)
+        pq, pd = pq.cpu().numpy().reshape(q.n_mol, k), pd.cpu().numpy().reshape(q.n_mol, k)
+        for i in range(q.n_mol):
+            order = np.lexsort((np.arange(d.n_mol), -S[i].astype(np.float64)))[:k]  # value desc, id asc
+            np.testing.assert_array_equal(pq[i], i)
+            np.testing.assert_array_equal(pd[i], np.sort(order))
+
+
+def test_prefilter_selection_rejects_bad_k(sets):
+    q, d, Sq, Sd = sets
+    T = torch.zeros(q.n_mol * d.n_mol, dtype=torch.float32, device="cuda")
+    for k in (0, d.n_mol + 1):
+        with pytest.raises(shp.ShapeError):
+            shp.fo_prefilter_select(Sq, Sd, T, k)
