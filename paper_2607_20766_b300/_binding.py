@@ -7,6 +7,7 @@ library or a CUDA device the calls raise.
 from __future__ import annotations
 
 import ctypes
+import functools
 import os
 
 import numpy as np
@@ -134,6 +135,21 @@ def _dptr(t):
     return None if t is None else t.data_ptr()
 
 
+def _on_stream(fn):
+    """Run a wrapper with its `stream` argument (a torch.cuda.Stream) as the
+    current stream, so that the device temporaries it creates (index and
+    argument tensors made contiguous, outputs) are allocated on, and ordered
+    with, the stream the library call is queued on. A raw cudaStream_t
+    handle (an int) is passed through unchanged."""
+    @functools.wraps(fn)
+    def wrapped(*args, stream=None, **kwargs):
+        if isinstance(stream, torch.cuda.Stream):
+            with torch.cuda.stream(stream):
+                return fn(*args, stream=stream, **kwargs)
+        return fn(*args, stream=stream, **kwargs)
+    return wrapped
+
+
 def _device_i32(x, device) -> torch.Tensor:
     if isinstance(x, torch.Tensor):
         t = x.to(device=device, dtype=torch.int32)
@@ -202,6 +218,7 @@ def shape_set_load(ms, c_alpha: float = 2.41798793, stream=None, device=None) ->
     return ShapeSet(h.value, len(off) - 1, int(off[-1]), np.diff(off).astype(np.int32), device)
 
 
+@_on_stream
 def overlap_estimate(A: ShapeSet, ia, B: ShapeSet, ib, seed: int, n_samples: int, flags: int = SYMMETRIC,
                      stream_base: int = 0, pose=None, stream=None, out=None):
     """(est, se): [n_pairs, 2] float64 device tensors; slot 0 first order, slot 1 union."""
@@ -223,6 +240,7 @@ def overlap_estimate(A: ShapeSet, ia, B: ShapeSet, ib, seed: int, n_samples: int
     return est, se
 
 
+@_on_stream
 def union_volume_estimate(S: ShapeSet, idx=None, seed: int = 0, n_samples: int = 4096, flags: int = 0,
                           stream_base: int = 0, stream=None, out=None):
     """(vol, vol_se, self_overlap, self_se): [n] float64 device tensors."""
@@ -239,6 +257,7 @@ def union_volume_estimate(S: ShapeSet, idx=None, seed: int = 0, n_samples: int =
     return outs
 
 
+@_on_stream
 def fo_overlap(A: ShapeSet, ia, B: ShapeSet, ib, pose=None, stream=None, out=None):
     """Closed-form first-order overlaps, [n_pairs] float64 device tensor."""
     dev = A.device
@@ -281,6 +300,7 @@ def _weights(omega, S: "ShapeSet"):
     return omega.to(device=S.device, dtype=torch.float32).contiguous()
 
 
+@_on_stream
 def tanimoto_screen(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: torch.Tensor, seed: int,
                     n_fixed: int = 0, flags: int = 0, stream_base: int = 0, stream=None, with_overlaps: bool = False,
                     out=None, tau: float = 0.005, round: int = 256, min_n: int = 1024, cap: int = 65536,
@@ -327,6 +347,7 @@ def tanimoto_screen(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: tor
     return out
 
 
+@_on_stream
 def fo_tanimoto_screen(Q: ShapeSet, D: ShapeSet, fo_self_q: torch.Tensor, fo_self_db: torch.Tensor, stream=None,
                        out: torch.Tensor | None = None) -> torch.Tensor:
     """Closed-form first-order Tanimoto of every pair, [n_q * n_db] float32
@@ -339,6 +360,7 @@ def fo_tanimoto_screen(Q: ShapeSet, D: ShapeSet, fo_self_q: torch.Tensor, fo_sel
     return T
 
 
+@_on_stream
 def fo_prefilter_select(Q: ShapeSet, D: ShapeSet, T: torch.Tensor, k: int, stream=None):
     """(pairs_q, pairs_db) int32 device tensors [n_q * k]: for every query the
     k database molecules with the largest scores T ([n_q * n_db] float32),
@@ -357,6 +379,7 @@ def fail_next_allocations(count: int) -> None:
     _check(load_library().shp_fail_next_allocations(count))
 
 
+@_on_stream
 def eval_probe(Q: ShapeSet, iq: int, D: ShapeSet, id_: int, variant: int = -1, draw: bool = False,
                batches: int = 256, stream=None) -> int:
     """Roofline calibration: the screen variant's per-sample work on the pair
@@ -381,6 +404,7 @@ def screen_variant_info(v: int) -> dict:
     return dict(sp=info[0], form=info[1], warps=info[2], ctas=info[3])
 
 
+@_on_stream
 def tanimoto_screen_tune(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: torch.Tensor, seed: int,
                          n_fixed: int = 0, n_sample: int = 4096, stream=None, tau: float = 0.005, round: int = 256,
                          min_n: int = 1024, cap: int = 65536, watch: int = 1, omega_q: torch.Tensor | None = None,
@@ -409,6 +433,7 @@ def tanimoto_screen_tune(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db
     return best.value, times
 
 
+@_on_stream
 def self_overlaps(S: ShapeSet, seed: int, n_samples: int, stream_base: int = 0, stream=None,
                   target_rel_se: float = 0.0, round: int = 256, omega=None, with_se: bool = False):
     """[n_mol, 2] float64 device tensor: slot 0 closed-form first-order
@@ -440,6 +465,7 @@ def self_overlaps(S: ShapeSet, seed: int, n_samples: int, stream_base: int = 0, 
 
 # ---------------------------------------------------------------- alignment
 
+@_on_stream
 def align_crn_points(Q: ShapeSet, iq: int, seed: int, n: int, stream_base: int = 0, stream=None):
     """[n, 4] float32 device tensor: CRN points of Q[iq] and their union weights."""
     pts = torch.empty((n, 4), dtype=torch.float32, device=Q.device)
@@ -448,6 +474,7 @@ def align_crn_points(Q: ShapeSet, iq: int, seed: int, n: int, stream_base: int =
     return pts
 
 
+@_on_stream
 def overlap_pose_grad(Q: ShapeSet, iq: int, points: torch.Tensor, B: ShapeSet, ib, pose, objective: int = OBJ_UNION,
                       stream=None):
     """(value [n] float64, grad [n, 7] float32): CRN overlap of B[ib[k]] posed by
@@ -488,6 +515,7 @@ def pose_overlap(pose, Q: ShapeSet, iq: int, points: torch.Tensor, B: ShapeSet, 
     return PoseOverlap.apply(pose, Q, iq, points, B, ib, objective)
 
 
+@_on_stream
 def align_rigid(Q: ShapeSet, iq: int, B: ShapeSet, ib, self_q: torch.Tensor, self_db: torch.Tensor, seed: int = 0,
                 starts: int = 8, steps: int = 100, n_crn: int = 1024, objective: int = OBJ_UNION, lr: float = 0.02,
                 lr_t: float = 0.05, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, n_score: int = 4096,
@@ -514,6 +542,7 @@ def align_rigid(Q: ShapeSet, iq: int, B: ShapeSet, ib, self_q: torch.Tensor, sel
 
 # ---------------------------------------------------------------- control variate
 
+@_on_stream
 def union_attributions(S: ShapeSet, seed: int, M: int = 512, stream_base: int = 0, stream=None):
     """[n_atoms] float32 device tensor: om*_i = E_{N(c_i, 1/(2 alpha_i))}[u/m]."""
     out = torch.empty(S.n_atoms, dtype=torch.float32, device=S.device)
@@ -521,6 +550,7 @@ def union_attributions(S: ShapeSet, seed: int, M: int = 512, stream_base: int = 
     return out
 
 
+@_on_stream
 def union_volume_cv(S: ShapeSet, idx=None, omega=None, seed: int = 0, n_samples: int = 4096,
                     target_rel_se: float = 0.0, round: int = 256, stream_base: int = 0, stream=None):
     """(vol, vol_se, n_used): union volumes with the control variate omega
@@ -542,6 +572,7 @@ def union_volume_cv(S: ShapeSet, idx=None, omega=None, seed: int = 0, n_samples:
     return vol, se, nu
 
 
+@_on_stream
 def union_self_estimate(S: ShapeSet, idx=None, omega=None, seed: int = 0, n_samples: int = 4096,
                         target_rel_se: float = 0.0, round: int = 256, watch: int = 1, stream_base: int = 0,
                         stream=None):
@@ -565,6 +596,7 @@ def union_self_estimate(S: ShapeSet, idx=None, omega=None, seed: int = 0, n_samp
     return (*outs, nu)
 
 
+@_on_stream
 def cv_fit_weights(S: ShapeSet, seed: int, n_samples: int = 1024, stream_base: int = 0, ridge: float = 1e-6,
                    idx=None, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """[n_atoms] float32 device tensor: least-squares control-variate weights
@@ -584,6 +616,7 @@ def cv_fit_weights(S: ShapeSet, seed: int, n_samples: int = 1024, stream_base: i
     return omega
 
 
+@_on_stream
 def cv_features(S: ShapeSet, stream=None):
     """[n_atoms, 33] float32 device tensor of per-atom neighbour features."""
     out = torch.empty((S.n_atoms, MLP_IN), dtype=torch.float32, device=S.device)
@@ -591,6 +624,7 @@ def cv_features(S: ShapeSet, stream=None):
     return out
 
 
+@_on_stream
 def mlp_forward(params: torch.Tensor, x: torch.Tensor, rows=None, stream=None):
     n = x.shape[0] if rows is None else rows.numel()
     y = torch.empty(n, dtype=torch.float32, device=x.device)
@@ -598,6 +632,7 @@ def mlp_forward(params: torch.Tensor, x: torch.Tensor, rows=None, stream=None):
     return y
 
 
+@_on_stream
 def mlp_loss_grad(params: torch.Tensor, x: torch.Tensor, target: torch.Tensor, rows=None, stream=None, out=None):
     """(loss [1] float64, grad [6401] float32) device tensors."""
     n = x.shape[0] if rows is None else rows.numel()
@@ -608,6 +643,7 @@ def mlp_loss_grad(params: torch.Tensor, x: torch.Tensor, target: torch.Tensor, r
     return loss, grad
 
 
+@_on_stream
 def mlp_adam(params, m, v, grad, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
              eps: float = 1e-8, stream=None):
     _check(load_library().mlp_adam(_dptr(params), _dptr(m), _dptr(v), _dptr(grad), params.numel(), step, lr, beta1,

@@ -309,3 +309,24 @@ def test_sharded_screen_reproduces_the_full_screen():
                 got[k].append(a.reshape(q.n_mol, e - s, *a.shape[1:]))
         for k, v in got.items():
             np.testing.assert_array_equal(np.concatenate(v, axis=1).reshape(full[k].shape), full[k].cpu().numpy())
+
+def test_calls_on_a_side_stream_match_the_current_stream():
+    """The binding runs a call with stream=<torch stream> in that stream's
+    context (its temporaries are allocated and ordered there): a screen
+    queued on a side stream equals the one on the current stream."""
+    q = synth.principal_axes(synth.generate(75, [26]))
+    d = synth.principal_axes(synth.generate(76, synth.counts_uniform(76, 200, 18, 60)))
+    Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
+    ref_sq = shp.self_overlaps(Sq, seed=1, n_samples=1024)
+    ref_sd = shp.self_overlaps(Sd, seed=2, n_samples=1024)
+    ref = shp.tanimoto_screen(Sq, Sd, ref_sq, ref_sd, seed=3, n_fixed=512, with_overlaps=True)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    sq = shp.self_overlaps(Sq, seed=1, n_samples=1024, stream=side)
+    sd = shp.self_overlaps(Sd, seed=2, n_samples=1024, stream=side)
+    res = shp.tanimoto_screen(Sq, Sd, sq, sd, seed=3, n_fixed=512, with_overlaps=True, stream=side,
+                              pairs=(np.zeros(d.n_mol, np.int32), np.arange(d.n_mol, dtype=np.int32)))
+    side.synchronize()
+    for k in ("T", "seT", "O", "n_used"):
+        np.testing.assert_array_equal(res[k].cpu().numpy(), ref[k].cpu().numpy())
