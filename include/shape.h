@@ -249,8 +249,9 @@ typedef struct {
                                (pairs_q[k], pairs_db[k]) are screened and the
                                outputs are indexed by k; streams stay keyed by
                                (q, d), so each listed pair gets the numbers
-                               the full screen would give it. NULL = every
-                               pair of Q x D                                  */
+                               the full screen would give it. NULL (with
+                               n_pairs 0) = every pair of Q x D; an empty list
+                               is not expressible, skip the call instead     */
   const int32_t* pairs_db;
   int64_t n_pairs;
 } shp_screen;

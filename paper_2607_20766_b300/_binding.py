@@ -335,6 +335,8 @@ def tanimoto_screen(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db: tor
         if with_overlaps:
             out["O"] = torch.empty((npairs, 2), dtype=torch.float64, device=dev)
             out["seO"] = torch.empty((npairs, 2), dtype=torch.float64, device=dev)
+    if pq is not None and npairs == 0:
+        return out  # an empty list: nothing to screen (the C call reads NULL arrays as "no list")
     omega_q, omega_db = _weights(omega_q, Q), _weights(omega_db, D)
     self_se_q, self_se_db = _self_se(self_se_q, Q), _self_se(self_se_db, D)
     cfg = screen_config(seed, n_fixed, tau, round, min_n, cap, watch, flags, stream_base, variant, omega_q, omega_db,

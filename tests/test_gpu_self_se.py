@@ -203,3 +203,32 @@ def test_full_se_matches_the_spread_of_T_over_replicates():
     r_pair = var_T / np.mean(pair_only["seT"][:, 1].cpu().numpy().astype(np.float64) ** 2)
     assert 0.72 < r_full < 1.30, (r_full, r_pair)
     assert r_pair > 4.0, (r_full, r_pair)
+
+
+def test_edge_cases_of_the_new_entry_points(mols):
+    ms, S = mols
+    empty = MolSet(np.zeros((0, 3), np.float32), np.zeros(0, np.float32), np.zeros(1, np.int32),
+                   np.zeros(0, np.uint8))
+    E = shp.shape_set_load(empty)
+    out = shp.union_self_estimate(E, None, seed=1, n_samples=256)
+    assert all(t.numel() == 0 for t in out)
+    with pytest.raises(shp.ShapeError):  # the cap is not a multiple of the round
+        shp.union_self_estimate(S, None, seed=1, n_samples=1000, target_rel_se=0.01, round=256)
+    with pytest.raises(shp.ShapeError):  # watch is 0 or 1
+        shp.union_self_estimate(S, None, seed=1, n_samples=512, watch=2)
+    # an out-of-range molecule id gives NaN outputs for that item only
+    vol, vse, so, sse, nu = shp.union_self_estimate(S, [0, 99, 2], seed=1, n_samples=512)
+    so = so.cpu().numpy()
+    assert np.isfinite(so[[0, 2]]).all() and np.isnan(so[1])
+    # an empty pair list screens nothing; k = n_db selects every pair
+    sq, sq_se, _ = shp.self_overlaps(S, seed=2, n_samples=512, with_se=True)
+    none = torch.zeros(0, dtype=torch.int32, device="cuda")
+    res = shp.tanimoto_screen(S, S, sq, sq, seed=1, n_fixed=256, pairs=(none, none))
+    assert res["T"].shape == (0, 2)
+    T_fo = shp.fo_tanimoto_screen(S, S, sq[:, 0], sq[:, 0])
+    pq, pd = shp.fo_prefilter_select(S, S, T_fo, ms.n_mol)
+    np.testing.assert_array_equal(pd.cpu().numpy(), np.tile(np.arange(ms.n_mol), ms.n_mol))
+    # a molecule with itself: first-order Tanimoto 1
+    diag = T_fo.view(ms.n_mol, ms.n_mol).diagonal().cpu().numpy()
+    np.testing.assert_allclose(diag, 1.0, rtol=2e-5)
+    assert shp.fo_tanimoto_screen(S, E, sq[:, 0], torch.zeros(0, dtype=torch.float64)).numel() == 0
