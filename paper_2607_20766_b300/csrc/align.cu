@@ -11,8 +11,14 @@
 // c_jk = 1 (first order) or w_k prod_{l != j} (1 - g_l(r_k)) (union); the
 // product over l != j is formed from prefix and suffix products kept in
 // per-lane shared-memory columns, never by dividing by (1 - g_j) (g_j
-// reaches 1 when p > 1). dF/dt = sum_j dF/dc'_j, dF/dR = sum_j dF/dc'_j c_j^T,
-// then through R(q) and q = p / |p|.
+// reaches 1 when p > 1). The pose gradient is carried as the force
+// f = dF/dt = sum_j dF/dc'_j and the torque tau = sum_j (c'_j - t) x dF/dc'_j
+// (dF = tau . omega for the rotation c'_j - t -> (I + [omega]x)(c'_j - t)).
+// With u_k = sum_j (dF/dc'_j)_k, point k's share of the force, and
+// c'_j - t = (r_k - t) - (r_k - c'_j), tau = sum_k (r_k - t) x u_k: three
+// FMAs per point and atom. For q = (w, v) = p / |p| the left perturbation
+// q -> (1, omega / 2) q gives dF/dw = -2 tau . v, dF/dv = 2 (w tau + tau x v),
+// orthogonal to q, so dF/dp is that vector over |p|.
 #include <cmath>
 
 #include "device.cuh"
@@ -94,16 +100,22 @@ __device__ void stage_query(AlignTables& T, const SetView& Q, int32_t iq, int la
   __syncwarp();
 }
 
-// Objective and gradient at the staged pose. acc = {F, dF/dt (3), dF/dR
-// (9)}, reduced over the warp (every lane gets lane 0's totals). CRN
-// objectives are returned before their Z_Q / n factor; the closed-form first
-// order (Eq. fo) is exact:
+// Objective and gradient at the staged pose (translation t). acc = {F, force
+// f = dF/dt (3), torque tau (3)}, reduced over the warp (every lane gets lane
+// 0's totals). CRN objectives are returned before their Z_Q / n factor; the
+// closed-form first order (Eq. fo) is exact:
 //   F = sum_ij K_ij,  K_ij = p_i p_j (pi/s)^{3/2} exp(-a d^2), s = alpha_i +
 //   alpha_j, a = alpha_i alpha_j / s, dF/dc'_j = sum_i 2 a K_ij (c_i - c'_j).
+__device__ __forceinline__ void add_cross(float acc[7], float ax, float ay, float az, float bx, float by, float bz) {
+  acc[4] = fmaf(ay, bz, fmaf(-az, by, acc[4]));
+  acc[5] = fmaf(az, bx, fmaf(-ax, bz, acc[5]));
+  acc[6] = fmaf(ax, by, fmaf(-ay, bx, acc[6]));
+}
+
 __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restrict__ pts, int n, int objective,
-                           int lane, float acc[13]) {
+                           const float t[3], int lane, float acc[7]) {
 #pragma unroll
-  for (int i = 0; i < 13; ++i) acc[i] = 0.f;
+  for (int i = 0; i < 7; ++i) acc[i] = 0.f;
   if (objective == SHP_OBJ_FO_CLOSED) {
     const float kLog2e = 1.4426950408889634f, kPi = 3.14159265358979f;
     for (int j = lane; j < nb; j += 32) {
@@ -120,15 +132,13 @@ __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restr
         const float h = 2.f * a * K;
         gx = fmaf(h, dx, gx); gy = fmaf(h, dy, gy); gz = fmaf(h, dz, gz);
       }
-      const float4 b = T.body[j];
       acc[1] += gx; acc[2] += gy; acc[3] += gz;
-      acc[4] = fmaf(gx, b.x, acc[4]); acc[5] = fmaf(gx, b.y, acc[5]); acc[6] = fmaf(gx, b.z, acc[6]);
-      acc[7] = fmaf(gy, b.x, acc[7]); acc[8] = fmaf(gy, b.y, acc[8]); acc[9] = fmaf(gy, b.z, acc[9]);
-      acc[10] = fmaf(gz, b.x, acc[10]); acc[11] = fmaf(gz, b.y, acc[11]); acc[12] = fmaf(gz, b.z, acc[12]);
+      add_cross(acc, c.x - t[0], c.y - t[1], c.z - t[2], gx, gy, gz);
     }
   }
   for (int k = lane; k < n && objective != SHP_OBJ_FO_CLOSED; k += 32) {
     const float4 r = pts[k];
+    float ux = 0.f, uy = 0.f, uz = 0.f;  // u_k
     if (objective == SHP_OBJ_FO) {
       float m = 0.f;
       for (int j = 0; j < nb; ++j) {
@@ -137,12 +147,7 @@ __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restr
         const float g = ex2_approx(fmaf(c.w, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), T.lp[j]));
         m += g;
         const float h = -2.f * c.w * 0.6931471805599453f * g;  // 2 alpha g
-        const float4 b = T.body[j];
-        const float gx = h * dx, gy = h * dy, gz = h * dz;
-        acc[1] += gx; acc[2] += gy; acc[3] += gz;
-        acc[4] = fmaf(gx, b.x, acc[4]); acc[5] = fmaf(gx, b.y, acc[5]); acc[6] = fmaf(gx, b.z, acc[6]);
-        acc[7] = fmaf(gy, b.x, acc[7]); acc[8] = fmaf(gy, b.y, acc[8]); acc[9] = fmaf(gy, b.z, acc[9]);
-        acc[10] = fmaf(gz, b.x, acc[10]); acc[11] = fmaf(gz, b.y, acc[11]); acc[12] = fmaf(gz, b.z, acc[12]);
+        ux = fmaf(h, dx, ux); uy = fmaf(h, dy, uy); uz = fmaf(h, dz, uz);
       }
       acc[0] += m;
     } else {
@@ -164,37 +169,27 @@ __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restr
         const float g = ex2_approx(fmaf(c.w, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), T.lp[j]));
         const float h = -2.f * c.w * 0.6931471805599453f * g * T.pre[j][lane] * S;
         S = fmaf(-g, S, S);
-        const float4 b = T.body[j];
-        const float gx = h * dx, gy = h * dy, gz = h * dz;
-        acc[1] += gx; acc[2] += gy; acc[3] += gz;
-        acc[4] = fmaf(gx, b.x, acc[4]); acc[5] = fmaf(gx, b.y, acc[5]); acc[6] = fmaf(gx, b.z, acc[6]);
-        acc[7] = fmaf(gy, b.x, acc[7]); acc[8] = fmaf(gy, b.y, acc[8]); acc[9] = fmaf(gy, b.z, acc[9]);
-        acc[10] = fmaf(gz, b.x, acc[10]); acc[11] = fmaf(gz, b.y, acc[11]); acc[12] = fmaf(gz, b.z, acc[12]);
+        ux = fmaf(h, dx, ux); uy = fmaf(h, dy, uy); uz = fmaf(h, dz, uz);
       }
     }
+    acc[1] += ux; acc[2] += uy; acc[3] += uz;
+    add_cross(acc, r.x - t[0], r.y - t[1], r.z - t[2], ux, uy, uz);
   }
 #pragma unroll
-  for (int i = 0; i < 13; ++i) acc[i] = __shfl_sync(0xffffffffu, warp_sum(acc[i]), 0);
+  for (int i = 0; i < 7; ++i) acc[i] = __shfl_sync(0xffffffffu, warp_sum(acc[i]), 0);
 }
 
-// dF/d(raw pose) from dF/dt, dF/dR and the raw quaternion p (q = p/|p|).
-__device__ void pose_gradient(const float pose[7], const float acc[13], float scale, float grad[7]) {
+// dF/d(raw pose) from the force, the torque and the raw quaternion p
+// (q = (w, v) = p / |p|): dF/dp = (-2 tau . v, 2 (w tau + tau x v)) / |p|.
+__device__ void pose_gradient(const float pose[7], const float acc[7], float scale, float grad[7]) {
   const float nq = sqrtf(pose[0] * pose[0] + pose[1] * pose[1] + pose[2] * pose[2] + pose[3] * pose[3]);
   const float w = pose[0] / nq, x = pose[1] / nq, y = pose[2] / nq, z = pose[3] / nq;
-  const float* G = acc + 4;  // dF/dR, row-major
-  // dR/dw, dR/dx, dR/dy, dR/dz contracted with G
-  const float gw = 2.f * (-z * G[1] + y * G[2] + z * G[3] - x * G[5] - y * G[6] + x * G[7]);
-  const float gx = 2.f * (y * G[1] + z * G[2] + y * G[3] - 2.f * x * G[4] - w * G[5] + z * G[6] + w * G[7] -
-                          2.f * x * G[8]);
-  const float gy = 2.f * (-2.f * y * G[0] + x * G[1] + w * G[2] + x * G[3] + z * G[5] - w * G[6] + z * G[7] -
-                          2.f * y * G[8]);
-  const float gz = 2.f * (-2.f * z * G[0] - w * G[1] + x * G[2] + w * G[3] - 2.f * z * G[4] + y * G[5] +
-                          x * G[6] + y * G[7]);
-  const float dot = gw * w + gx * x + gy * y + gz * z;
-  grad[0] = scale * (gw - dot * w) / nq;
-  grad[1] = scale * (gx - dot * x) / nq;
-  grad[2] = scale * (gy - dot * y) / nq;
-  grad[3] = scale * (gz - dot * z) / nq;
+  const float tx = acc[4], ty = acc[5], tz = acc[6];
+  const float k = 2.f * scale / nq;
+  grad[0] = -k * (tx * x + ty * y + tz * z);
+  grad[1] = k * (w * tx + ty * z - tz * y);
+  grad[2] = k * (w * ty + tz * x - tx * z);
+  grad[3] = k * (w * tz + tx * y - ty * x);
   grad[4] = scale * acc[1];
   grad[5] = scale * acc[2];
   grad[6] = scale * acc[3];
@@ -269,8 +264,8 @@ __global__ void __launch_bounds__(kAlignThreads) pose_grad_kernel(const GradArgs
   stage_body(T, a.B, b0, nb, lane);
   if (a.objective == SHP_OBJ_FO_CLOSED) stage_query(T, a.Q, a.iq, lane);
   stage_posed(T, nb, pose, lane);
-  float acc[13];
-  value_grad(T, nb, a.Q.off[a.iq + 1] - a.Q.off[a.iq], a.pts, a.n_pts, a.objective, lane, acc);
+  float acc[7];
+  value_grad(T, nb, a.Q.off[a.iq + 1] - a.Q.off[a.iq], a.pts, a.n_pts, a.objective, pose + 4, lane, acc);
   if (lane == 0) {
     float g[7];
     pose_gradient(pose, acc, (float)a.scale, g);
@@ -372,8 +367,8 @@ __global__ void __launch_bounds__(kAlignThreads) align_adam_kernel(const AdamArg
     float b1t = 1.f, b2t = 1.f, value = 0.f;
     for (int step = 0; step < a.steps; ++step) {
       stage_posed(T, nb, pose, lane);
-      float acc[13];
-      value_grad(T, nb, na, a.pts, a.n_pts, a.objective, lane, acc);
+      float acc[7];
+      value_grad(T, nb, na, a.pts, a.n_pts, a.objective, pose + 4, lane, acc);
       float g[7];
       pose_gradient(pose, acc, a.scale, g);
       value = a.scale * acc[0];
