@@ -15,8 +15,10 @@
 // f = dF/dt = sum_j dF/dc'_j and the torque tau = sum_j (c'_j - t) x dF/dc'_j
 // (dF = tau . omega for the rotation c'_j - t -> (I + [omega]x)(c'_j - t)).
 // With u_k = sum_j (dF/dc'_j)_k, point k's share of the force, and
-// c'_j - t = (r_k - t) - (r_k - c'_j), tau = sum_k (r_k - t) x u_k: three
-// FMAs per point and atom. For q = (w, v) = p / |p| the left perturbation
+// c'_j - t = (r_k - t) - (r_k - c'_j), tau = sum_k (r_k - t) x u_k. With
+// h_jk the scalar factor of dF/dc'_j's k term and o the query centroid,
+// u_k = (r_k - o) sum_j h_jk - sum_j h_jk (c'_j - o): four FMAs per point and
+// atom, against the expanded exponent's b_j = 2 alpha_j log2(e) (c'_j - o). For q = (w, v) = p / |p| the left perturbation
 // q -> (1, omega / 2) q gives dF/dw = -2 tau . v, dF/dv = 2 (w tau + tau x v),
 // orthogonal to q, so dF/dp is that vector over |p|.
 #include <cmath>
@@ -33,10 +35,12 @@ constexpr int kAlignThreads = kAlignWarps * 32;
 struct __align__(16) AlignTables {
   float4 body[SHP_MAX_ATOMS];   // B's centres (own frame), alpha
   float4 posed[SHP_MAX_ATOMS];  // R c + t, -alpha log2(e)
+  float4 coef[SHP_MAX_ATOMS];   // expanded exponent about the origin o: b = 2 alpha log2(e) (R c + t - o), c0
   float lp[SHP_MAX_ATOMS];      // log2 p
   float4 qatom[SHP_MAX_ATOMS];  // the query's centres and alpha (closed-form objective)
   float qlp[SHP_MAX_ATOMS];
   float pre[SHP_MAX_ATOMS][32]; // per-lane prefix products prod_{l<j} (1 - g_l) of the current point
+  float4 origin;                // o: the query's atom centroid
 };
 constexpr size_t kAlignSmem = sizeof(AlignTables) * kAlignWarps;
 
@@ -74,8 +78,12 @@ __device__ void stage_body(AlignTables& T, const SetView& B, int32_t a0, int nb,
   __syncwarp();
 }
 
+// Posed centres c' = R c + t and, for the CRN objectives, the expanded
+// exponent log2 g(r) = a |r - o|^2 + b . (r - o) + c0 with a = -alpha log2(e)
+// (the posed table's w), b = -2 a (c' - o), c0 = a |c' - o|^2 + log2 p.
 __device__ void stage_posed(AlignTables& T, int nb, const float pose[7], int lane) {
   const float kLog2e = 1.4426950408889634f;
+  const float4 o = T.origin;
   float q[4] = {pose[0], pose[1], pose[2], pose[3]};
   const float inv = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
   for (int k = 0; k < 4; ++k) q[k] *= inv;
@@ -84,11 +92,21 @@ __device__ void stage_posed(AlignTables& T, int nb, const float pose[7], int lan
   __syncwarp();
   for (int i = lane; i < nb; i += 32) {
     const float4 c = T.body[i];
-    T.posed[i] = make_float4(fmaf(R[0], c.x, fmaf(R[1], c.y, fmaf(R[2], c.z, pose[4]))),
-                             fmaf(R[3], c.x, fmaf(R[4], c.y, fmaf(R[5], c.z, pose[5]))),
-                             fmaf(R[6], c.x, fmaf(R[7], c.y, fmaf(R[8], c.z, pose[6]))), -c.w * kLog2e);
+    const float a = -c.w * kLog2e;
+    const float px = fmaf(R[0], c.x, fmaf(R[1], c.y, fmaf(R[2], c.z, pose[4])));
+    const float py = fmaf(R[3], c.x, fmaf(R[4], c.y, fmaf(R[5], c.z, pose[5])));
+    const float pz = fmaf(R[6], c.x, fmaf(R[7], c.y, fmaf(R[8], c.z, pose[6])));
+    T.posed[i] = make_float4(px, py, pz, a);
+    const float dx = px - o.x, dy = py - o.y, dz = pz - o.z;
+    T.coef[i] = make_float4(-2.f * a * dx, -2.f * a * dy, -2.f * a * dz,
+                            fmaf(a, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), T.lp[i]));
   }
   __syncwarp();
+}
+
+// g_j at a point r' = r - o with rr = |r'|^2 (expanded form).
+__device__ __forceinline__ float g_expanded(const float4 k, float a, float rx, float ry, float rz, float rr) {
+  return ex2_approx(fmaf(a, rr, fmaf(k.x, rx, fmaf(k.y, ry, fmaf(k.z, rz, k.w)))));
 }
 
 __device__ void stage_query(AlignTables& T, const SetView& Q, int32_t iq, int lane) {
@@ -97,6 +115,21 @@ __device__ void stage_query(AlignTables& T, const SetView& Q, int32_t iq, int la
     T.qatom[i] = Q.atom[a0 + i];
     T.qlp[i] = Q.aux[a0 + i].y;
   }
+  __syncwarp();
+}
+
+// The frame origin of the expanded exponent: the query's atom centroid.
+__device__ void stage_origin(AlignTables& T, const SetView& Q, int32_t iq, int lane) {
+  const int32_t a0 = Q.off[iq], na = Q.off[iq + 1] - a0;
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  for (int i = lane; i < na; i += 32) {
+    const float4 a = Q.atom[a0 + i];
+    sx += a.x; sy += a.y; sz += a.z;
+  }
+  sx = warp_sum(sx); sy = warp_sum(sy); sz = warp_sum(sz);
+  const float inv = 1.f / (float)na;
+  __syncwarp();
+  if (lane == 0) T.origin = make_float4(sx * inv, sy * inv, sz * inv, 0.f);
   __syncwarp();
 }
 
@@ -136,26 +169,29 @@ __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restr
       add_cross(acc, c.x - t[0], c.y - t[1], c.z - t[2], gx, gy, gz);
     }
   }
+  const float4 o = T.origin;
   for (int k = lane; k < n && objective != SHP_OBJ_FO_CLOSED; k += 32) {
     const float4 r = pts[k];
-    float ux = 0.f, uy = 0.f, uz = 0.f;  // u_k
+    const float ox = r.x - o.x, oy = r.y - o.y, oz = r.z - o.z;
+    const float rr = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
+    // ha = sum_j a_j e_jk, v = sum_j b_j e_jk with e_jk = h_jk / (2 alpha_j ln 2)
+    // (a_j = -alpha_j log2(e)): u_k = -ln 2 (2 ha (r_k - o) + v)
+    float ha = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
     if (objective == SHP_OBJ_FO) {
       float m = 0.f;
       for (int j = 0; j < nb; ++j) {
-        const float4 c = T.posed[j];
-        const float dx = r.x - c.x, dy = r.y - c.y, dz = r.z - c.z;
-        const float g = ex2_approx(fmaf(c.w, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), T.lp[j]));
+        const float4 k = T.coef[j];
+        const float a = T.posed[j].w;
+        const float g = g_expanded(k, a, ox, oy, oz, rr);  // h = 2 alpha g
         m += g;
-        const float h = -2.f * c.w * 0.6931471805599453f * g;  // 2 alpha g
-        ux = fmaf(h, dx, ux); uy = fmaf(h, dy, uy); uz = fmaf(h, dz, uz);
+        ha = fmaf(a, g, ha);
+        vx = fmaf(k.x, g, vx); vy = fmaf(k.y, g, vy); vz = fmaf(k.z, g, vz);
       }
       acc[0] += m;
     } else {
       float q = 1.f;
       for (int j = 0; j < nb; ++j) {
-        const float4 c = T.posed[j];
-        const float dx = r.x - c.x, dy = r.y - c.y, dz = r.z - c.z;
-        const float g = ex2_approx(fmaf(c.w, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), T.lp[j]));
+        const float g = g_expanded(T.coef[j], T.posed[j].w, ox, oy, oz, rr);
         T.pre[j][lane] = q;
         q = fmaf(-g, q, q);
       }
@@ -164,14 +200,18 @@ __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restr
       for (int j = nb - 1; j >= 0; --j) {
         // g_j again, from the same expression as the forward pass (the same
         // float): storing it would halve the warps per SM
-        const float4 c = T.posed[j];
-        const float dx = r.x - c.x, dy = r.y - c.y, dz = r.z - c.z;
-        const float g = ex2_approx(fmaf(c.w, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), T.lp[j]));
-        const float h = -2.f * c.w * 0.6931471805599453f * g * T.pre[j][lane] * S;
+        const float4 k = T.coef[j];
+        const float a = T.posed[j].w;
+        const float g = g_expanded(k, a, ox, oy, oz, rr);
+        const float e = g * T.pre[j][lane] * S;  // h = 2 alpha e
         S = fmaf(-g, S, S);
-        ux = fmaf(h, dx, ux); uy = fmaf(h, dy, uy); uz = fmaf(h, dz, uz);
+        ha = fmaf(a, e, ha);
+        vx = fmaf(k.x, e, vx); vy = fmaf(k.y, e, vy); vz = fmaf(k.z, e, vz);
       }
     }
+    const float kLn2 = 0.6931471805599453f;
+    const float ux = -kLn2 * fmaf(2.f * ha, ox, vx), uy = -kLn2 * fmaf(2.f * ha, oy, vy),
+                uz = -kLn2 * fmaf(2.f * ha, oz, vz);
     acc[1] += ux; acc[2] += uy; acc[3] += uz;
     add_cross(acc, r.x - t[0], r.y - t[1], r.z - t[2], ux, uy, uz);
   }
@@ -263,6 +303,7 @@ __global__ void __launch_bounds__(kAlignThreads) pose_grad_kernel(const GradArgs
   for (int d = 0; d < 7; ++d) pose[d] = a.pose[7 * item + d];
   stage_body(T, a.B, b0, nb, lane);
   if (a.objective == SHP_OBJ_FO_CLOSED) stage_query(T, a.Q, a.iq, lane);
+  stage_origin(T, a.Q, a.iq, lane);
   stage_posed(T, nb, pose, lane);
   float acc[7];
   value_grad(T, nb, a.Q.off[a.iq + 1] - a.Q.off[a.iq], a.pts, a.n_pts, a.objective, pose + 4, lane, acc);
@@ -363,6 +404,7 @@ __global__ void __launch_bounds__(kAlignThreads) align_adam_kernel(const AdamArg
     for (int d = 0; d < 7; ++d) { m1[d] = 0.f; m2[d] = 0.f; }
     stage_body(T, a.B, b0, nb, lane);
     if (a.objective == SHP_OBJ_FO_CLOSED) stage_query(T, a.Q, a.iq, lane);
+    stage_origin(T, a.Q, a.iq, lane);
     const int na = a.Q.off[a.iq + 1] - a.Q.off[a.iq];
     float b1t = 1.f, b2t = 1.f, value = 0.f;
     for (int step = 0; step < a.steps; ++step) {
