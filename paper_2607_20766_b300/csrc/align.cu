@@ -32,14 +32,30 @@ namespace {
 constexpr int kAlignWarps = 4;
 constexpr int kAlignThreads = kAlignWarps * 32;
 
+// Expanded exponent of one posed atom about the origin o, every scalar twice
+// (two CRN points per packed FP32x2 instruction): b = 2 alpha log2(e)
+// (R c + t - o), c0 = -alpha log2(e) |R c + t - o|^2 + log2 p, a = -alpha log2(e).
+struct __align__(16) CoefA {
+  float4 bxy;  // bx, bx, by, by
+  float4 bzc;  // bz, bz, c0, c0
+  float2 a;    // a, a
+  float2 pad;
+};
+
 struct __align__(16) AlignTables {
   float4 body[SHP_MAX_ATOMS];   // B's centres (own frame), alpha
   float4 posed[SHP_MAX_ATOMS];  // R c + t, -alpha log2(e)
-  float4 coef[SHP_MAX_ATOMS];   // expanded exponent about the origin o: b = 2 alpha log2(e) (R c + t - o), c0
+  CoefA coef[SHP_MAX_ATOMS];
   float lp[SHP_MAX_ATOMS];      // log2 p
-  float4 qatom[SHP_MAX_ATOMS];  // the query's centres and alpha (closed-form objective)
-  float qlp[SHP_MAX_ATOMS];
-  float pre[SHP_MAX_ATOMS][32]; // per-lane prefix products prod_{l<j} (1 - g_l) of the current point
+  union {
+    struct {                    // closed-form objective: the query's centres, alpha and log2 p
+      float4 qatom[SHP_MAX_ATOMS];
+      float qlp[SHP_MAX_ATOMS];
+    };
+    // union objective: per-lane prefix products prod_{l<j} (1 - g_l) of the
+    // lane's two current points, for even j (odd j are rebuilt from them)
+    float2 pre[SHP_MAX_ATOMS / 2][32];
+  };
   float4 origin;                // o: the query's atom centroid
 };
 constexpr size_t kAlignSmem = sizeof(AlignTables) * kAlignWarps;
@@ -98,15 +114,34 @@ __device__ void stage_posed(AlignTables& T, int nb, const float pose[7], int lan
     const float pz = fmaf(R[6], c.x, fmaf(R[7], c.y, fmaf(R[8], c.z, pose[6])));
     T.posed[i] = make_float4(px, py, pz, a);
     const float dx = px - o.x, dy = py - o.y, dz = pz - o.z;
-    T.coef[i] = make_float4(-2.f * a * dx, -2.f * a * dy, -2.f * a * dz,
-                            fmaf(a, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), T.lp[i]));
+    const float bx = -2.f * a * dx, by = -2.f * a * dy, bz = -2.f * a * dz;
+    const float c0 = fmaf(a, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), T.lp[i]);
+    CoefA k;
+    k.bxy = make_float4(bx, bx, by, by);
+    k.bzc = make_float4(bz, bz, c0, c0);
+    k.a = make_float2(a, a);
+    k.pad = make_float2(0.f, 0.f);
+    T.coef[i] = k;
   }
   __syncwarp();
 }
 
-// g_j at a point r' = r - o with rr = |r'|^2 (expanded form).
-__device__ __forceinline__ float g_expanded(const float4 k, float a, float rx, float ry, float rz, float rr) {
-  return ex2_approx(fmaf(a, rr, fmaf(k.x, rx, fmaf(k.y, ry, fmaf(k.z, rz, k.w)))));
+// g_j at two points r' = r - o (one per half) with rr = |r'|^2: the expanded
+// exponent in four packed FMAs, two SFU exp2.
+__device__ __forceinline__ float2 g_expanded2(const CoefA& k, float2 rx, float2 ry, float2 rz, float2 rr) {
+  float2 e = __ffma2_rn(make_float2(k.bzc.x, k.bzc.y), rz, make_float2(k.bzc.z, k.bzc.w));
+  e = __ffma2_rn(make_float2(k.bxy.z, k.bxy.w), ry, e);
+  e = __ffma2_rn(make_float2(k.bxy.x, k.bxy.y), rx, e);
+  e = __ffma2_rn(k.a, rr, e);
+  return make_float2(ex2_approx(e.x), ex2_approx(e.y));
+}
+
+// Adjoint sums of one atom j for two points: ha += a_j e, v += b_j e.
+__device__ __forceinline__ void adj_add(const CoefA& k, float2 e, float2& ha, float2& vx, float2& vy, float2& vz) {
+  ha = __ffma2_rn(k.a, e, ha);
+  vx = __ffma2_rn(make_float2(k.bxy.x, k.bxy.y), e, vx);
+  vy = __ffma2_rn(make_float2(k.bxy.z, k.bxy.w), e, vy);
+  vz = __ffma2_rn(make_float2(k.bzc.x, k.bzc.y), e, vz);
 }
 
 __device__ void stage_query(AlignTables& T, const SetView& Q, int32_t iq, int lane) {
@@ -169,51 +204,89 @@ __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restr
       add_cross(acc, c.x - t[0], c.y - t[1], c.z - t[2], gx, gy, gz);
     }
   }
+  // CRN objectives: each lane takes points k and k + 32 of every 64 (the
+  // second one, past n, with weight 0), both in the halves of packed FP32x2
+  // values. ha = sum_j a_j e_jk, v = sum_j b_j e_jk with e_jk = h_jk /
+  // (2 alpha_j ln 2): u_k = -ln 2 (2 ha (r_k - o) + v).
   const float4 o = T.origin;
-  for (int k = lane; k < n && objective != SHP_OBJ_FO_CLOSED; k += 32) {
-    const float4 r = pts[k];
-    const float ox = r.x - o.x, oy = r.y - o.y, oz = r.z - o.z;
-    const float rr = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
-    // ha = sum_j a_j e_jk, v = sum_j b_j e_jk with e_jk = h_jk / (2 alpha_j ln 2)
-    // (a_j = -alpha_j log2(e)): u_k = -ln 2 (2 ha (r_k - o) + v)
-    float ha = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
+  for (int k0 = lane; k0 < n && objective != SHP_OBJ_FO_CLOSED; k0 += 64) {
+    const bool has1 = k0 + 32 < n;
+    const float4 r0 = pts[k0];
+    const float4 r1 = has1 ? pts[k0 + 32] : r0;
+    const float2 ox = make_float2(r0.x - o.x, r1.x - o.x), oy = make_float2(r0.y - o.y, r1.y - o.y);
+    const float2 oz = make_float2(r0.z - o.z, r1.z - o.z);
+    const float2 rr = make_float2(fmaf(ox.x, ox.x, fmaf(oy.x, oy.x, oz.x * oz.x)),
+                                  fmaf(ox.y, ox.y, fmaf(oy.y, oy.y, oz.y * oz.y)));
+    const float2 w = make_float2(r0.w, has1 ? r1.w : 0.f);
+    float2 ha = make_float2(0.f, 0.f), vx = ha, vy = ha, vz = ha;
+    float2 F;
     if (objective == SHP_OBJ_FO) {
-      float m = 0.f;
+      float2 m = make_float2(0.f, 0.f);
       for (int j = 0; j < nb; ++j) {
-        const float4 k = T.coef[j];
-        const float a = T.posed[j].w;
-        const float g = g_expanded(k, a, ox, oy, oz, rr);  // h = 2 alpha g
-        m += g;
-        ha = fmaf(a, g, ha);
-        vx = fmaf(k.x, g, vx); vy = fmaf(k.y, g, vy); vz = fmaf(k.z, g, vz);
+        const CoefA& k = T.coef[j];
+        const float2 g = g_expanded2(k, ox, oy, oz, rr);  // h = 2 alpha g
+        m = __fadd2_rn(m, g);
+        adj_add(k, g, ha, vx, vy, vz);
       }
-      acc[0] += m;
+      F = m;
     } else {
-      float q = 1.f;
-      for (int j = 0; j < nb; ++j) {
-        const float g = g_expanded(T.coef[j], T.posed[j].w, ox, oy, oz, rr);
-        T.pre[j][lane] = q;
-        q = fmaf(-g, q, q);
+      float2 q = make_float2(1.f, 1.f);
+      int j = 0;
+      for (; j + 1 < nb; j += 2) {
+        const float2 g0 = g_expanded2(T.coef[j], ox, oy, oz, rr);
+        const float2 g1 = g_expanded2(T.coef[j + 1], ox, oy, oz, rr);
+        T.pre[j >> 1][lane] = q;
+        q = __ffma2_rn(make_float2(-g0.x, -g0.y), q, q);
+        q = __ffma2_rn(make_float2(-g1.x, -g1.y), q, q);
       }
-      acc[0] = fmaf(r.w, 1.f - q, acc[0]);
-      float S = r.w;  // w_k times the suffix product
-      for (int j = nb - 1; j >= 0; --j) {
-        // g_j again, from the same expression as the forward pass (the same
-        // float): storing it would halve the warps per SM
-        const float4 k = T.coef[j];
-        const float a = T.posed[j].w;
-        const float g = g_expanded(k, a, ox, oy, oz, rr);
-        const float e = g * T.pre[j][lane] * S;  // h = 2 alpha e
-        S = fmaf(-g, S, S);
-        ha = fmaf(a, e, ha);
-        vx = fmaf(k.x, e, vx); vy = fmaf(k.y, e, vy); vz = fmaf(k.z, e, vz);
+      if (j < nb) {
+        const float2 g0 = g_expanded2(T.coef[j], ox, oy, oz, rr);
+        T.pre[j >> 1][lane] = q;
+        q = __ffma2_rn(make_float2(-g0.x, -g0.y), q, q);
+      }
+      F = make_float2(w.x * (1.f - q.x), w.y * (1.f - q.y));
+      float2 S = w;  // w_k times the suffix product
+      // g_j again, from the same expression as the forward pass (the same
+      // float); the odd prefix from the even one as in the forward pass
+      j = nb - 1;
+      if (!(j & 1)) {
+        const CoefA& k = T.coef[j];
+        const float2 g = g_expanded2(k, ox, oy, oz, rr);
+        const float2 pr = T.pre[j >> 1][lane];
+        const float2 e = __fmul2_rn(__fmul2_rn(g, pr), S);  // h = 2 alpha e
+        S = __ffma2_rn(make_float2(-g.x, -g.y), S, S);
+        adj_add(k, e, ha, vx, vy, vz);
+        --j;
+      }
+      for (; j >= 1; j -= 2) {
+        const CoefA& k1 = T.coef[j];
+        const CoefA& k0 = T.coef[j - 1];
+        const float2 g1 = g_expanded2(k1, ox, oy, oz, rr);
+        const float2 g0 = g_expanded2(k0, ox, oy, oz, rr);
+        const float2 p0 = T.pre[j >> 1][lane];
+        const float2 p1 = __ffma2_rn(make_float2(-g0.x, -g0.y), p0, p0);
+        const float2 e1 = __fmul2_rn(__fmul2_rn(g1, p1), S);
+        S = __ffma2_rn(make_float2(-g1.x, -g1.y), S, S);
+        adj_add(k1, e1, ha, vx, vy, vz);
+        const float2 e0 = __fmul2_rn(__fmul2_rn(g0, p0), S);
+        S = __ffma2_rn(make_float2(-g0.x, -g0.y), S, S);
+        adj_add(k0, e0, ha, vx, vy, vz);
       }
     }
     const float kLn2 = 0.6931471805599453f;
-    const float ux = -kLn2 * fmaf(2.f * ha, ox, vx), uy = -kLn2 * fmaf(2.f * ha, oy, vy),
-                uz = -kLn2 * fmaf(2.f * ha, oz, vz);
-    acc[1] += ux; acc[2] += uy; acc[3] += uz;
-    add_cross(acc, r.x - t[0], r.y - t[1], r.z - t[2], ux, uy, uz);
+    const float4 rs[2] = {r0, r1};
+    const float2 hs[4] = {ha, vx, vy, vz};
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !has1) break;
+      const float oxh = h ? ox.y : ox.x, oyh = h ? oy.y : oy.x, ozh = h ? oz.y : oz.x;
+      const float hah = h ? hs[0].y : hs[0].x;
+      const float ux = -kLn2 * fmaf(2.f * hah, oxh, h ? hs[1].y : hs[1].x);
+      const float uy = -kLn2 * fmaf(2.f * hah, oyh, h ? hs[2].y : hs[2].x);
+      const float uz = -kLn2 * fmaf(2.f * hah, ozh, h ? hs[3].y : hs[3].x);
+      acc[0] += h ? F.y : F.x;
+      acc[1] += ux; acc[2] += uy; acc[3] += uz;
+      add_cross(acc, rs[h].x - t[0], rs[h].y - t[1], rs[h].z - t[2], ux, uy, uz);
+    }
   }
 #pragma unroll
   for (int i = 0; i < 7; ++i) acc[i] = __shfl_sync(0xffffffffu, warp_sum(acc[i]), 0);
