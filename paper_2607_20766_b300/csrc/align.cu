@@ -222,6 +222,7 @@ __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restr
     float2 F;
     if (objective == SHP_OBJ_FO) {
       float2 m = make_float2(0.f, 0.f);
+#pragma unroll 4
       for (int j = 0; j < nb; ++j) {
         const CoefA& k = T.coef[j];
         const float2 g = g_expanded2(k, ox, oy, oz, rr);  // h = 2 alpha g
@@ -232,6 +233,7 @@ __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restr
     } else {
       float2 q = make_float2(1.f, 1.f);
       int j = 0;
+#pragma unroll 2
       for (; j + 1 < nb; j += 2) {
         const float2 g0 = g_expanded2(T.coef[j], ox, oy, oz, rr);
         const float2 g1 = g_expanded2(T.coef[j + 1], ox, oy, oz, rr);
@@ -258,6 +260,7 @@ __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restr
         adj_add(k, e, ha, vx, vy, vz);
         --j;
       }
+#pragma unroll 2
       for (; j >= 1; j -= 2) {
         const CoefA& k1 = T.coef[j];
         const CoefA& k0 = T.coef[j - 1];
