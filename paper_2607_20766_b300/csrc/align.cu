@@ -44,7 +44,7 @@ struct __align__(16) CoefA {
 
 struct __align__(16) AlignTables {
   float4 body[SHP_MAX_ATOMS];   // B's centres (own frame), alpha
-  float4 posed[SHP_MAX_ATOMS];  // R c + t, -alpha log2(e)
+  float4 posed[SHP_MAX_ATOMS];  // R c (the posed centre less t), -alpha log2(e)
   CoefA coef[SHP_MAX_ATOMS];
   float lp[SHP_MAX_ATOMS];      // log2 p
   union {
@@ -109,11 +109,11 @@ __device__ void stage_posed(AlignTables& T, int nb, const float pose[7], int lan
   for (int i = lane; i < nb; i += 32) {
     const float4 c = T.body[i];
     const float a = -c.w * kLog2e;
-    const float px = fmaf(R[0], c.x, fmaf(R[1], c.y, fmaf(R[2], c.z, pose[4])));
-    const float py = fmaf(R[3], c.x, fmaf(R[4], c.y, fmaf(R[5], c.z, pose[5])));
-    const float pz = fmaf(R[6], c.x, fmaf(R[7], c.y, fmaf(R[8], c.z, pose[6])));
-    T.posed[i] = make_float4(px, py, pz, a);
-    const float dx = px - o.x, dy = py - o.y, dz = pz - o.z;
+    const float yx = fmaf(R[0], c.x, fmaf(R[1], c.y, R[2] * c.z));
+    const float yy = fmaf(R[3], c.x, fmaf(R[4], c.y, R[5] * c.z));
+    const float yz = fmaf(R[6], c.x, fmaf(R[7], c.y, R[8] * c.z));
+    T.posed[i] = make_float4(yx, yy, yz, a);
+    const float dx = yx + pose[4] - o.x, dy = yy + pose[5] - o.y, dz = yz + pose[6] - o.z;
     const float bx = -2.f * a * dx, by = -2.f * a * dy, bz = -2.f * a * dz;
     const float c0 = fmaf(a, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), T.lp[i]);
     CoefA k;
@@ -173,7 +173,10 @@ __device__ void stage_origin(AlignTables& T, const SetView& Q, int32_t iq, int l
 // 0's totals). CRN objectives are returned before their Z_Q / n factor; the
 // closed-form first order (Eq. fo) is exact:
 //   F = sum_ij K_ij,  K_ij = p_i p_j (pi/s)^{3/2} exp(-a d^2), s = alpha_i +
-//   alpha_j, a = alpha_i alpha_j / s, dF/dc'_j = sum_i 2 a K_ij (c_i - c'_j).
+//   alpha_j, a = alpha_i alpha_j / s, dF/dc'_j = sum_i 2 a K_ij (c_i - c'_j);
+// lanes over the query's atoms i: with x_i = c_i - t, y_j = c'_j - t and
+// h_ij = a K_ij, f = 2 sum_i (x_i H_i - W_i) and tau = 2 sum_i W_i x x_i for
+// H_i = sum_j h_ij, W_i = sum_j h_ij y_j.
 __device__ __forceinline__ void add_cross(float acc[7], float ax, float ay, float az, float bx, float by, float bz) {
   acc[4] = fmaf(ay, bz, fmaf(-az, by, acc[4]));
   acc[5] = fmaf(az, bx, fmaf(-ax, bz, acc[5]));
@@ -186,22 +189,27 @@ __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restr
   for (int i = 0; i < 7; ++i) acc[i] = 0.f;
   if (objective == SHP_OBJ_FO_CLOSED) {
     const float kLog2e = 1.4426950408889634f, kPi = 3.14159265358979f;
-    for (int j = lane; j < nb; j += 32) {
-      const float4 c = T.posed[j];
-      const float aj = T.body[j].w;
-      float gx = 0.f, gy = 0.f, gz = 0.f;
-      for (int i = 0; i < na; ++i) {
-        const float4 qa = T.qatom[i];
-        const float dx = qa.x - c.x, dy = qa.y - c.y, dz = qa.z - c.z;
-        const float s = qa.w + aj, inv = 1.f / s, a = qa.w * aj * inv, t = kPi * inv;
-        const float K = t * sqrtf(t) * ex2_approx(fmaf(-a * kLog2e, fmaf(dx, dx, fmaf(dy, dy, dz * dz)),
-                                                        T.qlp[i] + T.lp[j]));
-        acc[0] += K;
-        const float h = 2.f * a * K;
-        gx = fmaf(h, dx, gx); gy = fmaf(h, dy, gy); gz = fmaf(h, dz, gz);
+    for (int i = lane; i < na; i += 32) {
+      const float4 qa = T.qatom[i];
+      const float lpi = T.qlp[i], al = qa.w;
+      const float xi = qa.x - t[0], yi = qa.y - t[1], zi = qa.z - t[2];
+      float F = 0.f, H = 0.f, Wx = 0.f, Wy = 0.f, Wz = 0.f;
+#pragma unroll 2
+      for (int j = 0; j < nb; ++j) {
+        const float4 y = T.posed[j];
+        const float aj = T.body[j].w;
+        const float dx = xi - y.x, dy = yi - y.y, dz = zi - y.z;
+        const float r = __fdividef(1.f, al + aj), a = al * aj * r, tt = kPi * r;
+        const float K = tt * tt * rsqrtf(tt) *
+                        ex2_approx(fmaf(-a * kLog2e, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), lpi + T.lp[j]));
+        F += K;
+        const float h = a * K;
+        H += h;
+        Wx = fmaf(h, y.x, Wx); Wy = fmaf(h, y.y, Wy); Wz = fmaf(h, y.z, Wz);
       }
-      acc[1] += gx; acc[2] += gy; acc[3] += gz;
-      add_cross(acc, c.x - t[0], c.y - t[1], c.z - t[2], gx, gy, gz);
+      acc[0] += F;
+      acc[1] += 2.f * fmaf(xi, H, -Wx); acc[2] += 2.f * fmaf(yi, H, -Wy); acc[3] += 2.f * fmaf(zi, H, -Wz);
+      add_cross(acc, 2.f * Wx, 2.f * Wy, 2.f * Wz, xi, yi, zi);
     }
   }
   // CRN objectives: each lane takes points k and k + 32 of every 64 (the
