@@ -188,7 +188,9 @@ int fo_overlap(shp_set A, const int32_t* ia, shp_set B, const int32_t* ib, int64
  * with S the same closed form of a molecule with itself (fo_overlap of the
  * molecule with itself). The cheap first stage of the paper's hybrid
  * pipeline, used to drop clear misses before the union screen. Terms and the
- * per-pair sum in FP32 (SFU reciprocal, reciprocal square root and exp2).
+ * per-pair sum in FP32: each term as w_i w_j r^3 2^(-r^2 |c_i - c_j|^2) with
+ * r = (1/(a_i log2 e) + 1/(a_j log2 e))^(-1/2) and per-atom weights w (SFU
+ * rsqrt and exp2 per atom pair, SFU log2 and reciprocal per atom).
  *   fo_self_q [n_q], fo_self_db [n_db] double device; T_fo [n_q * n_db]
  *   float device. At most 65535 queries per call (SHP_ERANGE).
  */
