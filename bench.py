@@ -434,7 +434,8 @@ def main():
     if os.path.exists(peaks_path):
         with open(peaks_path) as f:
             sm_max = float(json.load(f).get("sm_max_mhz", sm_max))
-    peak = sms * 128 * sm_max * 1e6 / FP32_OPS_PER_EVAL / 1e9
+    lane_rate = sms * 128 * sm_max * 1e6  # FP32 lane operations per second
+    peak = lane_rate / FP32_OPS_PER_EVAL / 1e9
     ceiling = loop_ceiling(shp, torch, Sq, Sd, d, tuned, peak, achieved)
 
     # the whole database's per-query top-k union Tanimotos, merged on rank 0
@@ -456,14 +457,14 @@ def main():
 
     cvres, net = None, None
     if args.cv_train > 0:
-        net, cvres = cv_section(shp, torch, args.cv_train, args.cv_held, rank)
+        net, cvres = cv_section(shp, torch, args.cv_train, args.cv_held, rank, lane_rate)
     adaptive = None
     if args.adaptive_db > 0:
-        adaptive = adaptive_section(shp, torch, args.adaptive_db, rank, net=net, fit_samples=args.fit_samples,
-                                    self_rel_se=args.self_rel_se)
+        adaptive = adaptive_section(shp, torch, args.adaptive_db, rank, lane_rate, net=net,
+                                    fit_samples=args.fit_samples, self_rel_se=args.self_rel_se)
     aligned = None
     if args.align_db > 0:
-        aligned = align_section(shp, torch, args.align_db, rank)
+        aligned = align_section(shp, torch, args.align_db, rank, lane_rate)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -519,6 +520,15 @@ def main():
     return 0
 
 
+def alu_roofline(lane_rate: float, units: float, seconds: float, ops: int, unit: str, kernel: str, basis: str):
+    """Roofline of an ALU-bound kernel: `units` of work in `seconds` of its
+    launches, against the FP32 lanes' rate over `ops` FP32 operations per unit."""
+    achieved = units / seconds / 1e9
+    peak = lane_rate / ops / 1e9
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "basis": basis}
+
+
 def loop_ceiling(shp, torch, Sq, Sd, d, variant: int, peak: float, achieved: float, batches: int = 256):
     """What the screen's per-sample work reaches on this chip without the
     per-pair work around it: the tuned variant's evaluation loop and
@@ -545,8 +555,8 @@ def loop_ceiling(shp, torch, Sq, Sd, d, variant: int, peak: float, achieved: flo
     return out
 
 
-def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: int = 65536, net=None,
-                     fit_samples: int = 4096, self_rel_se: float = 3.5e-3):
+def adaptive_section(shp, torch, n_db: int, rank: int, lane_rate: float, tau: float = 0.005, cap: int = 65536,
+                     net=None, fit_samples: int = 4096, self_rel_se: float = 3.5e-3):
     """Confidence-bounded screen: 16 queries (20-48 atoms) x n_db molecules
     (18-60, heavy-tailed toward 40), rounds of 256 samples per direction
     until the full delta-method SE(T_union) <= tau or cap. The union
@@ -686,7 +696,12 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
         se_cv = rcv["seT"].cpu().numpy()[:, 1]
         kept.update(T=rcv["T"][:, 1].clone())
         pps = npairs / (t_cv + t_w + t_self)
+        evals_cv = int(2 * (nu_cv * pair_atoms).sum())
         return {
+            "roofline": alu_roofline(lane_rate, evals_cv, t_cv, FP32_OPS_PER_EVAL + 1, "Geval/s",
+                                     "cross_kernel<adaptive, control variate>",
+                                     "7 FP32 ops per sample-atom evaluation (the control variate's FMA "
+                                     "on top of the 6)"),
             "optional_stopping": stopping_effect(T_cv, se_cv.reshape(q.n_mol, d.n_mol)[:, sub]),
             "pairs_per_s": pps, "seconds": t_cv, "weights_seconds": t_w,
             "mean_samples_per_direction": float(nu_cv.mean()), "frac_at_cap": float((nu_cv >= cap).mean()),
@@ -743,6 +758,14 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
                 f"recall_at_{k_top}": {"mean": float(np.mean(recall)), "min": float(np.min(recall))}}
 
     prefilter = [prefilter_arm(0.25), prefilter_arm(0.1), prefilter_arm(0.05)]
+    # the first-order kernel alone (every query x database pair)
+    fo_q, fo_d = selfq[:, 0].contiguous(), selfd[:, 0].contiguous()
+    _, t_fo_kernel = timed(lambda: shp.fo_tanimoto_screen(Sq, Sd, fo_q, fo_d))
+    atom_pairs = float(nq_c.sum()) * float(nd_c.sum())
+    prefilter_roofline = alu_roofline(lane_rate, atom_pairs, t_fo_kernel, 11, "G atom pairs/s", "fo_tanimoto_kernel",
+                                      "11 FP32 ops per atom pair of the closed form w_i w_j r^3 2^(-r^2 d^2): "
+                                      "difference 3, d^2 3, beta sum 1, r^2 1, exponent 1, r^3 1, sum 1 "
+                                      "(plus SFU rsqrt and exp2)")
     pps = npairs / (t_ad + t_self)
     return {
         "workload": f"adaptive screen: 16 queries (20-48 atoms) x {n_db} molecules (18-60, heavy-tailed toward 40), "
@@ -755,6 +778,8 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
                           "se_t_term_p99": float(np.quantile(self_term, 0.99))},
         "pairs": npairs, "pairs_per_s": pps, "evals_per_s": (evals + self_evals) / (t_ad + t_self),
         "seconds": t_ad,
+        "roofline": alu_roofline(lane_rate, evals, t_ad, FP32_OPS_PER_EVAL, "Geval/s", "cross_kernel<adaptive>",
+                                 "6 FP32 ops per sample-atom evaluation"),
         "mean_samples_per_direction": float(nu.mean()), "median_samples_per_direction": float(np.median(nu)),
         "frac_at_cap": float((nu >= cap).mean()), "frac_se_met": float((se_ad <= tau * (1 + 1e-6)).mean()),
         "sample_reduction_vs_fixed": 1.0 - float(nu.mean()) / cap,
@@ -769,10 +794,11 @@ def adaptive_section(shp, torch, n_db: int, rank: int, tau: float = 0.005, cap: 
         "with_control_variate": with_cv,
         "with_fitted_control_variate": with_fit,
         "first_order_prefilter": prefilter,
+        "first_order_kernel": {"seconds": t_fo_kernel, "pairs": npairs, "roofline": prefilter_roofline},
     }
 
 
-def cv_section(shp, torch, n_train: int, n_held: int, rank: int, target: float = 1e-3):
+def cv_section(shp, torch, n_train: int, n_held: int, rank: int, lane_rate: float, target: float = 1e-3):
     """Learned control variate: train the crowding network on union
     attributions of n_train molecules (18-60 atoms), then estimate the union
     volume of n_held held-out molecules to relative SE <= target with and
@@ -805,20 +831,27 @@ def cv_section(shp, torch, n_train: int, n_held: int, rank: int, target: float =
     (v_pl, s_pl, n_pl), t_pl = timed(lambda: shp.union_volume_cv(Sh, None, None, seed=5, n_samples=cap,
                                                                  target_rel_se=target))
     n_cv, n_pl = n_cv.cpu().numpy().astype(np.float64), n_pl.cpu().numpy().astype(np.float64)
+    atoms = held.counts.astype(np.float64)
+    roof_cv = alu_roofline(lane_rate, float((n_cv * atoms).sum()), t_cv, FP32_OPS_PER_EVAL + 1, "Geval/s",
+                           "cv_volume_kernel (control variate)", "7 FP32 ops per sample-atom evaluation")
+    roof_pl = alu_roofline(lane_rate, float((n_pl * atoms).sum()), t_pl, FP32_OPS_PER_EVAL, "Geval/s",
+                           "cv_volume_kernel (plain)", "6 FP32 ops per sample-atom evaluation")
     z = ((v_cv - v_pl) / torch.sqrt(s_cv ** 2 + s_pl ** 2)).cpu().numpy()
     return net, {
         "workload": f"learned control variate: train on {n_train} molecules (18-60 atoms, union attributions, 256 "
                     f"samples/atom), union volume of {n_held} held-out molecules to relative SE <= {target}",
         "train_seconds": t_train, "targets_seconds": t_data, "predict_seconds": t_pred,
         "loss_first_last": [hist[0], hist[-1]],
-        "plain": {"mean_samples": float(n_pl.mean()), "seconds": t_pl, "molecules_per_s": n_held / t_pl},
-        "control_variate": {"mean_samples": float(n_cv.mean()), "seconds": t_cv, "molecules_per_s": n_held / t_cv},
+        "plain": {"mean_samples": float(n_pl.mean()), "seconds": t_pl, "molecules_per_s": n_held / t_pl,
+                  "roofline": roof_pl},
+        "control_variate": {"mean_samples": float(n_cv.mean()), "seconds": t_cv, "molecules_per_s": n_held / t_cv,
+                            "roofline": roof_cv},
         "sample_ratio": float(n_cv.mean() / n_pl.mean()), "speedup": t_pl / t_cv,
         "agreement_mean_z": float(z.mean()), "frac_at_cap": [float((n_pl >= cap).mean()), float((n_cv >= cap).mean())],
     }
 
 
-def align_section(shp, torch, n_db: int, rank: int, n_copies: int = 512):
+def align_section(shp, torch, n_db: int, rank: int, lane_rate: float, n_copies: int = 512):
     """Multi-start rigid alignment: 1 query (30 atoms) x n_db molecules
     (18-60 atoms), 8 starts, 100 Adam steps with 1024 CRN points on the union
     objective, and the paper's hybrid pipeline (align on the closed-form
@@ -881,6 +914,23 @@ def align_section(shp, torch, n_db: int, rank: int, n_copies: int = 512):
         res, t = timed(lambda: shp.align_rigid(Sq, 0, Sd, ib, sq, sd, seed=1, starts=8, steps=100, n_score=4096,
                                                **kw))
         T1 = res["T"].cpu().numpy()
+        # the optimiser kernel alone: the same call with a 2-sample final scoring
+        _, t_adam = timed(lambda: shp.align_rigid(Sq, 0, Sd, ib, sq, sd, seed=1, starts=8, steps=100, n_score=2,
+                                                  **kw))
+        nb_sum = float(d.counts.astype(np.float64).sum())
+        if kw["objective"] == shp.OBJ_UNION:
+            roof = alu_roofline(lane_rate, 8 * 100 * kw["n_crn"] * nb_sum, t_adam, 12,
+                                "G point-atom-steps/s", "align_adam_kernel (union CRN objective)",
+                                "12 FP32 ops per CRN point, atom and step: exponent 4 and prefix product 1 "
+                                "forward; adjoint weight 2, suffix product 1, force sums 4 (the kernel "
+                                "recomputes the exponent in the adjoint pass, 4 more)")
+        else:
+            roof = alu_roofline(lane_rate, 8 * 100 * float(q.counts[0]) * nb_sum, t_adam, 14,
+                                "G atom-pair-steps/s", "align_adam_kernel (closed-form first order)",
+                                "14 FP32 ops per query atom, database atom and step: difference 3, d^2 3, "
+                                "exponent 1, prefactor 1, sum 1, adjoint weight 1, force sums 4 (the kernel "
+                                "recomputes the pose-independent pair constants each step)")
+        roof["optimiser_seconds"] = t_adam
         rec = shp.align_rigid(Sq, 0, Sc, ic, sq, sc, seed=1, starts=8, steps=100, n_score=4096, **kw)
         pose = rec["pose"].cpu().numpy().astype(np.float64)
         rm = []
@@ -894,7 +944,7 @@ def align_section(shp, torch, n_db: int, rank: int, n_copies: int = 512):
                                        n_samples=1 << 20, pose=rec["pose"])
         O_hi = e_hi[:, 1].cpu().numpy()
         T_hi = O_hi / (S_hi - O_hi)  # SE ~0.001 near T = 1
-        out[name] = {"seconds": t, "pairs_per_s": n_db / t, "mean_T_aligned": float(T1.mean()),
+        out[name] = {"seconds": t, "pairs_per_s": n_db / t, "roofline": roof, "mean_T_aligned": float(T1.mean()),
                      "frac_improved": float((T1 >= T0 - 0.005).mean()),
                      "known_copies": {"rmsd_median": float(np.median(rm)), "rmsd_max": float(rm.max()),
                                       "T_min": float(T_hi.min()), "T_median": float(np.median(T_hi)),
