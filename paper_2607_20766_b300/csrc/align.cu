@@ -42,15 +42,27 @@ struct __align__(16) CoefA {
   float2 pad;
 };
 
+// Two posed atoms j, j + 1 of B for the closed-form objective: minus their
+// centres less t (y = R c), their beta' and log2 w' (fo_atom_consts); an odd
+// count is padded with an atom of weight 0.
+struct __align__(16) FoPairB {
+  float4 nxy;  // -y_j.x, -y_j+1.x, -y_j.y, -y_j+1.y
+  float4 nzb;  // -y_j.z, -y_j+1.z, beta'_j, beta'_j+1
+  float2 lw;   // log2 w'_j, log2 w'_j+1
+  float2 pad;
+};
+
 struct __align__(16) AlignTables {
   float4 body[SHP_MAX_ATOMS];   // B's centres (own frame), alpha
   float4 posed[SHP_MAX_ATOMS];  // R c (the posed centre less t), -alpha log2(e)
   CoefA coef[SHP_MAX_ATOMS];
   float lp[SHP_MAX_ATOMS];      // log2 p
   union {
-    struct {                    // closed-form objective: the query's centres, alpha and log2 p
-      float4 qatom[SHP_MAX_ATOMS];
-      float qlp[SHP_MAX_ATOMS];
+    struct {                    // closed-form objective
+      float4 qatom[SHP_MAX_ATOMS];         // the query's centres, beta'
+      float qlp[SHP_MAX_ATOMS];            // the query's log2 w'
+      float2 fob[SHP_MAX_ATOMS];           // B's beta', log2 w'
+      FoPairB fo2[SHP_MAX_ATOMS / 2];      // B's posed atoms in pairs
     };
     // union objective: per-lane prefix products prod_{l<j} (1 - g_l) of the
     // lane's two current points, for even j (odd j are rebuilt from them)
@@ -86,10 +98,16 @@ __device__ void rot_to_quat(const float R[9], float q[4]) {
   }
 }
 
-__device__ void stage_body(AlignTables& T, const SetView& B, int32_t a0, int nb, int lane) {
+__device__ void stage_body(AlignTables& T, const SetView& B, int32_t a0, int nb, bool closed, int lane) {
   for (int i = lane; i < nb; i += 32) {
-    T.body[i] = B.atom[a0 + i];
+    const float4 c = B.atom[a0 + i];
+    T.body[i] = c;
     T.lp[i] = B.aux[a0 + i].y;
+    if (closed) {
+      float beta, lw;
+      fo_atom_consts(c.w, T.lp[i], beta, lw);
+      T.fob[i] = make_float2(beta, lw);
+    }
   }
   __syncwarp();
 }
@@ -97,7 +115,7 @@ __device__ void stage_body(AlignTables& T, const SetView& B, int32_t a0, int nb,
 // Posed centres c' = R c + t and, for the CRN objectives, the expanded
 // exponent log2 g(r) = a |r - o|^2 + b . (r - o) + c0 with a = -alpha log2(e)
 // (the posed table's w), b = -2 a (c' - o), c0 = a |c' - o|^2 + log2 p.
-__device__ void stage_posed(AlignTables& T, int nb, const float pose[7], int lane) {
+__device__ void stage_posed(AlignTables& T, int nb, const float pose[7], bool closed, int lane) {
   const float kLog2e = 1.4426950408889634f;
   const float4 o = T.origin;
   float q[4] = {pose[0], pose[1], pose[2], pose[3]};
@@ -113,6 +131,7 @@ __device__ void stage_posed(AlignTables& T, int nb, const float pose[7], int lan
     const float yy = fmaf(R[3], c.x, fmaf(R[4], c.y, R[5] * c.z));
     const float yz = fmaf(R[6], c.x, fmaf(R[7], c.y, R[8] * c.z));
     T.posed[i] = make_float4(yx, yy, yz, a);
+    if (closed) continue;  // the closed form uses the posed centres only
     const float dx = yx + pose[4] - o.x, dy = yy + pose[5] - o.y, dz = yz + pose[6] - o.z;
     const float bx = -2.f * a * dx, by = -2.f * a * dy, bz = -2.f * a * dz;
     const float c0 = fmaf(a, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), T.lp[i]);
@@ -124,6 +143,21 @@ __device__ void stage_posed(AlignTables& T, int nb, const float pose[7], int lan
     T.coef[i] = k;
   }
   __syncwarp();
+  if (closed) {
+    for (int p = lane; 2 * p < nb; p += 32) {
+      const int j = 2 * p;
+      const bool two = j + 1 < nb;
+      const float4 y0 = T.posed[j], y1 = two ? T.posed[j + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float2 f0 = T.fob[j], f1 = two ? T.fob[j + 1] : make_float2(1.f, -INFINITY);
+      FoPairB P;
+      P.nxy = make_float4(-y0.x, -y1.x, -y0.y, -y1.y);
+      P.nzb = make_float4(-y0.z, -y1.z, f0.x, f1.x);
+      P.lw = make_float2(f0.y, f1.y);
+      P.pad = make_float2(0.f, 0.f);
+      T.fo2[p] = P;
+    }
+    __syncwarp();
+  }
 }
 
 // g_j at two points r' = r - o (one per half) with rr = |r'|^2: the expanded
@@ -144,11 +178,15 @@ __device__ __forceinline__ void adj_add(const CoefA& k, float2 e, float2& ha, fl
   vz = __ffma2_rn(make_float2(k.bzc.x, k.bzc.y), e, vz);
 }
 
+// The query's atoms for the closed-form objective: centres, beta', log2 w'.
 __device__ void stage_query(AlignTables& T, const SetView& Q, int32_t iq, int lane) {
   const int32_t a0 = Q.off[iq], na = Q.off[iq + 1] - a0;
   for (int i = lane; i < na; i += 32) {
-    T.qatom[i] = Q.atom[a0 + i];
-    T.qlp[i] = Q.aux[a0 + i].y;
+    const float4 c = Q.atom[a0 + i];
+    float beta, lw;
+    fo_atom_consts(c.w, Q.aux[a0 + i].y, beta, lw);
+    T.qatom[i] = make_float4(c.x, c.y, c.z, beta);
+    T.qlp[i] = lw;
   }
   __syncwarp();
 }
@@ -188,28 +226,38 @@ __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restr
 #pragma unroll
   for (int i = 0; i < 7; ++i) acc[i] = 0.f;
   if (objective == SHP_OBJ_FO_CLOSED) {
-    const float kLog2e = 1.4426950408889634f, kPi = 3.14159265358979f;
+    // K_ij = w'_i w'_j r^3 2^(-r^2 d^2) (fo_atom_consts) and h_ij = a K_ij =
+    // ln 2 r^5 2^(...) w'_i w'_j; two database atoms per packed instruction
+    const float kLn2 = 0.6931471805599453f;
+    const int nb2 = (nb + 1) / 2;
     for (int i = lane; i < na; i += 32) {
       const float4 qa = T.qatom[i];
-      const float lpi = T.qlp[i], al = qa.w;
       const float xi = qa.x - t[0], yi = qa.y - t[1], zi = qa.z - t[2];
-      float F = 0.f, H = 0.f, Wx = 0.f, Wy = 0.f, Wz = 0.f;
+      const float2 x2 = make_float2(xi, xi), y2 = make_float2(yi, yi), z2 = make_float2(zi, zi);
+      const float2 b2 = make_float2(qa.w, qa.w), l2 = make_float2(T.qlp[i], T.qlp[i]);
+      float2 Fn = make_float2(0.f, 0.f), Hs = Fn, Wx = Fn, Wy = Fn, Wz = Fn;  // -F, H / ln 2, -W / ln 2
 #pragma unroll 2
-      for (int j = 0; j < nb; ++j) {
-        const float4 y = T.posed[j];
-        const float aj = T.body[j].w;
-        const float dx = xi - y.x, dy = yi - y.y, dz = zi - y.z;
-        const float r = __fdividef(1.f, al + aj), a = al * aj * r, tt = kPi * r;
-        const float K = tt * tt * rsqrtf(tt) *
-                        ex2_approx(fmaf(-a * kLog2e, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), lpi + T.lp[j]));
-        F += K;
-        const float h = a * K;
-        H += h;
-        Wx = fmaf(h, y.x, Wx); Wy = fmaf(h, y.y, Wy); Wz = fmaf(h, y.z, Wz);
+      for (int p = 0; p < nb2; ++p) {
+        const FoPairB& P = T.fo2[p];
+        const float2 ny = make_float2(P.nxy.z, P.nxy.w), nx = make_float2(P.nxy.x, P.nxy.y);
+        const float2 nz = make_float2(P.nzb.x, P.nzb.y);
+        const float2 dx = __fadd2_rn(x2, nx), dy = __fadd2_rn(y2, ny), dz = __fadd2_rn(z2, nz);
+        const float2 d2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+        const float2 sb = __fadd2_rn(b2, make_float2(P.nzb.z, P.nzb.w));
+        const float2 r = make_float2(rsqrtf(sb.x), rsqrtf(sb.y));
+        const float2 rn = __fmul2_rn(r, make_float2(-r.x, -r.y));  // -r^2
+        const float2 e = __ffma2_rn(rn, d2, __fadd2_rn(l2, P.lw));
+        const float2 Kn = __fmul2_rn(__fmul2_rn(rn, r), make_float2(ex2_approx(e.x), ex2_approx(e.y)));  // -K
+        Fn = __fadd2_rn(Fn, Kn);
+        const float2 hp = __fmul2_rn(rn, Kn);  // h / ln 2
+        Hs = __fadd2_rn(Hs, hp);
+        Wx = __ffma2_rn(hp, nx, Wx); Wy = __ffma2_rn(hp, ny, Wy); Wz = __ffma2_rn(hp, nz, Wz);
       }
-      acc[0] += F;
-      acc[1] += 2.f * fmaf(xi, H, -Wx); acc[2] += 2.f * fmaf(yi, H, -Wy); acc[3] += 2.f * fmaf(zi, H, -Wz);
-      add_cross(acc, 2.f * Wx, 2.f * Wy, 2.f * Wz, xi, yi, zi);
+      const float H = kLn2 * (Hs.x + Hs.y);
+      const float Wxs = -kLn2 * (Wx.x + Wx.y), Wys = -kLn2 * (Wy.x + Wy.y), Wzs = -kLn2 * (Wz.x + Wz.y);
+      acc[0] -= Fn.x + Fn.y;
+      acc[1] += 2.f * fmaf(xi, H, -Wxs); acc[2] += 2.f * fmaf(yi, H, -Wys); acc[3] += 2.f * fmaf(zi, H, -Wzs);
+      add_cross(acc, 2.f * Wxs, 2.f * Wys, 2.f * Wzs, xi, yi, zi);
     }
   }
   // CRN objectives: each lane takes points k and k + 32 of every 64 (the
@@ -306,10 +354,10 @@ __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restr
 // dF/d(raw pose) from the force, the torque and the raw quaternion p
 // (q = (w, v) = p / |p|): dF/dp = (-2 tau . v, 2 (w tau + tau x v)) / |p|.
 __device__ void pose_gradient(const float pose[7], const float acc[7], float scale, float grad[7]) {
-  const float nq = sqrtf(pose[0] * pose[0] + pose[1] * pose[1] + pose[2] * pose[2] + pose[3] * pose[3]);
-  const float w = pose[0] / nq, x = pose[1] / nq, y = pose[2] / nq, z = pose[3] / nq;
+  const float inq = rsqrtf(pose[0] * pose[0] + pose[1] * pose[1] + pose[2] * pose[2] + pose[3] * pose[3]);
+  const float w = pose[0] * inq, x = pose[1] * inq, y = pose[2] * inq, z = pose[3] * inq;
   const float tx = acc[4], ty = acc[5], tz = acc[6];
-  const float k = 2.f * scale / nq;
+  const float k = 2.f * scale * inq;
   grad[0] = -k * (tx * x + ty * y + tz * z);
   grad[1] = k * (w * tx + ty * z - tz * y);
   grad[2] = k * (w * ty + tz * x - tx * z);
@@ -385,10 +433,11 @@ __global__ void __launch_bounds__(kAlignThreads) pose_grad_kernel(const GradArgs
   const int32_t b0 = a.B.off[xb], nb = a.B.off[xb + 1] - b0;
   float pose[7];
   for (int d = 0; d < 7; ++d) pose[d] = a.pose[7 * item + d];
-  stage_body(T, a.B, b0, nb, lane);
-  if (a.objective == SHP_OBJ_FO_CLOSED) stage_query(T, a.Q, a.iq, lane);
+  const bool closed = a.objective == SHP_OBJ_FO_CLOSED;
+  stage_body(T, a.B, b0, nb, closed, lane);
+  if (closed) stage_query(T, a.Q, a.iq, lane);
   stage_origin(T, a.Q, a.iq, lane);
-  stage_posed(T, nb, pose, lane);
+  stage_posed(T, nb, pose, closed, lane);
   float acc[7];
   value_grad(T, nb, a.Q.off[a.iq + 1] - a.Q.off[a.iq], a.pts, a.n_pts, a.objective, pose + 4, lane, acc);
   if (lane == 0) {
@@ -486,13 +535,14 @@ __global__ void __launch_bounds__(kAlignThreads) align_adam_kernel(const AdamArg
     float pose[7], m1[7], m2[7];
     start_pose(a, xb, pair, s, pose);
     for (int d = 0; d < 7; ++d) { m1[d] = 0.f; m2[d] = 0.f; }
-    stage_body(T, a.B, b0, nb, lane);
-    if (a.objective == SHP_OBJ_FO_CLOSED) stage_query(T, a.Q, a.iq, lane);
+    const bool closed = a.objective == SHP_OBJ_FO_CLOSED;
+    stage_body(T, a.B, b0, nb, closed, lane);
+    if (closed) stage_query(T, a.Q, a.iq, lane);
     stage_origin(T, a.Q, a.iq, lane);
     const int na = a.Q.off[a.iq + 1] - a.Q.off[a.iq];
     float b1t = 1.f, b2t = 1.f, value = 0.f;
     for (int step = 0; step < a.steps; ++step) {
-      stage_posed(T, nb, pose, lane);
+      stage_posed(T, nb, pose, closed, lane);
       float acc[7];
       value_grad(T, nb, na, a.pts, a.n_pts, a.objective, pose + 4, lane, acc);
       float g[7];
@@ -503,11 +553,12 @@ __global__ void __launch_bounds__(kAlignThreads) align_adam_kernel(const AdamArg
       // cosine step-size decay: constant-step Adam keeps moving by about the
       // step size around the optimum, the decay lets it settle
       const float decay = 0.5f * (1.f + cospif((float)step / (float)a.steps));
+      const float c1 = 1.f / (1.f - b1t), c2 = 1.f / (1.f - b2t);  // bias corrections
       for (int d = 0; d < 7; ++d) {  // Adam ascent (maximise the overlap)
         m1[d] = fmaf(a.beta1, m1[d], (1.f - a.beta1) * g[d]);
         m2[d] = fmaf(a.beta2, m2[d], (1.f - a.beta2) * g[d] * g[d]);
-        const float mh = m1[d] / (1.f - b1t), vh = m2[d] / (1.f - b2t);
-        pose[d] += decay * (d < 4 ? a.lr : a.lr_t) * mh / (sqrtf(vh) + a.eps);
+        const float mh = m1[d] * c1, vh = m2[d] * c2;
+        pose[d] += __fdividef(decay * (d < 4 ? a.lr : a.lr_t) * mh, sqrtf(vh) + a.eps);
       }
       // keep the raw quaternion near unit length (the objective ignores its scale)
       const float inv = rsqrtf(pose[0] * pose[0] + pose[1] * pose[1] + pose[2] * pose[2] + pose[3] * pose[3]);

@@ -56,6 +56,18 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, fl
   z1 = rho * s;
 }
 
+// Per-atom constants of the closed-form first-order term (Eq. fo): with
+// beta' = 1 / (alpha log2 e) and log2 w' = log2 p - (3/2) log2 alpha +
+// (3/4) (log2 pi - log2 log2 e), the term of atoms i, j at distance d is
+// w'_i w'_j r^3 2^(-r^2 d^2) with r = (beta'_i + beta'_j)^(-1/2)
+// (r^2 = log2(e) alpha_i alpha_j / (alpha_i + alpha_j)).
+__device__ __forceinline__ void fo_atom_consts(float alpha, float lp, float& beta, float& lw) {
+  const float kLog2e = 1.4426950408889634f;
+  const float kC = 0.8420473173955658f;  // (3/4) (log2 pi - log2 log2 e)
+  beta = __fdividef(1.f, alpha * kLog2e);
+  lw = fmaf(-1.5f, __log2f(alpha), lp + kC);
+}
+
 // ---------------------------------------------------------------- tables
 
 struct Pose {

@@ -68,13 +68,6 @@ struct __align__(16) FoAtom2 {
   float2 pad;
 };
 
-__device__ __forceinline__ void fo_atom_consts(float alpha, float lp, float& beta, float& lw) {
-  const float kLog2e = 1.4426950408889634f;
-  const float kC = 0.8420473173955658f;  // (3/4) (log2 pi - log2 log2 e)
-  beta = __fdividef(1.f, alpha * kLog2e);
-  lw = fmaf(-1.5f, __log2f(alpha), lp + kC);
-}
-
 // Queries per block: each thread screens its database molecule against all
 // of them, so every database atom is read, and its constants computed, once
 // per group of queries.
