@@ -72,6 +72,8 @@ def parse_args():
     p.add_argument("--self-rel-se", type=float, default=3.5e-3,
                    help="relative SE to which the adaptive screen estimates each database molecule's union "
                         "self-overlap (the queries: a quarter of it)")
+    p.add_argument("--profile-case", choices=["align", "prefilter"], default=None,
+                   help="run one small case of a kernel family for a profiler capture, print its timings, exit")
     p.add_argument("--align-db", type=int, default=10_000,
                    help="database size of the alignment section (0 skips it)")
     return p.parse_args()
@@ -353,6 +355,8 @@ def main():
     if world != args.gpus:
         raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
     torch.cuda.set_device(local)
+    if args.profile_case:
+        return profile_case(shp, torch, args.profile_case)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -517,6 +521,51 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def profile_case(shp, torch, case: str):
+    """Small standalone cases for profiler captures, each kernel launched once
+    for warm-up and once more:
+      align:     1 query (30 atoms) x 1000 molecules, 8 starts x 100 steps,
+                 1024-point union objective, then the closed form
+                 (align_adam_kernel launches 0-1 and 2-3)
+      prefilter: 16 queries x 200,000 molecules (18-60 atoms), first-order
+                 Tanimoto of every pair and the best 10% per query
+                 (fo_tanimoto_kernel launches 0-1)"""
+    from paper_2607_20766_b300 import synth
+    out = {"case": case}
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    if case == "align":
+        q = synth.principal_axes(synth.generate(5150, [30]))
+        d = synth.principal_axes(synth.generate(5151, synth.counts_uniform(5151, 1000, 18, 60)))
+        Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
+        sq = shp.self_overlaps(Sq, seed=2, n_samples=8192)
+        sd = shp.self_overlaps(Sd, seed=2, n_samples=8192, stream_base=1)
+        ib = torch.arange(d.n_mol, dtype=torch.int32, device="cuda")
+        for name, obj in (("union_crn", shp.OBJ_UNION), ("fo_closed", shp.OBJ_FO_CLOSED)):
+            for k in range(2):
+                _, ms = timed(lambda: shp.align_rigid(Sq, 0, Sd, ib, sq, sd, seed=1, starts=8, steps=100, n_score=2,
+                                                      objective=obj))
+            out[name + "_ms"] = ms
+    else:
+        q, d = synth.adaptive_screen(n_q=16, n_db=200_000, seed=4242)
+        Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
+        fq = shp.self_overlaps(Sq, seed=1, n_samples=256)[:, 0].contiguous()
+        fd = shp.self_overlaps(Sd, seed=1, n_samples=256, stream_base=1)[:, 0].contiguous()
+        for k in range(2):
+            T, ms = timed(lambda: shp.fo_tanimoto_screen(Sq, Sd, fq, fd))
+        out["fo_tanimoto_ms"] = ms
+        _, out["select_ms"] = timed(lambda: shp.fo_prefilter_select(Sq, Sd, T, d.n_mol // 10))
+    print(json.dumps(out), flush=True)
     return 0
 
 
