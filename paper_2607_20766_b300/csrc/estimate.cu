@@ -510,11 +510,14 @@ __device__ void pair_epilogue(const CrossArgs& args, int32_t xa, int32_t xb, int
 }
 
 // FP32 SE(T) of the watched slot from the running sums (adaptive stop rule),
-// with the self-overlaps' own errors when their SEs are given.
+// with the self-overlaps' own errors when their SEs are given. The lanes'
+// FP64 sums are reduced over the warp in FP32: the rule needs no more, and a
+// warp-wide FP64 add occupies the SM's FP64 unit ~16 cycles.
 __device__ __forceinline__ float watched_se_t(const CrossArgs& args, const DirState& sa, const DirState& sb, int32_t xa,
                                               int32_t xb, float n, float C = 0.f) {
   const bool w = args.watch != 0;
-  double h[4] = {w ? sa.s[2] : sa.s[0], w ? sa.s[3] : sa.s[1], w ? sb.s[2] : sb.s[0], w ? sb.s[3] : sb.s[1]};
+  float h[4] = {(float)(w ? sa.s[2] : sa.s[0]), (float)(w ? sa.s[3] : sa.s[1]), (float)(w ? sb.s[2] : sb.s[0]),
+                (float)(w ? sb.s[3] : sb.s[1])};
 #pragma unroll
   for (int i = 0; i < 4; ++i) h[i] = warp_sum(h[i]);
   const float ZA = (float)args.A.Z[xa], ZB = (float)args.B.Z[xb];
@@ -1357,7 +1360,8 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_volume_kernel(const CVArg
         b = nxt;
         if (b >= cap_b) break;
         const int w = a.watch;
-        const float nf = (float)n_now, s1 = (float)warp_sum(st.s[2 * w]), s2 = (float)warp_sum(st.s[2 * w + 1]);
+        // the stop rule in FP32 (the lanes' FP64 sums reduced in FP32)
+        const float nf = (float)n_now, s1 = warp_sum((float)st.s[2 * w]), s2 = warp_sum((float)st.s[2 * w + 1]);
         const float var = fmaxf((s2 - s1 * s1 / nf) / (nf - 1.f), 0.f);
         const float V = (float)(w ? closed_s : closed) + (float)Z * (st.K[w] + s1 / nf);
         const float se = (float)Z * sqrtf(var / nf);
