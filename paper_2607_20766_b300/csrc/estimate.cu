@@ -189,10 +189,7 @@ __device__ __forceinline__ void eval_atom(const float4 k0, const float4 k1, cons
       q[p].x = fmaf(-g.x, q[p].x, q[p].x);
       q[p].y = fmaf(-g.y, q[p].y, q[p].y);
     }
-    if (kCV) {
-      ut[p].x = fmaf(k2.z, g.x, ut[p].x);
-      ut[p].y = fmaf(k2.z, g.y, ut[p].y);
-    }
+    if (kCV) ut[p] = __ffma2_rn(make_float2(k2.z, k2.w), g, ut[p]);
   }
 }
 
@@ -826,10 +823,11 @@ constexpr Variant kVariants[] = {{4, 0, 8, 2}, {4, 2, 8, 2}, {4, 0, 4, 5}, {4, 2
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 // Variants also built with the control variate of the union slot (one more
-// FMA per evaluation and two more values per sample pair in registers).
+// FMA per evaluation, packed over the sample pair, and two more values per
+// sample pair in registers).
 constexpr bool cv_variant(int v) {
   return kVariants[v].sp == 4 && kVariants[v].warps == 8 && kVariants[v].min_blocks == 2 &&
-         (kVariants[v].form == 2 || kVariants[v].form == 3 || kVariants[v].form == 5);
+         (kVariants[v].form == 2 || kVariants[v].form == 3 || kVariants[v].form == 4 || kVariants[v].form == 5);
 }
 
 template <int V>
