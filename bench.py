@@ -743,7 +743,7 @@ def adaptive_section(shp, torch, n_db: int, rank: int, lane_rate: float, tau: fl
         T_cv = rcv["T"].cpu().numpy()[:, 1].reshape(q.n_mol, d.n_mol)[:, sub]
         rho_cv = [float(stats.spearmanr(T_cv[i], T_fx[i]).statistic) for i in range(q.n_mol)]
         se_cv = rcv["seT"].cpu().numpy()[:, 1]
-        kept.update(T=rcv["T"][:, 1].clone())
+        kept.update(T=rcv["T"][:, 1].clone(), T_all=rcv["T"].clone())
         pps = npairs / (t_cv + t_w + t_self)
         evals_cv = int(2 * (nu_cv * pair_atoms).sum())
         return {
@@ -772,38 +772,66 @@ def adaptive_section(shp, torch, n_db: int, rank: int, lane_rate: float, tau: fl
 
     def prefilter_arm(keep: float, k_top: int = 100):
         """The cheap first-order stage of the paper's hybrid pipeline applied
-        to screening: the closed-form first-order Tanimoto of every pair ranks
-        each query's database; only its best `keep` fraction goes through
-        the adaptive union screen (fitted control variate, the weights and
-        self-overlaps of the arm above); both stages are library kernels
-        (closed-form first order, exact per-query top-k). A listed pair gets exactly the
-        numbers of the unfiltered screen, so recall@k (the share of each
-        query's union top-k of the unfiltered screen that survives) measures
-        the prefilter alone."""
-        wq, wd, T_full = kept["wq"], kept["wd"], kept["T"]
+        to screening, timed end to end: closed-form first-order self-overlaps
+        and Tanimoto of every pair, each query's best `keep` fraction (exact
+        top-k), then the union stage on the kept database molecules only
+        (their self-overlaps to the same precision and their fitted
+        control-variate weights, on id-keyed streams, beside the queries' on a
+        side stream) and the adaptive union screen of the kept pairs. Every
+        stage is a library kernel. A kept pair gets exactly the numbers of the
+        unfiltered fitted-CV screen (same streams, self-overlaps and weights),
+        so recall@k (the share of each query's union top-k of the unfiltered
+        screen that survives) measures the prefilter alone."""
+        T_full = kept["T"]
+        k_keep = max(k_top, int(keep * d.n_mol))
+        ida = torch.arange(d.n_mol, dtype=torch.int32, device="cuda")
+        iqa = torch.arange(q.n_mol, dtype=torch.int32, device="cuda")
 
-        fo_q, fo_d = selfq[:, 0].contiguous(), selfd[:, 0].contiguous()
-
-        def stage1():
+        def pipeline():
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            fo_q = shp.fo_overlap(Sq, iqa, Sq, iqa)
+            fo_d = shp.fo_overlap(Sd, ida, Sd, ida)
             T_fo = shp.fo_tanimoto_screen(Sq, Sd, fo_q, fo_d)
-            return shp.fo_prefilter_select(Sq, Sd, T_fo, max(k_top, int(keep * d.n_mol)))
+            pq, pd = shp.fo_prefilter_select(Sq, Sd, T_fo, k_keep)
+            ids = shp.prefilter_db_ids(Sd, pd)
+            ev[1].record(stream)
+            side.wait_stream(stream)
+            with torch.cuda.stream(side):
+                sq_, sq_se_, _ = shp.self_overlaps(Sq, seed=11, n_samples=1 << 24, stream_base=0,
+                                                   target_rel_se=rel_q, round=4096, with_se=True)
+                wq_ = shp.cv_fit_weights(Sq, seed=91, n_samples=fit_samples)
+            sd_, sd_se_, _ = shp.self_overlaps(Sd, seed=11, n_samples=1 << 22, stream_base=16,
+                                               target_rel_se=self_rel_se, round=256, with_se=True, idx=ids)
+            wd_ = shp.cv_fit_weights(Sd, seed=92, n_samples=fit_samples, idx=ids, id_streams=True)
+            stream.wait_stream(side)
+            for t in (sq_, sq_se_, wq_):
+                t.record_stream(stream)
+            ev[2].record(stream)
+            res = shp.tanimoto_screen(Sq, Sd, sq_, sd_, seed=77, tau=tau, round=256, min_n=1024, cap=cap,
+                                      omega_q=wq_, omega_db=wd_, pairs=(pq, pd), self_se_q=sq_se_,
+                                      self_se_db=sd_se_)
+            ev[3].record(stream)
+            return res, pq, pd, ids, ev
 
-        stage1()  # warm-up
-        (pq, pd), t_fo = timed(stage1)
-        shp.tanimoto_screen(Sq, Sd, selfq, selfd, seed=77, tau=tau, round=256, min_n=1024, cap=cap, omega_q=wq,
-                            omega_db=wd, pairs=(pq[:4096], pd[:4096]), **se_kw)  # warm-up
-        res_f, t_scr = timed(lambda: shp.tanimoto_screen(Sq, Sd, selfq, selfd, seed=77, tau=tau, round=256,
-                                                         min_n=1024, cap=cap, omega_q=wq, omega_db=wd,
-                                                         pairs=(pq, pd), **se_kw))
+        pipeline()  # warm-up
+        torch.cuda.synchronize()
+        res_f, pq, pd, ids, ev = pipeline()
+        torch.cuda.synchronize()
+        t_fo, t_union_prep, t_scr = (ev[i].elapsed_time(ev[i + 1]) / 1e3 for i in range(3))
+        t_total = ev[0].elapsed_time(ev[3]) / 1e3
         Tf = torch.full((q.n_mol, d.n_mol), float("-inf"), device=pq.device)
         Tf[pq.long(), pd.long()] = res_f["T"][:, 1]
         top_f = torch.topk(Tf, k_top, dim=1).indices
         top_r = torch.topk(T_full.view(q.n_mol, d.n_mol), k_top, dim=1).indices
         recall = [len(np.intersect1d(top_f[i].cpu().numpy(), top_r[i].cpu().numpy())) / k_top for i in range(q.n_mol)]
-        pps = npairs / (t_fo + t_scr + kept["t_w"] + t_self)
-        return {"keep": keep, "pairs_screened": int(pq.numel()), "first_order_seconds": t_fo, "screen_seconds": t_scr,
+        same = bool(torch.equal(res_f["T"], kept["T_all"].view(-1, 2)[(pq.long() * d.n_mol + pd.long())]))
+        pps = npairs / t_total
+        return {"keep": keep, "pairs_screened": int(pq.numel()),
+                "molecules_kept": int((ids >= 0).sum().item()), "first_order_seconds": t_fo,
+                "union_prep_seconds": t_union_prep, "screen_seconds": t_scr, "seconds": t_total,
                 "pairs_per_s": pps, "speedup_vs_unfiltered_cv": pps / with_fit["pairs_per_s"],
-                "speedup_vs_p99_fixed": pps / fixed99_pps,
+                "speedup_vs_p99_fixed": pps / fixed99_pps, "kept_pairs_equal_unfiltered": same,
                 f"recall_at_{k_top}": {"mean": float(np.mean(recall)), "min": float(np.min(recall))}}
 
     prefilter = [prefilter_arm(0.25), prefilter_arm(0.1), prefilter_arm(0.05)]

@@ -56,6 +56,9 @@ extern "C" {
 /* Monte-Carlo flags */
 #define SHP_SYMMETRIC 1u  /* estimate from both proposals and average (Sec. IS estimator) */
 #define SHP_ANTITHETIC 2u /* pair each draw with its reflection about the component centre */
+#define SHP_ID_STREAMS 4u /* per-molecule calls with an idx list: molecule idx[k] draws from stream
+                             stream_base + idx[k] (its id) instead of stream_base + k, so the
+                             listed molecules get exactly the values of a call over the whole set */
 
 /* Stream tags (counter word 3) */
 #define SHP_TAG_AB 0u   /* samples drawn from A's mixture, B evaluated */
@@ -163,7 +166,7 @@ int overlap_estimate(shp_set A, const int32_t* ia, shp_set B, const int32_t* ib,
  *   vol[k], vol_se[k]         V = Z mean(u/m)
  *   self_ov[k], self_se[k]    O_AA = Z mean(u^2/m)   (both may be NULL)
  *   idx   [n] int32 device or NULL (= 0..n-1); outputs [n] double device.
- * mc->flags: SHP_ANTITHETIC only.
+ * mc->flags: SHP_ANTITHETIC, SHP_ID_STREAMS (stream mc->stream_base + idx[k]).
  */
 int union_volume_estimate(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, double* vol,
                           double* vol_se, double* self_ov, double* self_se, void* stream);
@@ -213,6 +216,19 @@ int fo_tanimoto_screen(shp_set Q, shp_set D, const double* fo_self_q, const doub
  */
 int fo_prefilter_select(shp_set Q, shp_set D, const float* T, int64_t k, int32_t* pairs_q, int32_t* pairs_db,
                         void* stream);
+
+/*
+ * The database molecules a pair list keeps (e.g. fo_prefilter_select's
+ * pairs_db), as an idx list for the per-molecule calls: ids[d] = d for every
+ * d listed at least once, -1 for the rest. Passed as idx (with
+ * SHP_ID_STREAMS) to union_self_estimate or cv_fit_weights, it computes the
+ * kept molecules only, each with exactly the values of a call over the whole
+ * set, at position d of the outputs (the -1 entries are skipped: NaN
+ * estimates, no weights written).
+ *   pairs_db [n_pairs] int32 device (ids outside the set are ignored);
+ *   ids [n_db] int32 device, written.
+ */
+int prefilter_db_ids(shp_set D, const int32_t* pairs_db, int64_t n_pairs, int32_t* ids, void* stream);
 
 /* Screening settings (Sec. confidence-bounded screening). */
 typedef struct {
@@ -443,7 +459,8 @@ int union_attributions(shp_set S, uint64_t seed, uint64_t stream_base, uint32_t 
  *   b_i = integral u g_i = Z E_q[(u / m) g_i],   lambda = ridge * trace(G) / N,
  * b from mc->n_samples (a positive multiple of 256) samples of the molecule's
  * own mixture (stream mc->stream_base + k, tag SHP_TAG_FIT, the usual sample
- * layout; mc->flags must be 0), solved by conjugate gradients to a relative
+ * layout; mc->flags: 0 or SHP_ID_STREAMS, then stream mc->stream_base +
+ * idx[k]), solved by conjugate gradients to a relative
  * residual of 1e-6 (at most 4 N iterations).
  *   idx [n] device int32 molecule ids, or NULL for molecules 0 .. n-1
  *   omega [n_atoms] float device: written for the atoms of the listed
@@ -461,7 +478,8 @@ int cv_fit_weights(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, f
 /*
  * Union volume of molecules S[idx[k]] with the control variate omega (per
  * set atom, float device; NULL = plain estimator), same samples as
- * union_volume_estimate (tag SHP_TAG_SELF, stream mc->stream_base + k).
+ * union_volume_estimate (tag SHP_TAG_SELF, stream mc->stream_base + k, or
+ * + idx[k] with mc->flags = SHP_ID_STREAMS; no other flags).
  * target_rel_se <= 0: mc->n_samples samples. target_rel_se > 0: rounds of
  * `round` samples (a multiple of 256 dividing mc->n_samples, which is then
  * the cap) until SE / V <= target_rel_se (checked in FP32).
@@ -475,8 +493,8 @@ int union_volume_cv(shp_set S, const int32_t* idx, int64_t n, const shp_mc* mc, 
  * Union volumes and union self-overlaps of molecules S[idx[k]] to a stated
  * precision (Eq. expectation with f = u/m and Eq. union-is with B = A; the
  * self-overlaps are the O_AA of the Tanimoto, Sec. union). Same samples as
- * union_volume_estimate (tag SHP_TAG_SELF, stream mc->stream_base + k, no
- * flags). With omega (per set atom, float device; NULL = plain) both carry
+ * union_volume_estimate (tag SHP_TAG_SELF, stream mc->stream_base + k, or
+ * + idx[k] with mc->flags = SHP_ID_STREAMS; no other flags). With omega (per set atom, float device; NULL = plain) both carry
  * the weighted-Gaussian control variate u~ = sum_i omega_i g_i:
  *   V    = sum_i omega_i v_i                  + Z E_q[(u - u~) / m]
  *   O_AA = sum_ij omega_i omega_j int g_i g_j + Z E_q[(u^2 - u~^2) / m]

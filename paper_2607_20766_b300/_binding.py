@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libshape.so")
 SHP_OK = 0
 SYMMETRIC = 1
 ANTITHETIC = 2
+ID_STREAMS = 4  # idx lists: molecule idx[k] draws from stream stream_base + idx[k]
 TAG_AB, TAG_BA, TAG_SELF = 0, 1, 2
 MAX_ATOMS = 64
 
@@ -29,7 +30,7 @@ EXPORTS = ("shp_last_error", "shp_version", "shp_fail_next_allocations", "shape_
            "overlap_pose_grad", "align_rigid", "shape_set_frames", "union_attributions", "union_volume_cv",
            "cv_features", "mlp_forward", "mlp_loss_grad", "mlp_adam", "mlp_loss_grad_noalloc", "cv_fit_weights",
            "union_self_estimate", "shp_eval_probe", "fo_tanimoto_screen",
-           "fo_prefilter_select")
+           "fo_prefilter_select", "prefilter_db_ids")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 33, 64, 6401
 OBJ_FO, OBJ_UNION, OBJ_FO_CLOSED = 0, 1, 2
 
@@ -95,6 +96,7 @@ def load_library():
         "cv_features": [_P, _P, _P],
         "fo_tanimoto_screen": [_P, _P, _P, _P, _P, _P],
         "fo_prefilter_select": [_P, _P, _P, ctypes.c_int64, _P, _P, _P],
+        "prefilter_db_ids": [_P, _P, ctypes.c_int64, _P, _P],
         "shp_eval_probe": [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, _P,
                            _P, _P],
         "union_self_estimate": [_P, _P, ctypes.c_int64, _P, _P, ctypes.c_float, ctypes.c_uint32, ctypes.c_uint32, _P,
@@ -375,6 +377,17 @@ def fo_prefilter_select(Q: ShapeSet, D: ShapeSet, T: torch.Tensor, k: int, strea
     return pq, pd
 
 
+@_on_stream
+def prefilter_db_ids(D: ShapeSet, pairs_db: torch.Tensor, stream=None) -> torch.Tensor:
+    """[n_db] int32 device tensor: d for every database molecule d listed in
+    pairs_db, -1 for the rest; as idx (with id_streams) it restricts the
+    per-molecule estimators to the kept molecules, results at position d."""
+    pd = _device_i32(pairs_db, D.device)
+    ids = torch.empty(D.n_mol, dtype=torch.int32, device=D.device)
+    _check(load_library().prefilter_db_ids(D.handle, _dptr(pd), pd.numel(), _dptr(ids), _stream(stream)))
+    return ids
+
+
 def fail_next_allocations(count: int) -> None:
     """Test hook: the next `count` device allocations of library calls fail
     as out of memory (0 clears)."""
@@ -437,30 +450,34 @@ def tanimoto_screen_tune(Q: ShapeSet, D: ShapeSet, self_q: torch.Tensor, self_db
 
 @_on_stream
 def self_overlaps(S: ShapeSet, seed: int, n_samples: int, stream_base: int = 0, stream=None,
-                  target_rel_se: float = 0.0, round: int = 256, omega=None, with_se: bool = False):
-    """[n_mol, 2] float64 device tensor: slot 0 closed-form first-order
-    self-overlap, slot 1 union self-overlap estimate (n_samples draws, or
-    rounds of `round` up to the cap n_samples until its relative SE is
-    <= target_rel_se; omega: control-variate weights per set atom). With
-    with_se, returns (self, se, n_used): se [n_mol, 2] (slot 0 zero, the
-    closed form is exact) and the samples per molecule."""
+                  target_rel_se: float = 0.0, round: int = 256, omega=None, with_se: bool = False, idx=None):
+    """[n, 2] float64 device tensor (n = n_mol, or the length of idx): slot 0
+    closed-form first-order self-overlap, slot 1 union self-overlap estimate
+    (n_samples draws, or rounds of `round` up to the cap n_samples until its
+    relative SE is <= target_rel_se; omega: control-variate weights per set
+    atom). With with_se, returns (self, se, n_used): se [n, 2] (slot 0 zero,
+    the closed form is exact) and the samples per molecule. With idx, only
+    the listed molecules, each on its own id's stream (stream_base + id), so
+    they get exactly the values of the call over the whole set."""
     dev = S.device
-    idx = torch.arange(S.n_mol, dtype=torch.int32, device=dev)
-    out = torch.empty((S.n_mol, 2), dtype=torch.float64, device=dev)
+    by_id = idx is not None
+    idx = torch.arange(S.n_mol, dtype=torch.int32, device=dev) if idx is None else _device_i32(idx, dev)
+    n = idx.numel()
+    out = torch.empty((n, 2), dtype=torch.float64, device=dev)
     fo = fo_overlap(S, idx, S, idx, stream=stream)
     if target_rel_se <= 0 and omega is None and not with_se:
         vol, vse, so, sse = union_volume_estimate(S, idx, seed=seed, n_samples=n_samples, stream_base=stream_base,
-                                                  stream=stream)
+                                                  stream=stream, flags=ID_STREAMS if by_id else 0)
         nu = None
     else:
-        _, _, so, sse, nu = union_self_estimate(S, None, omega=omega, seed=seed, n_samples=n_samples,
-                                                target_rel_se=target_rel_se, round=round, watch=1,
-                                                stream_base=stream_base, stream=stream)
+        _, _, so, sse, nu = union_self_estimate(S, idx if by_id else None, omega=omega, seed=seed,
+                                                n_samples=n_samples, target_rel_se=target_rel_se, round=round,
+                                                watch=1, stream_base=stream_base, stream=stream, id_streams=by_id)
     out[:, 0] = fo
     out[:, 1] = so
     if not with_se:
         return out
-    se = torch.zeros((S.n_mol, 2), dtype=torch.float64, device=dev)
+    se = torch.zeros((n, 2), dtype=torch.float64, device=dev)
     se[:, 1] = sse
     return out, se, nu
 
@@ -554,9 +571,11 @@ def union_attributions(S: ShapeSet, seed: int, M: int = 512, stream_base: int = 
 
 @_on_stream
 def union_volume_cv(S: ShapeSet, idx=None, omega=None, seed: int = 0, n_samples: int = 4096,
-                    target_rel_se: float = 0.0, round: int = 256, stream_base: int = 0, stream=None):
+                    target_rel_se: float = 0.0, round: int = 256, stream_base: int = 0, stream=None,
+                    id_streams: bool = False):
     """(vol, vol_se, n_used): union volumes with the control variate omega
-    (per set atom; None = plain), fixed n_samples or adaptive to a relative SE."""
+    (per set atom; None = plain), fixed n_samples or adaptive to a relative SE.
+    id_streams: molecule idx[k] uses stream stream_base + idx[k]."""
     dev = S.device
     if idx is not None:
         idx = _device_i32(idx, dev)
@@ -568,7 +587,7 @@ def union_volume_cv(S: ShapeSet, idx=None, omega=None, seed: int = 0, n_samples:
     vol = torch.empty(n, dtype=torch.float64, device=dev)
     se = torch.empty(n, dtype=torch.float64, device=dev)
     nu = torch.empty(n, dtype=torch.int32, device=dev)
-    mc = ShpMC(seed, stream_base, n_samples, 0)
+    mc = ShpMC(seed, stream_base, n_samples, ID_STREAMS if id_streams else 0)
     _check(load_library().union_volume_cv(S.handle, _dptr(idx), n, ctypes.byref(mc), _dptr(omega), target_rel_se,
                                           round, _dptr(vol), _dptr(se), _dptr(nu), _stream(stream)))
     return vol, se, nu
@@ -577,11 +596,12 @@ def union_volume_cv(S: ShapeSet, idx=None, omega=None, seed: int = 0, n_samples:
 @_on_stream
 def union_self_estimate(S: ShapeSet, idx=None, omega=None, seed: int = 0, n_samples: int = 4096,
                         target_rel_se: float = 0.0, round: int = 256, watch: int = 1, stream_base: int = 0,
-                        stream=None):
+                        stream=None, id_streams: bool = False):
     """(vol, vol_se, self_ov, self_se, n_used): union volumes and union
     self-overlaps, plain or with the control variate omega, fixed n_samples
     or rounds until the watched estimate (0 volume, 1 self-overlap) reaches
-    target_rel_se (n_samples is then the cap)."""
+    target_rel_se (n_samples is then the cap). id_streams: molecule idx[k]
+    uses stream stream_base + idx[k], so a subset gets the whole set's values."""
     dev = S.device
     if idx is not None:
         idx = _device_i32(idx, dev)
@@ -592,7 +612,7 @@ def union_self_estimate(S: ShapeSet, idx=None, omega=None, seed: int = 0, n_samp
         omega = torch.as_tensor(omega, dtype=torch.float32, device=dev).contiguous()
     outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4)]
     nu = torch.empty(n, dtype=torch.int32, device=dev)
-    mc = ShpMC(seed, stream_base, n_samples, 0)
+    mc = ShpMC(seed, stream_base, n_samples, ID_STREAMS if id_streams else 0)
     _check(load_library().union_self_estimate(S.handle, _dptr(idx), n, ctypes.byref(mc), _dptr(omega), target_rel_se,
                                               round, watch, *(_dptr(t) for t in outs), _dptr(nu), _stream(stream)))
     return (*outs, nu)
@@ -600,11 +620,11 @@ def union_self_estimate(S: ShapeSet, idx=None, omega=None, seed: int = 0, n_samp
 
 @_on_stream
 def cv_fit_weights(S: ShapeSet, seed: int, n_samples: int = 1024, stream_base: int = 0, ridge: float = 1e-6,
-                   idx=None, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+                   idx=None, out: torch.Tensor | None = None, stream=None, id_streams: bool = False) -> torch.Tensor:
     """[n_atoms] float32 device tensor: least-squares control-variate weights
     (the projection of u onto each molecule's Gaussians, the right-hand side
     from n_samples of its own samples) for the listed molecules (all if idx
-    is None)."""
+    is None). id_streams: molecule idx[k] uses stream stream_base + idx[k]."""
     dev = S.device
     omega = out if out is not None else torch.zeros(S.n_atoms, dtype=torch.float32, device=dev)
     if idx is None:
@@ -612,7 +632,7 @@ def cv_fit_weights(S: ShapeSet, seed: int, n_samples: int = 1024, stream_base: i
     else:
         ip = _device_i32(idx, dev)
         n = ip.numel()
-    mc = ShpMC(seed, stream_base, n_samples, 0)
+    mc = ShpMC(seed, stream_base, n_samples, ID_STREAMS if id_streams else 0)
     _check(load_library().cv_fit_weights(S.handle, _dptr(ip), n, ctypes.byref(mc), ridge, _dptr(omega),
                                          _stream(stream)))
     return omega

@@ -673,6 +673,7 @@ struct SelfArgs {
   uint64_t stream_base;
   uint32_t n;
   bool anti;
+  bool by_id;  // stream stream_base + molecule id instead of + item
   double* vol;
   double* vol_se;
   double* self_ov;
@@ -704,7 +705,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) self_kernel(const Sel
       continue;
     }
     const MolRef M = mol_ref(args.S, xm);
-    const uint64_t stream = args.stream_base + item;
+    const uint64_t stream = args.stream_base + (args.by_id ? (uint64_t)xm : (uint64_t)item);
     stage_direction(T, args.S, M, nullptr, nullptr, M, nullptr, lane);
     DirState& st = T.st[0][lane];
     dir_init(st);
@@ -968,14 +969,14 @@ bool variant_valid(int mode, bool cv, int v) {
 
 static_assert(cv_variant(kDefaultVariant), "the default variant must be built with the control variate");
 
-int check_mc(const shp_mc* mc, const char* who) {
+int check_mc(const shp_mc* mc, const char* who, uint32_t allowed = SHP_SYMMETRIC | SHP_ANTITHETIC) {
   if (!mc) { set_error("%s: NULL shp_mc", who); return SHP_EINVAL; }
   if (mc->n_samples < 2) { set_error("%s: n_samples must be >= 2", who); return SHP_EINVAL; }
   if ((mc->flags & SHP_ANTITHETIC) && (mc->n_samples & 1u)) {
     set_error("%s: antithetic sampling needs an even n_samples", who);
     return SHP_EINVAL;
   }
-  if (mc->flags & ~(SHP_SYMMETRIC | SHP_ANTITHETIC)) { set_error("%s: unknown flags", who); return SHP_EINVAL; }
+  if (mc->flags & ~allowed) { set_error("%s: unknown flags", who); return SHP_EINVAL; }
   return SHP_OK;
 }
 
@@ -1111,7 +1112,7 @@ extern "C" int union_volume_estimate(shp_set S, const int32_t* idx, int64_t n, c
                                      double* vol_se, double* self_ov, double* self_se, void* stream) {
   clear_error();
   if (!S) { set_error("union_volume_estimate: NULL set"); return SHP_EINVAL; }
-  int rc = check_mc(mc, "union_volume_estimate");
+  int rc = check_mc(mc, "union_volume_estimate", SHP_SYMMETRIC | SHP_ANTITHETIC | SHP_ID_STREAMS);
   if (rc) return rc;
   if (mc->flags & SHP_SYMMETRIC) { set_error("union_volume_estimate: SHP_SYMMETRIC does not apply"); return SHP_EINVAL; }
   if (n < 0) { set_error("union_volume_estimate: negative n"); return SHP_EINVAL; }
@@ -1126,6 +1127,7 @@ extern "C" int union_volume_estimate(shp_set S, const int32_t* idx, int64_t n, c
   a.stream_base = mc->stream_base;
   a.n = mc->n_samples;
   a.anti = (mc->flags & SHP_ANTITHETIC) != 0;
+  a.by_id = idx && (mc->flags & SHP_ID_STREAMS);
   a.vol = vol;
   a.vol_se = vol_se;
   a.self_ov = self_ov;
@@ -1285,6 +1287,7 @@ struct CVArgs {
                        // estimand (checked every round_b batches)
   uint32_t round_b;
   int watch;           // 0: volume, 1: self-overlap
+  bool by_id;          // stream stream_base + molecule id instead of + item
   double* vol;
   double* vol_se;
   double* self_ov;
@@ -1339,7 +1342,7 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_volume_kernel(const CVArg
     const double Z = a.S.Z[xm];
     DirState& st = T.st[0][lane];
     dir_init(st);
-    const uint64_t stream = a.stream_base + item;
+    const uint64_t stream = a.stream_base + (a.by_id ? (uint64_t)xm : (uint64_t)item);
     const uint32_t slo = (uint32_t)stream, shi = (uint32_t)(stream >> 32);
     uint32_t n_done;
     if (a.target <= 0.f) {
@@ -1393,6 +1396,7 @@ struct FitArgs {
   uint32_t nb;    // batches of 256 samples per molecule
   float ridge;
   float* omega;
+  bool by_id;     // stream stream_base + molecule id instead of + item
   unsigned long long* queue;
 };
 
@@ -1429,7 +1433,7 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_fit_kernel(const FitArgs 
     const int32_t xm = a.idx ? a.idx[item] : (int32_t)item;
     if (xm < 0 || xm >= a.S.n_mol) continue;  // an id outside the set has no atoms to write
     const MolRef M = mol_ref(a.S, xm);
-    const uint64_t stream = a.stream_base + item;
+    const uint64_t stream = a.stream_base + (a.by_id ? (uint64_t)xm : (uint64_t)item);
     stage_direction(T, a.S, M, nullptr, nullptr, M, nullptr, lane);
     for (int j = lane; j < SHP_MAX_ATOMS; j += 32) bsum[j] = 0.f;
     __syncwarp();
@@ -1535,8 +1539,8 @@ extern "C" int cv_fit_weights(shp_set S, const int32_t* idx, int64_t n, const sh
                               void* stream) {
   clear_error();
   if (!S || !mc || !omega) { set_error("cv_fit_weights: NULL argument"); return SHP_EINVAL; }
-  if (mc->n_samples == 0 || mc->n_samples % 256u || mc->flags) {
-    set_error("cv_fit_weights: n_samples must be a positive multiple of 256, no flags");
+  if (mc->n_samples == 0 || mc->n_samples % 256u || (mc->flags & ~SHP_ID_STREAMS)) {
+    set_error("cv_fit_weights: n_samples must be a positive multiple of 256, no flags but SHP_ID_STREAMS");
     return SHP_EINVAL;
   }
   if (!(ridge >= 0.f)) { set_error("cv_fit_weights: ridge must be >= 0"); return SHP_EINVAL; }
@@ -1552,6 +1556,7 @@ extern "C" int cv_fit_weights(shp_set S, const int32_t* idx, int64_t n, const sh
   a.nb = mc->n_samples / 256u;
   a.ridge = ridge;
   a.omega = omega;
+  a.by_id = idx && (mc->flags & SHP_ID_STREAMS);
   return launch_persistent(cv_fit_kernel, a, n, kCVWarps, sizeof(WarpTables) * kCVWarps, (cudaStream_t)stream);
 }
 
@@ -1562,7 +1567,10 @@ int self_estimate(const char* who, shp_set S, const int32_t* idx, int64_t n, con
                   float target_rel_se, uint32_t round, int watch, double* vol, double* vol_se, double* self_ov,
                   double* self_se, uint32_t* n_used, cudaStream_t stream) {
   if (!S || !mc) { set_error("%s: NULL argument", who); return SHP_EINVAL; }
-  if (mc->n_samples < 2 || mc->flags) { set_error("%s: n_samples >= 2 and no flags", who); return SHP_EINVAL; }
+  if (mc->n_samples < 2 || (mc->flags & ~SHP_ID_STREAMS)) {
+    set_error("%s: n_samples >= 2 and no flags but SHP_ID_STREAMS", who);
+    return SHP_EINVAL;
+  }
   if (n < 0) { set_error("%s: negative n", who); return SHP_EINVAL; }
   if (watch != 0 && watch != 1) { set_error("%s: watch must be 0 (volume) or 1 (self-overlap)", who); return SHP_EINVAL; }
   if (n == 0) return SHP_OK;
@@ -1585,6 +1593,7 @@ int self_estimate(const char* who, shp_set S, const int32_t* idx, int64_t n, con
   a.n = mc->n_samples;
   a.target = target_rel_se;
   a.watch = watch;
+  a.by_id = idx && (mc->flags & SHP_ID_STREAMS);
   a.vol = vol;
   a.vol_se = vol_se;
   a.self_ov = self_ov;

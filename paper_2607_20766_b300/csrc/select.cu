@@ -249,3 +249,38 @@ extern "C" int fo_prefilter_select(shp_set Q, shp_set D, const float* T_fo, int6
   if (e != cudaSuccess) return cuda_fail(e, "fo_prefilter_select");
   return SHP_OK;
 }
+
+namespace shp {
+namespace {
+
+__global__ void fill_ids_kernel(int32_t* ids, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) ids[i] = -1;
+}
+
+// Every listed database id d marks ids[d] = d (several pairs may mark the
+// same entry with the same value); ids outside 0 .. n_db - 1 are ignored.
+__global__ void mark_ids_kernel(const int32_t* pairs_db, int64_t n_pairs, int32_t n_db, int32_t* ids) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_pairs) return;
+  const int32_t d = pairs_db[i];
+  if (d >= 0 && d < n_db) ids[d] = d;
+}
+
+}  // namespace
+}  // namespace shp
+
+extern "C" int prefilter_db_ids(shp_set D, const int32_t* pairs_db, int64_t n_pairs, int32_t* ids, void* stream) {
+  clear_error();
+  if (!D) { set_error("prefilter_db_ids: NULL set"); return SHP_EINVAL; }
+  if (n_pairs < 0) { set_error("prefilter_db_ids: negative n_pairs"); return SHP_EINVAL; }
+  const int64_t n_db = D->n_mol;
+  if (n_db == 0) return SHP_OK;
+  if (!ids || (n_pairs > 0 && !pairs_db)) { set_error("prefilter_db_ids: NULL array"); return SHP_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  fill_ids_kernel<<<(unsigned)((n_db + 255) / 256), 256, 0, st>>>(ids, n_db);
+  if (n_pairs > 0)
+    mark_ids_kernel<<<(unsigned)((n_pairs + 255) / 256), 256, 0, st>>>(pairs_db, n_pairs, (int32_t)n_db, ids);
+  SHP_CUDA(cudaGetLastError());
+  return SHP_OK;
+}

@@ -63,6 +63,7 @@ def test_null_and_bad_arguments_rejected(lib):
     assert lib.union_self_estimate(None, None, 1, ctypes.byref(mc), None, 0.0, 256, 1, None, None, None, None, None,
                                    None) == -1
     assert lib.fo_tanimoto_screen(None, None, None, None, None, None) == -1
+    assert lib.prefilter_db_ids(None, None, 0, None, None) == -1
     n_ev = ctypes.c_int64()
     assert lib.shp_eval_probe(None, 0, None, 0, -1, 0, 8, None, ctypes.byref(n_ev), None) == -1
     assert lib.align_rigid(None, 0, None, None, 1, None, None, None, None, None, None, None, None) in (-1, -4)

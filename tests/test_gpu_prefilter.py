@@ -112,3 +112,35 @@ def test_prefilter_full_size_sampled():
     assert torch.equal(pq.view(q.n_mol, k), torch.arange(q.n_mol, dtype=torch.int32, device="cuda")[:, None]
                        .expand(q.n_mol, k))
     assert torch.equal(pd.view(q.n_mol, k), want)
+
+
+def test_kept_molecules_get_the_whole_sets_values(sets):
+    """prefilter_db_ids marks the kept database molecules; as an idx list with
+    id-keyed streams the per-molecule estimators then give every kept
+    molecule exactly the values of the call over the whole set (self-overlaps
+    fixed and to a relative SE, least-squares weights), and skip the rest."""
+    q, d, Sq, Sd = sets
+    rng = np.random.default_rng(5)
+    pd = torch.tensor(rng.choice(d.n_mol, 120), dtype=torch.int32, device="cuda")
+    ids = shp.prefilter_db_ids(Sd, pd)
+    keep = np.zeros(d.n_mol, bool)
+    keep[pd.cpu().numpy()] = True
+    want = np.where(keep, np.arange(d.n_mol), -1)
+    np.testing.assert_array_equal(ids.cpu().numpy(), want)
+    full = shp.self_overlaps(Sd, seed=3, n_samples=2048, stream_base=7)
+    sub = shp.self_overlaps(Sd, seed=3, n_samples=2048, stream_base=7, idx=ids)
+    np.testing.assert_array_equal(sub.cpu().numpy()[keep], full.cpu().numpy()[keep])
+    assert np.all(np.isnan(sub.cpu().numpy()[~keep, 1]))
+    fs, fse, fn = shp.self_overlaps(Sd, seed=3, n_samples=1 << 16, stream_base=7, target_rel_se=1e-2, with_se=True)
+    ss, sse, sn = shp.self_overlaps(Sd, seed=3, n_samples=1 << 16, stream_base=7, target_rel_se=1e-2, with_se=True,
+                                    idx=ids)
+    for a, b in ((ss, fs), (sse, fse), (sn, fn)):
+        np.testing.assert_array_equal(a.cpu().numpy()[keep], b.cpu().numpy()[keep])
+    wf = shp.cv_fit_weights(Sd, seed=4, n_samples=1024)
+    ws = shp.cv_fit_weights(Sd, seed=4, n_samples=1024, idx=ids, id_streams=True)
+    atom_keep = np.repeat(keep, np.diff(d.offsets))
+    np.testing.assert_array_equal(ws.cpu().numpy()[atom_keep], wf.cpu().numpy()[atom_keep])
+    assert np.all(ws.cpu().numpy()[~atom_keep] == 0)
+    # id-keyed streams apply to per-molecule calls only
+    with pytest.raises(shp.ShapeError):
+        shp.overlap_estimate(Sq, [0], Sd, [0], seed=1, n_samples=256, flags=shp.ID_STREAMS)
