@@ -1,7 +1,7 @@
 // Closed-form first-order overlap (Eq. fo, with heights p_i p_j): one warp
-// per pair, lanes over A's atoms, B's atoms read as warp-wide broadcasts.
-// Terms are evaluated in FP32 (SFU exp2) and each lane's partial sum is
-// reduced over the warp in FP64.
+// per pair over its flattened atom pairs, and the first-order Tanimoto of
+// every (query, database) pair for the screen's prefilter. Terms are
+// evaluated in FP32 with per-atom constants (SFU rsqrt and exp2 per term).
 #include "device.cuh"
 #include "internal.h"
 
@@ -9,37 +9,65 @@ namespace shp {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kFoWarps = kThreads / 32;
 
+struct FoAtom {
+  float x, y, z, beta;  // centre, beta' = 1 / (alpha log2 e)
+};
+
+struct FoWarpStage {
+  FoAtom a[SHP_MAX_ATOMS], b[SHP_MAX_ATOMS];
+  float la[SHP_MAX_ATOMS], lb[SHP_MAX_ATOMS];  // log2 w'
+};
+
+// Warp per pair: both molecules staged in shared memory with their per-atom
+// constants (fo_atom_consts; B's centres posed once), lanes over the
+// flattened atom pairs (i, j) so that every lane has work for any atom
+// counts, FP32 terms w'_i w'_j r^3 2^(-r^2 d^2) summed per lane, then over
+// the warp in FP64.
 __global__ void __launch_bounds__(kThreads) fo_kernel(SetView A, const int32_t* ia, SetView B,
                                                       const int32_t* ib, const float* poses,
                                                       int64_t n_pairs, double* out) {
-  const int64_t k = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  __shared__ FoWarpStage stage[kFoWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t k = (int64_t)blockIdx.x * kFoWarps + warp;
   if (k >= n_pairs) return;
   const int32_t xa = ia[k], xb = ib[k];
   if (xa < 0 || xa >= A.n_mol || xb < 0 || xb >= B.n_mol) {
     if (lane == 0) out[k] = __longlong_as_double(0x7ff8000000000000ll);
     return;
   }
+  FoWarpStage& S = stage[warp];
   const Pose P = make_pose(poses ? poses + 7 * k : nullptr);
   const int32_t a0 = A.off[xa], na = A.off[xa + 1] - a0;
   const int32_t b0 = B.off[xb], nb = B.off[xb + 1] - b0;
-  const float kLog2e = 1.4426950408889634f, kPi = 3.14159265358979f;
-  float acc = 0.f;
   for (int i = lane; i < na; i += 32) {
-    const float4 ai = A.atom[a0 + i];
-    const float lpi = A.aux[a0 + i].y;
-    for (int j = 0; j < nb; ++j) {
-      const float4 bj = B.atom[b0 + j];
-      const float3 c = apply_pose(P, make_float3(bj.x, bj.y, bj.z));
-      const float dx = ai.x - c.x, dy = ai.y - c.y, dz = ai.z - c.z;
-      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      const float s = ai.w + bj.w;
-      const float inv = 1.0f / s;
-      const float t = kPi * inv;
-      const float e = fmaf(-kLog2e * ai.w * bj.w * inv, d2, lpi + B.aux[b0 + j].y);
-      acc = fmaf(t * sqrtf(t), ex2_approx(e), acc);
-    }
+    const float4 c = A.atom[a0 + i];
+    float beta, lw;
+    fo_atom_consts(c.w, A.aux[a0 + i].y, beta, lw);
+    S.a[i] = FoAtom{c.x, c.y, c.z, beta};
+    S.la[i] = lw;
+  }
+  for (int j = lane; j < nb; j += 32) {
+    const float4 c = B.atom[b0 + j];
+    const float3 p = apply_pose(P, make_float3(c.x, c.y, c.z));
+    float beta, lw;
+    fo_atom_consts(c.w, B.aux[b0 + j].y, beta, lw);
+    S.b[j] = FoAtom{p.x, p.y, p.z, beta};
+    S.lb[j] = lw;
+  }
+  __syncwarp();
+  float acc = 0.f;
+  const int total = na * nb;
+  int i = lane / nb, j = lane - i * nb;
+  for (int t = lane; t < total; t += 32) {
+    const FoAtom a = S.a[i], b = S.b[j];
+    const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    const float r = rsqrtf(a.beta + b.beta), rn = -r * r;
+    const float e = fmaf(rn, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), S.la[i] + S.lb[j]);
+    acc = fmaf(-rn * r, ex2_approx(e), acc);
+    j += 32;
+    while (j >= nb) { j -= nb; ++i; }
   }
   const double tot = warp_sum((double)acc);
   if (lane == 0) out[k] = tot;
@@ -182,7 +210,7 @@ extern "C" int fo_overlap(shp_set A, const int32_t* ia, shp_set B, const int32_t
   if (n_pairs < 0) { set_error("fo_overlap: negative n_pairs"); return SHP_EINVAL; }
   if (n_pairs == 0) return SHP_OK;
   if (!ia || !ib || !out) { set_error("fo_overlap: NULL array"); return SHP_EINVAL; }
-  const int64_t blocks = (n_pairs * 32 + kThreads - 1) / kThreads;
+  const int64_t blocks = (n_pairs + kFoWarps - 1) / kFoWarps;
   fo_kernel<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(view(A), ia, view(B), ib, poseB, n_pairs,
                                                                        out);
   SHP_CUDA(cudaGetLastError());
