@@ -772,54 +772,23 @@ def adaptive_section(shp, torch, n_db: int, rank: int, lane_rate: float, tau: fl
 
     def prefilter_arm(keep: float, k_top: int = 100):
         """The cheap first-order stage of the paper's hybrid pipeline applied
-        to screening, timed end to end: closed-form first-order self-overlaps
-        and Tanimoto of every pair, each query's best `keep` fraction (exact
-        top-k), then the union stage on the kept database molecules only
-        (their self-overlaps to the same precision and their fitted
-        control-variate weights, on id-keyed streams, beside the queries' on a
-        side stream) and the adaptive union screen of the kept pairs. Every
-        stage is a library kernel. A kept pair gets exactly the numbers of the
-        unfiltered fitted-CV screen (same streams, self-overlaps and weights),
-        so recall@k (the share of each query's union top-k of the unfiltered
-        screen that survives) measures the prefilter alone."""
+        to screening (`pipeline.hybrid_screen`), timed end to end: closed-form
+        first-order self-overlaps and Tanimoto of every pair, each query's
+        best `keep` fraction (exact top-k), then the union stage on the kept
+        database molecules only (their self-overlaps to the same precision
+        and fitted control-variate weights, on id-keyed streams, beside the
+        queries' on a side stream) and the adaptive union screen of the kept
+        pairs. A kept pair gets exactly the numbers of the unfiltered
+        fitted-CV screen (same seeds and streams), checked here, so recall@k
+        (the share of each query's union top-k of the unfiltered screen that
+        survives) measures the prefilter alone."""
+        from paper_2607_20766_b300 import pipeline
         T_full = kept["T"]
-        k_keep = max(k_top, int(keep * d.n_mol))
-        ida = torch.arange(d.n_mol, dtype=torch.int32, device="cuda")
-        iqa = torch.arange(q.n_mol, dtype=torch.int32, device="cuda")
-
-        def pipeline():
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-            ev[0].record(stream)
-            fo_q = shp.fo_overlap(Sq, iqa, Sq, iqa)
-            fo_d = shp.fo_overlap(Sd, ida, Sd, ida)
-            T_fo = shp.fo_tanimoto_screen(Sq, Sd, fo_q, fo_d)
-            pq, pd = shp.fo_prefilter_select(Sq, Sd, T_fo, k_keep)
-            ids = shp.prefilter_db_ids(Sd, pd)
-            ev[1].record(stream)
-            side.wait_stream(stream)
-            with torch.cuda.stream(side):
-                sq_, sq_se_, _ = shp.self_overlaps(Sq, seed=11, n_samples=1 << 24, stream_base=0,
-                                                   target_rel_se=rel_q, round=4096, with_se=True)
-                wq_ = shp.cv_fit_weights(Sq, seed=91, n_samples=fit_samples)
-            sd_, sd_se_, _ = shp.self_overlaps(Sd, seed=11, n_samples=1 << 22, stream_base=16,
-                                               target_rel_se=self_rel_se, round=256, with_se=True, idx=ids)
-            wd_ = shp.cv_fit_weights(Sd, seed=92, n_samples=fit_samples, idx=ids, id_streams=True)
-            stream.wait_stream(side)
-            for t in (sq_, sq_se_, wq_):
-                t.record_stream(stream)
-            ev[2].record(stream)
-            res = shp.tanimoto_screen(Sq, Sd, sq_, sd_, seed=77, tau=tau, round=256, min_n=1024, cap=cap,
-                                      omega_q=wq_, omega_db=wd_, pairs=(pq, pd), self_se_q=sq_se_,
-                                      self_se_db=sd_se_)
-            ev[3].record(stream)
-            return res, pq, pd, ids, ev
-
-        pipeline()  # warm-up
-        torch.cuda.synchronize()
-        res_f, pq, pd, ids, ev = pipeline()
-        torch.cuda.synchronize()
-        t_fo, t_union_prep, t_scr = (ev[i].elapsed_time(ev[i + 1]) / 1e3 for i in range(3))
-        t_total = ev[0].elapsed_time(ev[3]) / 1e3
+        kw = dict(tau=tau, cap=cap, min_n=1024, round=256, self_rel_se=self_rel_se, fit_samples=fit_samples,
+                  seed=77, self_seed=11, self_base_q=0, self_base_db=16, fit_seed_q=91, fit_seed_db=92)
+        pipeline.hybrid_screen(Sq, Sd, keep, **kw)  # warm-up
+        res_f, t_total = timed(lambda: pipeline.hybrid_screen(Sq, Sd, keep, **kw))
+        pq, pd, ids = res_f["pairs_q"], res_f["pairs_db"], res_f["ids"]
         Tf = torch.full((q.n_mol, d.n_mol), float("-inf"), device=pq.device)
         Tf[pq.long(), pd.long()] = res_f["T"][:, 1]
         top_f = torch.topk(Tf, k_top, dim=1).indices
@@ -828,8 +797,7 @@ def adaptive_section(shp, torch, n_db: int, rank: int, lane_rate: float, tau: fl
         same = bool(torch.equal(res_f["T"], kept["T_all"].view(-1, 2)[(pq.long() * d.n_mol + pd.long())]))
         pps = npairs / t_total
         return {"keep": keep, "pairs_screened": int(pq.numel()),
-                "molecules_kept": int((ids >= 0).sum().item()), "first_order_seconds": t_fo,
-                "union_prep_seconds": t_union_prep, "screen_seconds": t_scr, "seconds": t_total,
+                "molecules_kept": int((ids >= 0).sum().item()), "seconds": t_total,
                 "pairs_per_s": pps, "speedup_vs_unfiltered_cv": pps / with_fit["pairs_per_s"],
                 "speedup_vs_p99_fixed": pps / fixed99_pps, "kept_pairs_equal_unfiltered": same,
                 f"recall_at_{k_top}": {"mean": float(np.mean(recall)), "min": float(np.min(recall))}}

@@ -144,3 +144,34 @@ def test_kept_molecules_get_the_whole_sets_values(sets):
     # id-keyed streams apply to per-molecule calls only
     with pytest.raises(shp.ShapeError):
         shp.overlap_estimate(Sq, [0], Sd, [0], seed=1, n_samples=256, flags=shp.ID_STREAMS)
+
+
+def test_hybrid_screen_keeps_the_full_screens_numbers(sets):
+    """pipeline.hybrid_screen (first-order prefilter, union stage on the kept
+    molecules only) against the unfiltered pipeline with the same seeds:
+    every kept pair has the full screen's T, SE(T) and sample count bit for
+    bit, the kept molecules' self-overlaps are the full call's, and each
+    query keeps exactly its k best first-order pairs."""
+    from paper_2607_20766_b300 import pipeline
+    q, d, Sq, Sd = sets
+    kw = dict(tau=0.01, cap=8192, min_n=512, round=256, self_rel_se=1e-2, fit_samples=1024)
+    res = pipeline.hybrid_screen(Sq, Sd, 0.1, **kw)
+    k = int(0.1 * d.n_mol)
+    assert res["pairs_q"].numel() == q.n_mol * k
+    sq, sq_se, _ = shp.self_overlaps(Sq, seed=11, n_samples=1 << 24, stream_base=0, target_rel_se=2.5e-3, round=4096,
+                                     with_se=True)
+    sd, sd_se, _ = shp.self_overlaps(Sd, seed=11, n_samples=1 << 22, stream_base=16, target_rel_se=1e-2, round=256,
+                                     with_se=True)
+    wq = shp.cv_fit_weights(Sq, seed=91, n_samples=1024)
+    wd = shp.cv_fit_weights(Sd, seed=92, n_samples=1024)
+    full = shp.tanimoto_screen(Sq, Sd, sq, sd, seed=77, tau=0.01, round=256, min_n=512, cap=8192, omega_q=wq,
+                               omega_db=wd, self_se_q=sq_se, self_se_db=sd_se)
+    flat = (res["pairs_q"].long() * d.n_mol + res["pairs_db"].long()).cpu().numpy()
+    for key in ("T", "seT", "n_used"):
+        np.testing.assert_array_equal(res[key].cpu().numpy(), full[key].cpu().numpy()[flat], err_msg=key)
+    kept = res["ids"].cpu().numpy() >= 0
+    np.testing.assert_array_equal(res["self_db"].cpu().numpy()[kept], sd.cpu().numpy()[kept])
+    T_fo = res["T_fo"].view(q.n_mol, d.n_mol)
+    kth = torch.sort(T_fo, dim=1, descending=True).values[:, k - 1]
+    got = T_fo.gather(1, res["pairs_db"].view(q.n_mol, k).long())
+    assert torch.all(got >= kth[:, None])
