@@ -175,3 +175,18 @@ def test_hybrid_screen_keeps_the_full_screens_numbers(sets):
     kth = torch.sort(T_fo, dim=1, descending=True).values[:, k - 1]
     got = T_fo.gather(1, res["pairs_db"].view(q.n_mol, k).long())
     assert torch.all(got >= kth[:, None])
+
+
+def test_fo_tanimoto_query_groups():
+    """37 queries: two full groups of 16 per block and a ragged third, odd and
+    even atom counts (the packed pairs' padding), against the oracle."""
+    q = synth.principal_axes(synth.generate(61, synth.counts_uniform(61, 37, 7, 48)))
+    d = synth.principal_axes(synth.generate(62, synth.counts_heavy(62, 200)))
+    Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
+    kq, kd = np.arange(q.n_mol), np.arange(d.n_mol)
+    fq, fd = O.fo_overlap(q, kq, q, kq), O.fo_overlap(d, kd, d, kd)
+    T = shp.fo_tanimoto_screen(Sq, Sd, torch.tensor(fq), torch.tensor(fd)).cpu().numpy()
+    iq, idd = np.meshgrid(kq, kd, indexing="ij")
+    O_ = O.fo_overlap(q, iq.ravel(), d, idd.ravel())
+    np.testing.assert_allclose(T, O_ / (fq[iq.ravel()] + fd[idd.ravel()] - O_), rtol=2e-5)
+    assert np.any(q.counts % 2 == 1) and np.any(q.counts % 2 == 0)
