@@ -573,6 +573,21 @@ int mlp_adam(float* params, float* m, float* v, const float* grad, int64_t n_par
              float lr, float beta1, float beta2, float eps, void* stream);
 
 /*
+ * One epoch of minibatch training in one call: for each minibatch of
+ * `batch` rows of perm (the last one may be shorter), mlp_loss_grad on those
+ * rows, then mlp_adam with step step0 + 1, step0 + 2, ... The launches are
+ * those of the step-by-step calls, in the same order, so the parameters and
+ * moments end exactly as theirs; the host loop runs inside the library.
+ *   params, m, v [SHP_MLP_PARAMS] float device, updated in place;
+ *   x [*][SHP_MLP_IN], target [*] float device; perm [n] int32 device rows;
+ *   losses [ceil(n / batch)] double device: each minibatch's mean squared error.
+ * Scratch (partial gradients, the gradient) is stream-ordered library memory.
+ */
+int mlp_train_epoch(float* params, float* m, float* v, const float* x, const float* target, const int32_t* perm,
+                    int64_t n, int64_t batch, int64_t step0, float lr, float beta1, float beta2, float eps,
+                    double* losses, void* stream);
+
+/*
  * Host copy of each molecule's principal frame ([n_mol][12] float: the
  * Gaussian-volume-weighted centroid, then the 3x3 axis matrix row-major with
  * the axes as columns, sorted by decreasing second moment, the first two

@@ -11,7 +11,7 @@ from ._binding import (ANTITHETIC, EXPORTS, ID_STREAMS, LIB_PATH, MAX_ATOMS, OBJ
                        ShapeError, ShapeSet, fo_overlap, load_library, overlap_estimate, screen_config,
                        fail_next_allocations, eval_probe, fo_tanimoto_screen, fo_prefilter_select, prefilter_db_ids, screen_variant_info, screen_variants, self_overlaps, shape_set_load, tanimoto_screen, tanimoto_screen_tune,
                        union_volume_estimate, union_attributions, union_volume_cv, union_self_estimate, cv_features, cv_fit_weights, mlp_forward,
-                       mlp_loss_grad, mlp_adam, MLP_PARAMS)
+                       mlp_loss_grad, mlp_adam, mlp_train_epoch, MLP_PARAMS)
 from .graph import StepGraph
 from . import pipeline
 
@@ -21,4 +21,4 @@ __all__ = ["ANTITHETIC", "EXPORTS", "ID_STREAMS", "LIB_PATH", "MAX_ATOMS", "OBJ_
            "ShapeError", "ShapeSet", "fo_overlap", "load_library", "overlap_estimate", "screen_config",
            "fail_next_allocations", "eval_probe", "fo_tanimoto_screen", "fo_prefilter_select", "prefilter_db_ids", "screen_variant_info", "screen_variants", "self_overlaps", "shape_set_load", "tanimoto_screen", "tanimoto_screen_tune",
            "union_volume_estimate", "union_attributions", "union_volume_cv", "union_self_estimate", "cv_features", "cv_fit_weights", "mlp_forward",
-           "mlp_loss_grad", "mlp_adam", "MLP_PARAMS", "StepGraph", "pipeline"]
+           "mlp_loss_grad", "mlp_adam", "mlp_train_epoch", "MLP_PARAMS", "StepGraph", "pipeline"]

@@ -30,7 +30,7 @@ EXPORTS = ("shp_last_error", "shp_version", "shp_fail_next_allocations", "shape_
            "overlap_pose_grad", "align_rigid", "shape_set_frames", "union_attributions", "union_volume_cv",
            "cv_features", "mlp_forward", "mlp_loss_grad", "mlp_adam", "mlp_loss_grad_noalloc", "cv_fit_weights",
            "union_self_estimate", "shp_eval_probe", "fo_tanimoto_screen",
-           "fo_prefilter_select", "prefilter_db_ids")
+           "fo_prefilter_select", "prefilter_db_ids", "mlp_train_epoch")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 33, 64, 6401
 OBJ_FO, OBJ_UNION, OBJ_FO_CLOSED = 0, 1, 2
 
@@ -107,6 +107,8 @@ def load_library():
         "mlp_loss_grad_noalloc": [_P, _P, _P, _P, ctypes.c_int64, _P, _P, _P],
         "mlp_adam": [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                      ctypes.c_float, _P],
+        "mlp_train_epoch": [_P, _P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_float,
+                            ctypes.c_float, ctypes.c_float, ctypes.c_float, _P, _P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -670,3 +672,17 @@ def mlp_adam(params, m, v, grad, step: int, lr: float, beta1: float = 0.9, beta2
              eps: float = 1e-8, stream=None):
     _check(load_library().mlp_adam(_dptr(params), _dptr(m), _dptr(v), _dptr(grad), params.numel(), step, lr, beta1,
                                    beta2, eps, _stream(stream)))
+
+
+@_on_stream
+def mlp_train_epoch(params, m, v, x, target, perm, batch: int, step0: int, lr: float, beta1: float = 0.9,
+                    beta2: float = 0.999, eps: float = 1e-8, stream=None) -> torch.Tensor:
+    """One epoch of minibatches over perm (mlp_loss_grad then mlp_adam per
+    minibatch, steps step0 + 1 ...), the loop inside the library; returns
+    each minibatch's mean squared error ([ceil(n / batch)] float64 device)."""
+    perm = _device_i32(perm, params.device)
+    n = perm.numel()
+    losses = torch.empty((n + batch - 1) // batch, dtype=torch.float64, device=params.device)
+    _check(load_library().mlp_train_epoch(_dptr(params), _dptr(m), _dptr(v), _dptr(x), _dptr(target), _dptr(perm), n,
+                                          batch, step0, lr, beta1, beta2, eps, _dptr(losses), _stream(stream)))
+    return losses

@@ -461,3 +461,36 @@ extern "C" int mlp_adam(float* params, float* m, float* v, const float* grad, in
   SHP_CUDA(cudaGetLastError());
   return SHP_OK;
 }
+
+extern "C" int mlp_train_epoch(float* params, float* m, float* v, const float* x, const float* target,
+                               const int32_t* perm, int64_t n, int64_t batch, int64_t step0, float lr, float beta1,
+                               float beta2, float eps, double* losses, void* stream) {
+  clear_error();
+  if (!params || !m || !v || !x || !target || !perm || !losses || n <= 0 || batch <= 0 || step0 < 0) {
+    set_error("mlp_train_epoch: bad arguments");
+    return SHP_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t b = batch < n ? batch : n;
+  float* part = nullptr;
+  float* grad = nullptr;
+  cudaError_t e = dev_alloc((void**)&part, sizeof(float) * (size_t)((b + 63) / 64) * (kP + 1), st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&grad, sizeof(float) * kP, st);
+  int rc = e == cudaSuccess ? SHP_OK : cuda_fail(e, "mlp_train_epoch: scratch");
+  // the same launches, in the same order, as mlp_loss_grad then mlp_adam per
+  // minibatch: the result is that of the step-by-step calls
+  int64_t step = step0;
+  for (int64_t s0 = 0; s0 < n && rc == SHP_OK; s0 += b) {
+    const int64_t nb = n - s0 < b ? n - s0 : b;
+    rc = mlp_loss_grad_into(params, x, target, perm + s0, nb, part, grad, losses + s0 / b, st);
+    if (rc) break;
+    ++step;
+    const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
+    adam_kernel<<<(unsigned)((kP + 255) / 256), 256, 0, st>>>(params, m, v, grad, kP, lr, beta1, beta2, eps, c1, c2);
+    const cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) rc = cuda_fail(le, "mlp_train_epoch: adam");
+  }
+  for (void* p : {(void*)part, (void*)grad})
+    if (p) cudaFreeAsync(p, st);
+  return rc;
+}

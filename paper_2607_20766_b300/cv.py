@@ -50,21 +50,13 @@ class CrowdingNet:
         targets = targets.to(torch.float32).contiguous()
         n = feats.shape[0]
         g = torch.Generator(device=feats.device).manual_seed(seed)
-        grad = torch.empty(B.MLP_PARAMS, dtype=torch.float32, device=feats.device)
-        loss = torch.empty(1, dtype=torch.float64, device=feats.device)
         history = []
         for _ in range(epochs):
             perm = torch.randperm(n, generator=g, device=feats.device).to(torch.int32)
-            tot = torch.zeros(1, dtype=torch.float64, device=feats.device)
-            nb = 0
-            for s in range(0, n, batch):
-                rows = perm[s:s + batch]
-                B.mlp_loss_grad(self.params, feats, targets, rows, out=(grad, loss))
-                self.step += 1
-                B.mlp_adam(self.params, self.m, self.v, grad, self.step, lr)
-                tot += loss
-                nb += 1
-            history.append(float(tot.item()) / nb)
+            # the epoch's minibatch loop (loss/gradient, Adam) runs inside the library
+            losses = B.mlp_train_epoch(self.params, self.m, self.v, feats, targets, perm, batch, self.step, lr)
+            self.step += losses.numel()
+            history.append(float(losses.mean().item()))
         return history
 
 

@@ -89,6 +89,28 @@ def test_mlp_forward_and_gradients_match_oracle():
     assert np.linalg.norm(g_gpu - g) <= 1e-4 * np.linalg.norm(g)
 
 
+def test_train_epoch_equals_step_by_step_calls():
+    """mlp_train_epoch runs an epoch's minibatches (the last one shorter)
+    inside the library: the same parameters, moments and per-minibatch losses
+    as mlp_loss_grad then mlp_adam called per minibatch, bit for bit."""
+    rng = np.random.default_rng(4)
+    X = torch.tensor(rng.uniform(0, 2.5, (3000, M.N_IN)), dtype=torch.float32, device="cuda")
+    t = torch.tensor(rng.uniform(0.2, 1.0, 3000), dtype=torch.float32, device="cuda")
+    perm = torch.tensor(rng.permutation(3000)[:2900], dtype=torch.int32, device="cuda")
+    p0 = cv.init_params(3)
+    a = [p0.clone(), torch.zeros_like(p0), torch.zeros_like(p0)]
+    b = [p0.clone(), torch.zeros_like(p0), torch.zeros_like(p0)]
+    losses = shp.mlp_train_epoch(a[0], a[1], a[2], X, t, perm, 512, 5, 3e-3).cpu().numpy()
+    ref = []
+    for k, s0 in enumerate(range(0, 2900, 512)):
+        loss, grad = shp.mlp_loss_grad(b[0], X, t, perm[s0:s0 + 512])
+        shp.mlp_adam(b[0], b[1], b[2], grad, 5 + k + 1, 3e-3)
+        ref.append(loss.item())
+    for u, w in zip(a, b):
+        assert torch.equal(u, w)
+    np.testing.assert_array_equal(losses, np.array(ref))
+
+
 def test_adam_step():
     rng = np.random.default_rng(2)
     p = rng.normal(size=100).astype(np.float32)
