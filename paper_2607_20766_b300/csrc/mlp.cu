@@ -24,8 +24,11 @@ __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__floa
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.7071067811865476f)); }
 
-__device__ __forceinline__ float gelu_grad(float z) {
-  return 0.5f * (1.f + erff(z * 0.7071067811865476f)) + z * 0.3989422804014327f * expf(-0.5f * z * z);
+// gelu(z) = z Phi(z) and gelu'(z) = Phi(z) + z phi(z) from one erf.
+__device__ __forceinline__ void gelu_both(float z, float& h, float& d) {
+  const float c = 1.f + erff(z * 0.7071067811865476f);
+  h = 0.5f * z * c;
+  d = 0.5f * c + z * 0.3989422804014327f * expf(-0.5f * z * z);
 }
 
 __device__ void load_weights(float* W, const float* params) {
@@ -220,8 +223,7 @@ __global__ void __launch_bounds__(kTrThreads) train_kernel(const float* params, 
       float h[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        h[c] = gelu(z[r][c]);
-        d1g[r][c] = gelu_grad(z[r][c]);
+        gelu_both(z[r][c], h[c], d1g[r][c]);
         s.AT[4 * th + c][2 * ta + r] = h[c];
       }
       *reinterpret_cast<float4*>(&s.H1N[2 * ta + r][4 * th]) = make_float4(h[0], h[1], h[2], h[3]);
@@ -245,8 +247,7 @@ __global__ void __launch_bounds__(kTrThreads) train_kernel(const float* params, 
       float part_y = 0.f;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        h2[r][c] = gelu(z[r][c]);
-        d2[r][c] = gelu_grad(z[r][c]);
+        gelu_both(z[r][c], h2[r][c], d2[r][c]);
         part_y = fmaf(s.w3[4 * th + c], h2[r][c], part_y);
       }
       // the 16 threads of an atom pair are one half-warp
@@ -372,13 +373,27 @@ int train_launch(const float* params, const float* x, const float* target, const
 }
 
 // grad[e] = sum over blocks of part[b][e] (fixed order); loss = SSE / n.
-__global__ void reduce_kernel(const float* part, int64_t n_blocks, int64_t n, float* grad, double* loss) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e > kP) return;
+// Blocks of 32 columns x 8 row groups: row group r sums rows r, r + 8, ...
+// in FP64, then the 8 group sums are added in order (a fixed order for every
+// run).
+constexpr int kRedCols = 32, kRedGroups = 8;
+
+__global__ void __launch_bounds__(kRedCols * kRedGroups) reduce_kernel(const float* part, int64_t n_blocks, int64_t n,
+                                                                      float* grad, double* loss) {
+  __shared__ double sums[kRedGroups][kRedCols];
+  const int c = threadIdx.x % kRedCols, r = threadIdx.x / kRedCols;
+  const int e = blockIdx.x * kRedCols + c;
   double acc = 0.0;
-  for (int64_t b = 0; b < n_blocks; ++b) acc += (double)part[b * (kP + 1) + e];
-  if (e < kP) grad[e] = (float)acc;
-  else *loss = acc / (double)n;
+  if (e <= kP)
+    for (int64_t b = r; b < n_blocks; b += kRedGroups) acc += (double)part[b * (kP + 1) + e];
+  sums[r][c] = acc;
+  __syncthreads();
+  if (r == 0 && e <= kP) {
+    double t = 0.0;
+    for (int g = 0; g < kRedGroups; ++g) t += sums[g][c];
+    if (e < kP) grad[e] = (float)t;
+    else *loss = t / (double)n;
+  }
 }
 
 __global__ void adam_kernel(float* p, float* m, float* v, const float* g, int64_t n, float lr, float b1, float b2,
@@ -444,7 +459,7 @@ int mlp_loss_grad_into(const float* params, const float* x, const float* target,
   int64_t blocks = 0;
   const int rc = train_launch(params, x, target, rows, n, part, &blocks, st);
   if (rc) return rc;
-  reduce_kernel<<<(kP + 1 + 255) / 256, 256, 0, st>>>(part, blocks, n, grad, loss);
+  reduce_kernel<<<(kP + 1 + kRedCols - 1) / kRedCols, kRedCols * kRedGroups, 0, st>>>(part, blocks, n, grad, loss);
   SHP_CUDA(cudaGetLastError());
   return SHP_OK;
 }
