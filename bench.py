@@ -866,7 +866,15 @@ def cv_section(shp, torch, n_train: int, n_held: int, rank: int, lane_rate: floa
 
     (feats, targets), t_data = timed(lambda: cv.attributions_and_features(St, seed=1, M=256))
     net = cv.CrowdingNet(seed=0)
-    hist, t_train = timed(lambda: net.fit(feats, targets, epochs=8, batch=65536, lr=3e-3))
+    epochs = 8
+    hist, t_train = timed(lambda: net.fit(feats, targets, epochs=epochs, batch=65536, lr=3e-3))
+    # multiply-adds per atom and step: forward 33x64 + 64x64 + 64, the hidden
+    # layer's back-propagation 64x64, weight gradients 64x33 + 64x64 + 64
+    fma_per_atom = 2 * 33 * 64 + 3 * 64 * 64 + 2 * 64
+    roof_train = alu_roofline(lane_rate, float(feats.shape[0]) * epochs, t_train, fma_per_atom,
+                              "G atom-steps/s", "train_kernel (loss, back-propagation, weight gradients)",
+                              f"{fma_per_atom} FP32 multiply-adds per atom and step (forward, back-propagation "
+                              f"and weight gradients of the 33-64-64-1 network)")
     fh = shp.cv_features(Sh)
     om, t_pred = timed(lambda: net.predict(fh))
     cap = 1 << 21
@@ -885,7 +893,8 @@ def cv_section(shp, torch, n_train: int, n_held: int, rank: int, lane_rate: floa
     return net, {
         "workload": f"learned control variate: train on {n_train} molecules (18-60 atoms, union attributions, 256 "
                     f"samples/atom), union volume of {n_held} held-out molecules to relative SE <= {target}",
-        "train_seconds": t_train, "targets_seconds": t_data, "predict_seconds": t_pred,
+        "train_seconds": t_train, "train_roofline": roof_train, "targets_seconds": t_data,
+        "predict_seconds": t_pred,
         "loss_first_last": [hist[0], hist[-1]],
         "plain": {"mean_samples": float(n_pl.mean()), "seconds": t_pl, "molecules_per_s": n_held / t_pl,
                   "roofline": roof_pl},
