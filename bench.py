@@ -865,6 +865,11 @@ def cv_section(shp, torch, n_train: int, n_held: int, rank: int, lane_rate: floa
         return out, e0.elapsed_time(e1) / 1e3
 
     (feats, targets), t_data = timed(lambda: cv.attributions_and_features(St, seed=1, M=256))
+    # warm-up on a slice with a throw-away network: the first on-device
+    # randperm of a process loads torch's sort kernels, on a fresh machine
+    # from disk, which must not land in the timed training
+    cv.CrowdingNet(seed=1).fit(feats[:8192], targets[:8192], epochs=1, batch=4096, lr=3e-3)
+    torch.cuda.synchronize()
     net = cv.CrowdingNet(seed=0)
     epochs = 8
     hist, t_train = timed(lambda: net.fit(feats, targets, epochs=epochs, batch=65536, lr=3e-3))
@@ -878,7 +883,8 @@ def cv_section(shp, torch, n_train: int, n_held: int, rank: int, lane_rate: floa
     fh = shp.cv_features(Sh)
     om, t_pred = timed(lambda: net.predict(fh))
     cap = 1 << 21
-    shp.union_volume_cv(Sh, None, om, seed=5, n_samples=cap, target_rel_se=target)  # warm-up
+    for w in (om, None):  # warm-up of both kernels
+        shp.union_volume_cv(Sh, None, w, seed=5, n_samples=cap, target_rel_se=target)
     (v_cv, s_cv, n_cv), t_cv = timed(lambda: shp.union_volume_cv(Sh, None, om, seed=5, n_samples=cap,
                                                                  target_rel_se=target))
     (v_pl, s_pl, n_pl), t_pl = timed(lambda: shp.union_volume_cv(Sh, None, None, seed=5, n_samples=cap,
