@@ -62,3 +62,22 @@ def test_bench_json_line_small():
     assert a["self_overlaps"]["seconds"] > 0
     assert a["with_control_variate"]["pairs_per_s"] > 0 and a["with_fitted_control_variate"]["pairs_per_s"] > 0
     assert line["alignment"]["frac_improved"] > 0.5
+    # every kernel family's roofline is there and plausible
+    for arm in ("union_crn", "hybrid_fo_closed"):
+        assert 0.0 < line["alignment"][arm]["roofline"]["frac"] < 1.5
+    assert 0.0 < line["control_variate"]["train_roofline"]["frac"] < 1.5
+    assert 0.0 < a["roofline"]["frac"] < 1.5 and 0.0 < a["first_order_kernel"]["roofline"]["frac"] < 1.5
+    for pf in a["first_order_prefilter"]:
+        assert pf["kept_pairs_equal_unfiltered"] and pf["molecules_kept"] > 0
+
+
+@pytest.mark.parametrize("case, keys", [("align", ("union_crn_ms", "fo_closed_ms")),
+                                        ("prefilter", ("fo_tanimoto_ms", "select_ms"))])
+def test_profile_cases(case, keys):
+    """The small standalone cases that the profiler captures run and report
+    their timings (one JSON line)."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--profile-case", case], cwd=ROOT,
+                         capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["case"] == case and all(line[k] > 0 for k in keys)
