@@ -115,6 +115,23 @@ def test_closed_form_objective_matches_analytic_gradient(mols):
         assert np.linalg.norm(grad[k] - g) <= 1e-4 * np.linalg.norm(g) + 1e-7
 
 
+@pytest.mark.parametrize("iq", [3, 4])
+def test_closed_form_objective_large_queries(mols, iq):
+    """The closed-form objective with queries of 45 and 64 atoms (lanes over
+    the query's atoms take two passes) against the oracle's analytic
+    first-order value and gradient."""
+    q, b, Sq, Sb = mols
+    rng = np.random.default_rng(20 + iq)
+    ib = np.arange(b.n_mol, dtype=np.int32)
+    pose = _poses(len(ib), rng)
+    value, grad = shp.overlap_pose_grad(Sb, iq, None, Sb, ib, pose, objective=shp.OBJ_FO_CLOSED)
+    value, grad = value.cpu().numpy(), grad.cpu().numpy()
+    for k in range(len(ib)):
+        F, g = O.fo_pose_grad(b, iq, b, int(ib[k]), pose[k].astype(np.float64))
+        assert value[k] == pytest.approx(F, rel=1e-5, abs=1e-9)
+        assert np.linalg.norm(grad[k] - g) <= 1e-4 * np.linalg.norm(g) + 1e-7
+
+
 def test_autograd_wrapper(mols):
     q, b, Sq, Sb = mols
     pts = shp.align_crn_points(Sq, 0, seed=1, n=512)

@@ -179,9 +179,12 @@ def test_hybrid_screen_keeps_the_full_screens_numbers(sets):
 
 def test_fo_tanimoto_query_groups():
     """37 queries: two full groups of 16 per block and a ragged third, odd and
-    even atom counts (the packed pairs' padding), against the oracle."""
-    q = synth.principal_axes(synth.generate(61, synth.counts_uniform(61, 37, 7, 48)))
-    d = synth.principal_axes(synth.generate(62, synth.counts_heavy(62, 200)))
+    even atom counts (the packed pairs' padding) from 1 to 64 atoms on both
+    sides, against the oracle."""
+    qc = np.concatenate([[1, 64, 63, 2], synth.counts_uniform(61, 33, 7, 48)]).astype(np.int32)
+    dc = np.concatenate([synth.counts_heavy(62, 200), [1, 64, 2, 63]]).astype(np.int32)
+    q = synth.principal_axes(synth.generate(61, qc))
+    d = synth.principal_axes(synth.generate(62, dc))
     Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)
     kq, kd = np.arange(q.n_mol), np.arange(d.n_mol)
     fq, fd = O.fo_overlap(q, kq, q, kq), O.fo_overlap(d, kd, d, kd)
