@@ -914,7 +914,7 @@ def cv_section(shp, torch, n_train: int, n_held: int, rank: int, lane_rate: floa
 def align_section(shp, torch, n_db: int, rank: int, lane_rate: float, n_copies: int = 512):
     """Multi-start rigid alignment: 1 query (30 atoms) x n_db molecules
     (18-60 atoms), 8 starts, 100 Adam steps with 1024 CRN points on the union
-    objective, and the paper's hybrid pipeline (align on the closed-form
+    objective (plain, and in antithetic pairs), and the paper's hybrid pipeline (align on the closed-form
     first-order overlap, score on the union); final union Tanimoto with 4096
     samples per direction. Recovery of known superpositions: n_copies rigidly
     displaced copies of the query (random rotation, 15 A shift), each
@@ -943,6 +943,7 @@ def align_section(shp, torch, n_db: int, rank: int, lane_rate: float, n_copies: 
         return out, e0.elapsed_time(e1) / 1e3
 
     arms = {"union_crn": dict(objective=shp.OBJ_UNION, n_crn=1024),
+            "union_crn_antithetic": dict(objective=shp.OBJ_UNION, n_crn=1024, antithetic=True),
             "hybrid_fo_closed": dict(objective=shp.OBJ_FO_CLOSED, n_crn=1024)}
     pose_id = torch.tensor([[1, 0, 0, 0, 0, 0, 0]], dtype=torch.float32, device="cuda").expand(n_db, 7).contiguous()
     est, _ = shp.overlap_estimate(Sq, torch.zeros(n_db, dtype=torch.int32, device="cuda"), Sd, ib, seed=3,
@@ -966,7 +967,8 @@ def align_section(shp, torch, n_db: int, rank: int, lane_rate: float, n_copies: 
     sc = shp.self_overlaps(Sc, seed=2, n_samples=8192, stream_base=1)
     ic = torch.arange(n_copies, dtype=torch.int32, device="cuda")
     out = {"workload": f"multi-start alignment: 1 query (30 atoms) x {n_db} molecules, 8 starts x 100 Adam steps, "
-                       f"1024 CRN points (union objective) or the closed-form first-order overlap (hybrid); "
+                       f"1024 CRN points (union objective; plain or in antithetic pairs) or the closed-form "
+                       f"first-order overlap (hybrid); "
                        f"recovery of {n_copies} rigidly displaced copies of the query",
            "mean_T_prealigned": float(T0.mean())}
     for name, kw in arms.items():

@@ -370,6 +370,8 @@ int tanimoto_screen_tune(shp_set Q, shp_set D, const shp_screen* cfg, const doub
  * Common random numbers: mc->n_samples points drawn from Q[iq]'s mixture
  * (tag SHP_TAG_CRN, stream mc->stream_base, the usual sample layout) with
  * their union weights: points [n][4] float device = (x, y, z, u_Q/m_Q).
+ * mc->flags: 0 or SHP_ANTITHETIC (each odd point the reflection of the even
+ * one about its component centre, Sec. IS estimator's antithetic pairs).
  */
 int align_crn_points(shp_set Q, int32_t iq, const shp_mc* mc, float* points, void* stream);
 
@@ -401,6 +403,8 @@ typedef struct {
   float lr, lr_t;     /* Adam step sizes of the quaternion and of the translation   */
   float beta1, beta2, eps;
   uint32_t n_score;   /* samples per direction for the final union Tanimoto          */
+  uint32_t crn_flags; /* 0 or SHP_ANTITHETIC: the CRN points in antithetic pairs
+                         (align_crn_points), the same number of points            */
 } shp_align;
 
 /*

@@ -69,7 +69,7 @@ _SIGS = {
                  ctypes.c_int],
     "orc_tanimoto_pairs": [_P, _P, _P, _P, _P, ctypes.c_int64, _P, _P, _P, _P, ctypes.c_uint64,
                            ctypes.c_uint32, ctypes.c_uint32, _P, _P, _P, _P, _P, _P, ctypes.c_int],
-    "orc_crn_points": [_P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P],
+    "orc_crn_points": [_P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, _P],
     "orc_pose_objective": [ctypes.c_double, _P, ctypes.c_uint32, _P, ctypes.c_int32, _P, ctypes.c_int, _P],
     "orc_pose_grad_fd": [ctypes.c_double, _P, ctypes.c_uint32, _P, ctypes.c_int32, _P, ctypes.c_int,
                          ctypes.c_double, _P, _P],
@@ -314,11 +314,13 @@ TAG_CRN = 3
 OBJ_FO, OBJ_UNION = 0, 1
 
 
-def crn_points(Q, iq, seed, stream, n, c_alpha=2.41798793):
-    """[n, 4] float64: CRN points drawn from Q[iq] (tag 3) and their union weights u/m."""
+def crn_points(Q, iq, seed, stream, n, c_alpha=2.41798793, antithetic=False):
+    """[n, 4] float64: CRN points drawn from Q[iq] (tag 3) and their union
+    weights u/m; antithetic: each odd point reflects the even one about its
+    component centre."""
     s = _oset(Q, c_alpha)
     pts = np.empty((n, 4))
-    _check(lib().orc_crn_points(s.ref, iq, seed, stream, n, pts.ctypes.data), "crn_points")
+    _check(lib().orc_crn_points(s.ref, iq, seed, stream, n, int(antithetic), pts.ctypes.data), "crn_points")
     return pts
 
 

@@ -167,6 +167,6 @@ def adam(Q, iq, B, ib, pose0, steps, objective=OBJ_UNION, points=None, lr=0.02, 
     return np.array(traj)
 
 
-def crn(Q, iq, seed, stream, n):
+def crn(Q, iq, seed, stream, n, antithetic=False):
     """The CRN points of the alignment (tag 3) with their union weights."""
-    return crn_points(Q, iq, seed=seed, stream=stream, n=n)
+    return crn_points(Q, iq, seed=seed, stream=stream, n=n, antithetic=antithetic)

@@ -793,17 +793,19 @@ int orc_tanimoto_pairs(const orc_set* Q, const int32_t* iq, const orc_set* D, co
 
 /*
  * Common random numbers: n points drawn once from the query's mixture
- * (tag 3, the usual sample layout) with their union weights w = u/m.
- * points[n][4] = (x, y, z, w).
+ * (tag 3, the usual sample layout; antithetic: each odd point the reflection
+ * of the even one about its component centre) with their union weights
+ * w = u/m. points[n][4] = (x, y, z, w).
  */
-int orc_crn_points(const orc_set* S, int32_t idx, uint64_t seed, uint64_t stream, uint32_t n, double* points) {
+int orc_crn_points(const orc_set* S, int32_t idx, uint64_t seed, uint64_t stream, uint32_t n, int antithetic,
+                   double* points) {
   orc_mol m;
   int rc = load_mol(S, idx, NULL, &m);
   if (rc) return rc;
   for (uint32_t k = 0; k < n; k += 2) {
     double r[2][3];
     int i0, i1;
-    draw_pair(&m, seed, stream, 3u, k / 2, 0, r[0], r[1], &i0, &i1);
+    draw_pair(&m, seed, stream, 3u, k / 2, antithetic, r[0], r[1], &i0, &i1);
     for (int j = 0; j < 2 && k + j < n; ++j) {
       double ms, u;
       occupancy(&m, r[j], &ms, &u);

@@ -55,7 +55,8 @@ class ShpAlign(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("stream", ctypes.c_uint64), ("starts", ctypes.c_uint32),
                 ("steps", ctypes.c_uint32), ("n_crn", ctypes.c_uint32), ("objective", ctypes.c_uint32),
                 ("lr", ctypes.c_float), ("lr_t", ctypes.c_float), ("beta1", ctypes.c_float),
-                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("n_score", ctypes.c_uint32)]
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("n_score", ctypes.c_uint32),
+                ("crn_flags", ctypes.c_uint32)]
 
 
 _lib = None
@@ -487,10 +488,12 @@ def self_overlaps(S: ShapeSet, seed: int, n_samples: int, stream_base: int = 0, 
 # ---------------------------------------------------------------- alignment
 
 @_on_stream
-def align_crn_points(Q: ShapeSet, iq: int, seed: int, n: int, stream_base: int = 0, stream=None):
-    """[n, 4] float32 device tensor: CRN points of Q[iq] and their union weights."""
+def align_crn_points(Q: ShapeSet, iq: int, seed: int, n: int, stream_base: int = 0, stream=None,
+                     antithetic: bool = False):
+    """[n, 4] float32 device tensor: CRN points of Q[iq] and their union
+    weights (antithetic: in pairs reflected about their component centre)."""
     pts = torch.empty((n, 4), dtype=torch.float32, device=Q.device)
-    mc = ShpMC(seed, stream_base, n, 0)
+    mc = ShpMC(seed, stream_base, n, ANTITHETIC if antithetic else 0)
     _check(load_library().align_crn_points(Q.handle, iq, ctypes.byref(mc), _dptr(pts), _stream(stream)))
     return pts
 
@@ -540,14 +543,16 @@ def pose_overlap(pose, Q: ShapeSet, iq: int, points: torch.Tensor, B: ShapeSet, 
 def align_rigid(Q: ShapeSet, iq: int, B: ShapeSet, ib, self_q: torch.Tensor, self_db: torch.Tensor, seed: int = 0,
                 starts: int = 8, steps: int = 100, n_crn: int = 1024, objective: int = OBJ_UNION, lr: float = 0.02,
                 lr_t: float = 0.05, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, n_score: int = 4096,
-                stream_base: int = 0, with_starts: bool = False, stream=None):
+                stream_base: int = 0, with_starts: bool = False, stream=None, antithetic: bool = False):
     """Multi-start Adam alignment of B[ib[k]] onto Q[iq]. Returns dict pose
     ([n, 7]), T ([n]) and, with with_starts, T_starts ([n, starts]) and
-    pose_starts ([n, starts, 7], every start's final raw pose)."""
+    pose_starts ([n, starts, 7], every start's final raw pose). antithetic:
+    the CRN points in antithetic pairs (same n_crn)."""
     dev = Q.device
     ib = _device_i32(ib, dev)
     n = ib.numel()
-    cfg = ShpAlign(seed, stream_base, starts, steps, n_crn, objective, lr, lr_t, beta1, beta2, eps, n_score)
+    cfg = ShpAlign(seed, stream_base, starts, steps, n_crn, objective, lr, lr_t, beta1, beta2, eps, n_score,
+                   ANTITHETIC if antithetic else 0)
     out = dict(pose=torch.empty((n, 7), dtype=torch.float32, device=dev),
                T=torch.empty(n, dtype=torch.float32, device=dev))
     if with_starts:

@@ -367,7 +367,10 @@ __device__ void pose_gradient(const float pose[7], const float acc[7], float sca
   grad[6] = scale * acc[3];
 }
 
-__global__ void crn_points_kernel(SetView Q, int32_t iq, Key key, uint64_t stream, uint32_t n, float4* out) {
+// Points 2s, 2s + 1 of the usual sample layout; antithetic: 2s + 1 is the
+// reflection of 2s about its component centre (same pick, negated normals).
+__global__ void crn_points_kernel(SetView Q, int32_t iq, Key key, uint64_t stream, uint32_t n, bool anti,
+                                  float4* out) {
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;  // sample pair
   if (2u * s >= n) return;
   const int32_t a0 = Q.off[iq], na = Q.off[iq + 1] - a0;
@@ -378,8 +381,8 @@ __global__ void crn_points_kernel(SetView Q, int32_t iq, Key key, uint64_t strea
   box_muller(w0.z, w0.w, z[0], z[1]);
   box_muller(w1.x, w1.y, z[2], z[3]);
   box_muller(w1.z, w1.w, z[4], z[5]);
-  const uint32_t words[2] = {w0.x, w0.y};
-  const float zz[2][3] = {{z[0], z[1], z[4]}, {z[2], z[3], z[5]}};
+  const uint32_t words[2] = {w0.x, anti ? w0.x : w0.y};
+  const float zz[2][3] = {{z[0], z[1], z[4]}, {anti ? -z[0] : z[2], anti ? -z[1] : z[3], anti ? -z[4] : z[5]}};
   const float kLog2e = 1.4426950408889634f;
   for (int t = 0; t < 2; ++t) {
     if (2u * s + t >= n) break;
@@ -624,11 +627,14 @@ extern "C" int align_crn_points(shp_set Q, int32_t iq, const shp_mc* mc, float* 
   clear_error();
   int rc = check_points_args(Q, iq, "align_crn_points");
   if (rc) return rc;
-  if (!mc || mc->n_samples < 1 || !points) { set_error("align_crn_points: bad arguments"); return SHP_EINVAL; }
+  if (!mc || mc->n_samples < 1 || !points || (mc->flags & ~SHP_ANTITHETIC)) {
+    set_error("align_crn_points: bad arguments (flags: SHP_ANTITHETIC only)");
+    return SHP_EINVAL;
+  }
   const uint32_t pairs = (mc->n_samples + 1u) / 2u;
   crn_points_kernel<<<(pairs + 127u) / 128u, 128, 0, (cudaStream_t)stream>>>(
       view(Q), iq, Key{(uint32_t)mc->seed, (uint32_t)(mc->seed >> 32)}, mc->stream_base, mc->n_samples,
-      reinterpret_cast<float4*>(points));
+      (mc->flags & SHP_ANTITHETIC) != 0, reinterpret_cast<float4*>(points));
   SHP_CUDA(cudaGetLastError());
   return SHP_OK;
 }
@@ -677,6 +683,7 @@ extern "C" int align_rigid(shp_set Q, int32_t iq, shp_set B, const int32_t* ib, 
   if (rc) return rc;
   if (!B || !cfg || n_pairs < 0) { set_error("align_rigid: bad arguments"); return SHP_EINVAL; }
   if (cfg->starts < 1 || cfg->starts > 64 || cfg->n_crn < 2 || cfg->n_score < 2 || cfg->objective > SHP_OBJ_FO_CLOSED ||
+      (cfg->crn_flags & ~SHP_ANTITHETIC) ||
       !(cfg->lr > 0.f) || !(cfg->lr_t > 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
       !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) || !(cfg->eps > 0.f)) {
     set_error("align_rigid: invalid configuration");
@@ -712,7 +719,7 @@ extern "C" int align_rigid(shp_set Q, int32_t iq, shp_set B, const int32_t* ib, 
   if (e == cudaSuccess) e = dev_alloc((void**)&queue, sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) { release(); return cuda_fail(e, "align_rigid: scratch"); }
-  shp_mc mc{cfg->seed, cfg->stream, cfg->n_crn, 0u};
+  shp_mc mc{cfg->seed, cfg->stream, cfg->n_crn, cfg->crn_flags & SHP_ANTITHETIC};
   rc = align_crn_points(Q, iq, &mc, reinterpret_cast<float*>(pts), stream);
   if (rc) { release(); return rc; }
   AdamArgs a{};

@@ -277,7 +277,7 @@ using namespace shp;
 
 extern "C" const char* shp_last_error(void) { return g_err.c_str(); }
 
-extern "C" int shp_version(void) { return 5; }
+extern "C" int shp_version(void) { return 6; }
 
 extern "C" int shp_fail_next_allocations(int32_t count) {
   clear_error();

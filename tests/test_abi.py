@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version_and_error_string(lib):
-    assert lib.shp_version() == 5
+    assert lib.shp_version() == 6
     assert isinstance(lib.shp_last_error(), bytes)
 
 

@@ -46,10 +46,11 @@ def test_principal_frames(mols):
                 np.testing.assert_allclose(E[:, k], v, atol=1e-4)
 
 
-def test_crn_points_match_oracle(mols):
+@pytest.mark.parametrize("anti", [False, True])
+def test_crn_points_match_oracle(mols, anti):
     q, b, Sq, Sb = mols
-    pts = shp.align_crn_points(Sq, 0, seed=9, n=1001, stream_base=4).cpu().numpy()
-    ref = O.crn_points(q, 0, seed=9, stream=4, n=1001)
+    pts = shp.align_crn_points(Sq, 0, seed=9, n=1001, stream_base=4, antithetic=anti).cpu().numpy()
+    ref = O.crn_points(q, 0, seed=9, stream=4, n=1001, antithetic=anti)
     np.testing.assert_allclose(pts[:, :3], ref[:, :3], rtol=1e-5, atol=2e-5)
     np.testing.assert_allclose(pts[:, 3], ref[:, 3], rtol=2e-5, atol=1e-6)
 
@@ -293,6 +294,14 @@ def test_recovers_known_superpositions():
     rmsd8, T8 = judged(res8)
     assert np.all(rmsd8 < 0.1) and np.median(rmsd8) < 0.6 * np.median(rmsd), (rmsd8, rmsd)
     assert np.all(T8 >= 0.99), T8
+    # the same 1024 points in antithetic pairs: the query atom a point was
+    # drawn from contributes an odd term to the gradient at the exact
+    # superposition, which each pair cancels, and every copy reaches 0.99
+    resa = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=12, starts=8, steps=100, n_crn=1024, n_score=8192,
+                           antithetic=True)
+    rmsda, Ta = judged(resa)
+    assert np.all(rmsda < 0.2) and np.median(rmsda) < np.median(rmsd), (rmsda, rmsd)
+    assert np.all(Ta >= 0.99), Ta
     T = res["T"].cpu().numpy()
     # the unaligned copies do not overlap at all
     est, _ = shp.overlap_estimate(Sq, np.zeros(6), Sb, ib[:6], seed=1, n_samples=1024)

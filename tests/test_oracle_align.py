@@ -60,6 +60,26 @@ def test_crn_objectives_estimate_the_exact_overlaps(pair):
     np.testing.assert_allclose(pts[:100, 3], u / m, rtol=1e-14)
 
 
+def test_antithetic_crn_points(pair):
+    """Antithetic CRN points: each odd point is the reflection of the even one
+    about an atom centre of the query (the even point's component), the even
+    points are those of the plain layout, and the objectives still estimate
+    the exact overlaps."""
+    a, b = pair
+    plain = O.crn_points(a, 0, seed=3, stream=0, n=2000)
+    anti = O.crn_points(a, 0, seed=3, stream=0, n=2000, antithetic=True)
+    np.testing.assert_array_equal(anti[0::2], plain[0::2])
+    mid = 0.5 * (anti[0::2, :3] + anti[1::2, :3])
+    d = np.linalg.norm(mid[:, None, :] - a.xyz[None, :, :].astype(np.float64), axis=2).min(1)
+    assert d.max() < 1e-12
+    assert not np.allclose(anti[1::2], plain[1::2])
+    ZQ = O.mixture_mass(a)[0]
+    pts = O.crn_points(a, 0, seed=4, stream=0, n=1 << 16, antithetic=True)
+    un = O.pose_objective(ZQ, pts, b, 0, POSE, objective=O.OBJ_UNION)
+    un_exact = O.union_overlap_ie(a, 0, b, 0, poseB=POSE.astype(np.float32))
+    assert un == pytest.approx(un_exact, rel=0.015)
+
+
 def test_crn_first_order_gradient_estimates_the_analytic_one(pair):
     a, b = pair
     ZQ = O.mixture_mass(a)[0]
