@@ -72,7 +72,7 @@ def parse_args():
     p.add_argument("--self-rel-se", type=float, default=3.5e-3,
                    help="relative SE to which the adaptive screen estimates each database molecule's union "
                         "self-overlap (the queries: a quarter of it)")
-    p.add_argument("--profile-case", choices=["align", "prefilter"], default=None,
+    p.add_argument("--profile-case", choices=["align", "prefilter", "self", "train"], default=None,
                    help="run one small case of a kernel family for a profiler capture, print its timings, exit")
     p.add_argument("--align-db", type=int, default=10_000,
                    help="database size of the alignment section (0 skips it)")
@@ -532,7 +532,14 @@ def profile_case(shp, torch, case: str):
                  (align_adam_kernel launches 0-1 and 2-3)
       prefilter: 16 queries x 200,000 molecules (18-60 atoms), first-order
                  Tanimoto of every pair and the best 10% per query
-                 (fo_tanimoto_kernel launches 0-1)"""
+                 (fo_tanimoto_kernel launches 0-1)
+      self:      union self-overlaps of the fixed-budget screen's 100,000
+                 database molecules, 4096 samples each (self_kernel
+                 launches 0-1)
+      train:     one epoch of the control-variate network on the features
+                 and attributions of 20,000 molecules, minibatches of 65,536
+                 atoms (train_kernel launches 0-11 in the warm-up epoch, then
+                 the timed epoch's)"""
     from paper_2607_20766_b300 import synth
     out = {"case": case}
 
@@ -556,6 +563,21 @@ def profile_case(shp, torch, case: str):
                 _, ms = timed(lambda: shp.align_rigid(Sq, 0, Sd, ib, sq, sd, seed=1, starts=8, steps=100, n_score=2,
                                                       objective=obj))
             out[name + "_ms"] = ms
+    elif case == "self":
+        q, d, _, _ = workload(N_DB, 0, 1)
+        Sd = shp.shape_set_load(d)
+        for k in range(2):
+            _, ms = timed(lambda: shp.union_volume_estimate(Sd, None, seed=1, n_samples=4096, stream_base=1))
+        out["self_ms"] = ms
+    elif case == "train":
+        from paper_2607_20766_b300 import cv
+        St = shp.shape_set_load(synth.generate(9100, synth.counts_uniform(9100, 20_000, 18, 60)))
+        feats, targets = cv.attributions_and_features(St, seed=1, M=256)
+        net = cv.CrowdingNet(seed=0)
+        for k in range(2):
+            _, ms = timed(lambda: net.fit(feats, targets, epochs=1, batch=65536, lr=3e-3))
+        out["epoch_ms"] = ms
+        out["atoms"] = int(feats.shape[0])
     else:
         q, d = synth.adaptive_screen(n_q=16, n_db=200_000, seed=4242)
         Sq, Sd = shp.shape_set_load(q), shp.shape_set_load(d)

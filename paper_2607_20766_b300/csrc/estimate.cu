@@ -39,10 +39,12 @@ struct __align__(16) CoefT {
 };
 
 // Running per-lane sums of one proposal direction: FP64 sums of the shifted
-// values {fa, fa^2, fb, fb^2} (each batch adds its FP32 partial over the
-// lane's 2 SP samples), and the warp-uniform shifts.
+// values {fa, fa^2, fb, fb^2}, the FP32 partial of the batches not yet added
+// to them (a batch's partial covers the lane's 2 SP samples; fixed-budget
+// runs add two batches' partials at a time), and the warp-uniform shifts.
 struct DirState {
   double s[4];
+  float p[4];
   float K[2];
 };
 
@@ -219,7 +221,10 @@ __device__ __forceinline__ void eval_table(const CoefT* __restrict__ tab, int n,
 
 __device__ __forceinline__ void dir_init(DirState& s) {
 #pragma unroll
-  for (int t = 0; t < 4; ++t) s.s[t] = 0.0;
+  for (int t = 0; t < 4; ++t) {
+    s.s[t] = 0.0;
+    s.p[t] = 0.f;
+  }
   s.K[0] = s.K[1] = 0.f;
 }
 
@@ -266,11 +271,13 @@ __device__ __forceinline__ void draw_batch(const float4* __restrict__ samp, cons
 //          fb = u_X^2 / m_X (self-overlap), with kCV (u_X^2 - ut_X^2) / m_X
 // With antithetic pairs the unit is the mean of a sample and its
 // reflection. The first batch sets the shifts from sample 0.
+// The batch's FP32 partial is added to the FP64 sums when `flush` (with the
+// partial carried from an unflushed batch before it), else carried.
 template <bool kSelf, int SP, int kForm, bool kCV = false>
 __device__ __forceinline__ void eval_batch(const CoefT* __restrict__ tx, const CoefT* __restrict__ ty, int nx,
                                            int ny, uint32_t b, uint32_t n, bool anti, int lane, DirState& st,
                                            const float2 (&rx)[SP], const float2 (&ry)[SP], const float2 (&rz)[SP],
-                                           const float2 (&rr)[SP]) {
+                                           const float2 (&rr)[SP], bool flush = true) {
   const uint32_t P = (n + 1u) >> 1;
   const uint32_t base = b * 32u * SP;
   float2 m[SP], q[SP], ut[SP], fa[SP], fb[SP];
@@ -361,8 +368,16 @@ __device__ __forceinline__ void eval_batch(const CoefT* __restrict__ tx, const C
     }
   }
   }
+  if (flush) {
 #pragma unroll
-  for (int t = 0; t < 4; ++t) st.s[t] += (double)acc[t];
+    for (int t = 0; t < 4; ++t) {
+      st.s[t] += (double)(st.p[t] + acc[t]);
+      st.p[t] = 0.f;
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) st.p[t] += acc[t];
+  }
 }
 
 // One batch of one direction (draw, evaluate, accumulate) by a single warp;
@@ -371,10 +386,12 @@ __device__ __forceinline__ void eval_batch(const CoefT* __restrict__ tx, const C
 template <bool kSelf, int SP, int kForm, bool kCV = false>
 __device__ __forceinline__ void run_batch(WarpTables& T, int nx, int ny, uint32_t b, uint32_t n, Key key,
                                           uint32_t slo, uint32_t shi, uint32_t tag, bool anti, int lane,
-                                          DirState& st, const CoefT* tx = nullptr, const CoefT* ty = nullptr) {
+                                          DirState& st, const CoefT* tx = nullptr, const CoefT* ty = nullptr,
+                                          bool flush = true) {
   float2 rx[SP], ry[SP], rz[SP], rr[SP];
   draw_batch<SP>(T.samp, T.thr, T.alias, nx, b, key, slo, shi, tag, anti, lane, rx, ry, rz, rr);
-  eval_batch<kSelf, SP, kForm, kCV>(tx ? tx : T.x, ty ? ty : T.y, nx, ny, b, n, anti, lane, st, rx, ry, rz, rr);
+  eval_batch<kSelf, SP, kForm, kCV>(tx ? tx : T.x, ty ? ty : T.y, nx, ny, b, n, anti, lane, st, rx, ry, rz, rr,
+                                    flush);
 }
 
 // est = Z mean, se = Z sqrt(s^2 / n) (n-1 sample variance, Eq. var) from
@@ -557,9 +574,11 @@ __device__ __forceinline__ void run_direction(WarpTables& T, const CrossArgs& ar
   const CoefT* tx = (shared && dir) ? T.y : T.x;
   const CoefT* ty = (shared && dir) ? T.x : T.y;
   DirState& st = T.st[dir][lane];
+  // batches in twos: the FP64 sums take every second batch's partial (and
+  // the last one's); an adaptive round's single batch is always added
   for (uint32_t k = b0; k < b1; ++k)
     run_batch<false, SP, kForm, kCV>(T, MX.n, MY.n, k, n, args.key, slo, shi, dir ? SHP_TAG_BA : SHP_TAG_AB, anti,
-                                     lane, st, tx, ty);
+                                     lane, st, tx, ty, ((k - b0) & 1u) || k + 1u == b1);
 }
 
 // kCV (screen modes): union slot with the weighted-Gaussian control variate.
@@ -712,7 +731,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) self_kernel(const Sel
     const uint32_t nb = ((args.n + 1u) / 2u + batch - 1u) / batch;
     for (uint32_t b = 0; b < nb; ++b)
       run_batch<true, SP, kForm>(T, M.n, 0, b, args.n, args.key, (uint32_t)stream, (uint32_t)(stream >> 32),
-                                 SHP_TAG_SELF, args.anti, lane, st);
+                                 SHP_TAG_SELF, args.anti, lane, st, nullptr, nullptr, (b & 1u) || b + 1u == nb);
     double s[4];
     dir_totals(st, s);
     if (lane == 0) {
@@ -788,7 +807,8 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) probe_kernel(const Pr
     const uint32_t n = a.batches * 64u * SP;
     if (a.draw) {
       for (uint32_t b = 0; b < a.batches; ++b)
-        run_batch<false, SP, kForm>(T, MX.n, MY.n, b, n, a.key, gw, 0u, (uint32_t)dir, false, lane, st);
+        run_batch<false, SP, kForm>(T, MX.n, MY.n, b, n, a.key, gw, 0u, (uint32_t)dir, false, lane, st, nullptr,
+                                    nullptr, (b & 1u) || b + 1u == a.batches);
     } else {
       int k0[SP], k1[SP];
 #pragma unroll
@@ -799,7 +819,8 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) probe_kernel(const Pr
       for (uint32_t b = 0; b < a.batches; ++b) {
         float2 rx[SP], ry[SP], rz[SP], rr[SP];
         synth_batch<SP>(T.samp, MX.n, b, k0, k1, rx, ry, rz, rr);
-        eval_batch<false, SP, kForm>(T.x, T.y, MX.n, MY.n, b, n, false, lane, st, rx, ry, rz, rr);
+        eval_batch<false, SP, kForm>(T.x, T.y, MX.n, MY.n, b, n, false, lane, st, rx, ry, rz, rr,
+                                     (b & 1u) || b + 1u == a.batches);
       }
     }
     double sums[4];
@@ -1348,7 +1369,8 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_volume_kernel(const CVArg
     if (a.target <= 0.f) {
       const uint32_t nb = ((a.n + 1u) / 2u + batch - 1u) / batch;
       for (uint32_t b = 0; b < nb; ++b)
-        run_batch<true, SP, 2, kCV>(T, M.n, 0, b, a.n, a.key, slo, shi, SHP_TAG_SELF, false, lane, st);
+        run_batch<true, SP, 2, kCV>(T, M.n, 0, b, a.n, a.key, slo, shi, SHP_TAG_SELF, false, lane, st, nullptr,
+                                    nullptr, (b & 1u) || b + 1u == nb);
       n_done = a.n;
     } else {
       const uint32_t cap_b = a.n / (2u * batch);
@@ -1357,7 +1379,8 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_volume_kernel(const CVArg
         const uint32_t nxt = b + a.round_b;
         const uint32_t n_now = nxt * batch * 2u;
         for (uint32_t k = b; k < nxt; ++k)
-          run_batch<true, SP, 2, kCV>(T, M.n, 0, k, n_now, a.key, slo, shi, SHP_TAG_SELF, false, lane, st);
+          run_batch<true, SP, 2, kCV>(T, M.n, 0, k, n_now, a.key, slo, shi, SHP_TAG_SELF, false, lane, st, nullptr,
+                                      nullptr, ((k - b) & 1u) || k + 1u == nxt);
         b = nxt;
         if (b >= cap_b) break;
         const int w = a.watch;
