@@ -190,21 +190,47 @@ __global__ void __launch_bounds__(kTrThreads) train_kernel(const float* params, 
   const int64_t n_tiles = (n + kTile - 1) / kTile;
   const int64_t t0 = (int64_t)blockIdx.x * tiles_per_block;
   const int64_t t1 = t0 + tiles_per_block < n_tiles ? t0 + tiles_per_block : n_tiles;
-  for (int64_t tile = t0; tile < t1; ++tile) {
-    __syncthreads();  // the previous tile's buffers (and the weights, first time) are done with
+  // each tile's features (this thread's share of the kTile x kXP entries)
+  // and the targets of this thread's two atoms are loaded one tile ahead, so
+  // the gather's latency overlaps the previous tile's GEMMs
+  constexpr int kXPer = (kTile * kXP + kTrThreads - 1) / kTrThreads;
+  float xv[kXPer], tv[2];
+  auto load_tile = [&](int64_t tile) {
     const int64_t a_base = tile * kTile;
-    for (int e = tid; e < kTile * kXP; e += kTrThreads) {
+#pragma unroll
+    for (int j = 0; j < kXPer; ++j) {
+      const int e = tid + j * kTrThreads;
       const int a = e / kXP, i = e - a * kXP;
       const int64_t k = a_base + a;
       float v = 0.f;
-      if (k < n) {
+      if (e < kTile * kXP && k < n) {
         const int64_t r = rows ? rows[k] : k;
         v = i < kIn ? x[(int64_t)kIn * r + i] : (i == kIn ? 1.f : 0.f);
       }
-      s.XN[a][i] = v;
-      if (i < kIn) s.XT[i][a] = v;
+      xv[j] = v;
     }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int64_t k = a_base + 2 * ta + r;
+      tv[r] = k < n ? target[rows ? rows[k] : k] : 0.f;
+    }
+  };
+  if (t0 < t1) load_tile(t0);
+  for (int64_t tile = t0; tile < t1; ++tile) {
+    __syncthreads();  // the previous tile's buffers (and the weights, first time) are done with
+    const int64_t a_base = tile * kTile;
+#pragma unroll
+    for (int j = 0; j < kXPer; ++j) {
+      const int e = tid + j * kTrThreads;
+      if (e < kTile * kXP) {
+        const int a = e / kXP, i = e - a * kXP;
+        s.XN[a][i] = xv[j];
+        if (i < kIn) s.XT[i][a] = xv[j];
+      }
+    }
+    const float tcur[2] = {tv[0], tv[1]};
     __syncthreads();
+    if (tile + 1 < t1) load_tile(tile + 1);
     // z1 and h1
     float z[2][4], d1g[2][4];
 #pragma unroll
@@ -255,7 +281,7 @@ __global__ void __launch_bounds__(kTrThreads) train_kernel(const float* params, 
       for (int o = 8; o > 0; o >>= 1) part_y += __shfl_xor_sync(0xffffffffu, part_y, o);
       const int64_t k = a_base + 2 * ta + r;
       float err = 0.f;
-      if (k < n) err = part_y + s.b3[0] - target[rows ? rows[k] : k];
+      if (k < n) err = part_y + s.b3[0] - tcur[r];
       dy[r] = err * inv_n;
       if (th == 0) { sse = fmaf(err, err, sse); sdy += dy[r]; }
     }
