@@ -48,7 +48,7 @@ FP32_OPS_PER_EVAL = 6  # 4 FMA (expanded exponent) + 1 add (first-order sum) + 1
 # DRAM bytes per screened pair, from one ncu capture of the screen kernel on a 20,000-pair case
 # (dram__bytes_read.sum + dram__bytes_write.sum = 24.42 MB; each database molecule is read once,
 # so the traffic scales with the pairs)
-SCREEN_DRAM_BYTES_PER_PAIR = (23_695_360 + 727_808) / 20_000
+SCREEN_DRAM_BYTES_PER_PAIR = (23_694_336 + 853_248) / 20_000
 
 
 def parse_args():
