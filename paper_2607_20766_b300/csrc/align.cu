@@ -57,17 +57,11 @@ struct __align__(16) AlignTables {
   float4 posed[SHP_MAX_ATOMS];  // R c (the posed centre less t), -alpha log2(e)
   CoefA coef[SHP_MAX_ATOMS];
   float lp[SHP_MAX_ATOMS];      // log2 p
-  union {
-    struct {                    // closed-form objective
-      float4 qatom[SHP_MAX_ATOMS];         // the query's centres, beta'
-      float qlp[SHP_MAX_ATOMS];            // the query's log2 w'
-      float2 fob[SHP_MAX_ATOMS];           // B's beta', log2 w'
-      FoPairB fo2[SHP_MAX_ATOMS / 2];      // B's posed atoms in pairs
-    };
-    // union objective: per-lane prefix products prod_{l<j} (1 - g_l) of the
-    // lane's two current points, for even j (odd j are rebuilt from them)
-    float2 pre[SHP_MAX_ATOMS / 2][32];
-  };
+  // closed-form objective
+  float4 qatom[SHP_MAX_ATOMS];     // the query's centres, beta'
+  float qlp[SHP_MAX_ATOMS];        // the query's log2 w'
+  float2 fob[SHP_MAX_ATOMS];       // B's beta', log2 w'
+  FoPairB fo2[SHP_MAX_ATOMS / 2];  // B's posed atoms in pairs
   float4 origin;                // o: the query's atom centroid
 };
 constexpr size_t kAlignSmem = sizeof(AlignTables) * kAlignWarps;
@@ -287,50 +281,31 @@ __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restr
       }
       F = m;
     } else {
+      // one pass: with f_j = 1 - g_j (rounded once) and q = prod_j f_j, the
+      // adjoint weight of atom j is w prod_{l != j} f_l g_j = w q g_j / f_j;
+      // the same rounded f_j enters the product and the quotient, so they
+      // cancel exactly. An f_j of exactly 0 is replaced by 2^-100: q then
+      // carries that factor (u = w (1 - q) is unchanged to FP32) and q / f_j
+      // still gives the other factors' product.
       float2 q = make_float2(1.f, 1.f);
-      int j = 0;
+      const float2 one = make_float2(1.f, 1.f), m1 = make_float2(-1.f, -1.f);
 #pragma unroll 2
-      for (; j + 1 < nb; j += 2) {
-        const float2 g0 = g_expanded2(T.coef[j], ox, oy, oz, rr);
-        const float2 g1 = g_expanded2(T.coef[j + 1], ox, oy, oz, rr);
-        T.pre[j >> 1][lane] = q;
-        q = __ffma2_rn(make_float2(-g0.x, -g0.y), q, q);
-        q = __ffma2_rn(make_float2(-g1.x, -g1.y), q, q);
-      }
-      if (j < nb) {
-        const float2 g0 = g_expanded2(T.coef[j], ox, oy, oz, rr);
-        T.pre[j >> 1][lane] = q;
-        q = __ffma2_rn(make_float2(-g0.x, -g0.y), q, q);
-      }
-      F = make_float2(w.x * (1.f - q.x), w.y * (1.f - q.y));
-      float2 S = w;  // w_k times the suffix product
-      // g_j again, from the same expression as the forward pass (the same
-      // float); the odd prefix from the even one as in the forward pass
-      j = nb - 1;
-      if (!(j & 1)) {
+      for (int j = 0; j < nb; ++j) {
         const CoefA& k = T.coef[j];
         const float2 g = g_expanded2(k, ox, oy, oz, rr);
-        const float2 pr = T.pre[j >> 1][lane];
-        const float2 e = __fmul2_rn(__fmul2_rn(g, pr), S);  // h = 2 alpha e
-        S = __ffma2_rn(make_float2(-g.x, -g.y), S, S);
+        float2 f = __ffma2_rn(g, m1, one);
+        f.x = f.x == 0.f ? 0x1p-100f : f.x;
+        f.y = f.y == 0.f ? 0x1p-100f : f.y;
+        q = __fmul2_rn(q, f);
+        const float2 e = make_float2(__fdividef(g.x, f.x), __fdividef(g.y, f.y));
         adj_add(k, e, ha, vx, vy, vz);
-        --j;
       }
-#pragma unroll 2
-      for (; j >= 1; j -= 2) {
-        const CoefA& k1 = T.coef[j];
-        const CoefA& k0 = T.coef[j - 1];
-        const float2 g1 = g_expanded2(k1, ox, oy, oz, rr);
-        const float2 g0 = g_expanded2(k0, ox, oy, oz, rr);
-        const float2 p0 = T.pre[j >> 1][lane];
-        const float2 p1 = __ffma2_rn(make_float2(-g0.x, -g0.y), p0, p0);
-        const float2 e1 = __fmul2_rn(__fmul2_rn(g1, p1), S);
-        S = __ffma2_rn(make_float2(-g1.x, -g1.y), S, S);
-        adj_add(k1, e1, ha, vx, vy, vz);
-        const float2 e0 = __fmul2_rn(__fmul2_rn(g0, p0), S);
-        S = __ffma2_rn(make_float2(-g0.x, -g0.y), S, S);
-        adj_add(k0, e0, ha, vx, vy, vz);
-      }
+      F = make_float2(w.x * (1.f - q.x), w.y * (1.f - q.y));
+      const float2 qw = __fmul2_rn(q, w);  // h = 2 alpha e qw
+      ha = __fmul2_rn(ha, qw);
+      vx = __fmul2_rn(vx, qw);
+      vy = __fmul2_rn(vy, qw);
+      vz = __fmul2_rn(vz, qw);
     }
     const float kLn2 = 0.6931471805599453f;
     const float4 rs[2] = {r0, r1};
