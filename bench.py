@@ -1003,11 +1003,11 @@ def align_section(shp, torch, n_db: int, rank: int, lane_rate: float, n_copies: 
                                                   **kw))
         nb_sum = float(d.counts.astype(np.float64).sum())
         if kw["objective"] == shp.OBJ_UNION:
-            roof = alu_roofline(lane_rate, 8 * 100 * kw["n_crn"] * nb_sum, t_adam, 12,
+            roof = alu_roofline(lane_rate, 8 * 100 * kw["n_crn"] * nb_sum, t_adam, 11,
                                 "G point-atom-steps/s", "align_adam_kernel (union CRN objective)",
-                                "12 FP32 ops per CRN point, atom and step: exponent 4 and prefix product 1 "
-                                "forward; adjoint weight 2, suffix product 1, force sums 4 (the kernel "
-                                "recomputes the exponent in the adjoint pass, 4 more)")
+                                "11 FP32 ops per CRN point, atom and step in one pass: exponent 4, "
+                                "f = 1 - g 1, product of the f 1, adjoint weight g / f 1 (after an SFU "
+                                "reciprocal), force sums 4; plus the exp2 and the reciprocal on the SFU")
         else:
             roof = alu_roofline(lane_rate, 8 * 100 * float(q.counts[0]) * nb_sum, t_adam, 14,
                                 "G atom-pair-steps/s", "align_adam_kernel (closed-form first order)",

@@ -382,8 +382,9 @@ int align_crn_points(shp_set Q, int32_t iq, const shp_mc* mc, float* points, voi
  *   value[k] = (Z_Q / n) sum_j f(r_j),  f = m_B (SHP_OBJ_FO) or w_j u_B
  *              (SHP_OBJ_UNION)
  *   grad[k][7] = d value[k] / d pose[k]  (through the normalisation)
- * The union derivative uses prefix and suffix products of (1 - g_l), never
- * a division by (1 - g_j).
+ * The union derivative is w q g_j / f_j with f_j = 1 - g_j rounded once and
+ * q the product of the same rounded f_l, so the quotient is the product over
+ * l != j to rounding (an f_j of exactly 0 is replaced by 2^-100).
  *   points [n_points][4] float, ib [n_items] int32, pose [n_items][7] float,
  *   value [n_items] double, grad [n_items][7] float; all device.
  */

@@ -9,9 +9,10 @@
 //   union        F = (Z_Q / n) sum_k w_k u_B(r_k),   w_k = u_Q(r_k) / m_Q(r_k)
 // dF/dc'_j = (Z_Q / n) sum_k c_jk 2 alpha_j g_j(r_k) (r_k - c'_j) with
 // c_jk = 1 (first order) or w_k prod_{l != j} (1 - g_l(r_k)) (union); the
-// product over l != j is formed from prefix and suffix products kept in
-// per-lane shared-memory columns, never by dividing by (1 - g_j) (g_j
-// reaches 1 when p > 1). The pose gradient is carried as the force
+// product over l != j is w_k q_k g_j / f_j in one pass over the atoms, with
+// f_j = 1 - g_j rounded once and q_k the product of those same f: the
+// rounded factor cancels exactly (g_j can reach 1 when p > 1: an f_j of
+// exactly 0 is replaced by 2^-100, which keeps the other factors' product). The pose gradient is carried as the force
 // f = dF/dt = sum_j dF/dc'_j and the torque tau = sum_j (c'_j - t) x dF/dc'_j
 // (dF = tau . omega for the rotation c'_j - t -> (I + [omega]x)(c'_j - t)).
 // With u_k = sum_j (dF/dc'_j)_k, point k's share of the force, and
