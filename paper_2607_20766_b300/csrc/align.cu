@@ -255,32 +255,49 @@ __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restr
       add_cross(acc, 2.f * Wxs, 2.f * Wys, 2.f * Wzs, xi, yi, zi);
     }
   }
-  // CRN objectives: each lane takes points k and k + 32 of every 64 (the
-  // second one, past n, with weight 0), both in the halves of packed FP32x2
-  // values. ha = sum_j a_j e_jk, v = sum_j b_j e_jk with e_jk = h_jk /
+  // CRN objectives: each lane takes kPairs packed point pairs per pass,
+  // points k + 64 p and k + 64 p + 32 of every 64 kPairs (those past n with
+  // weight 0, skipped in the sums), in the halves of packed FP32x2 values.
+  // ha = sum_j a_j e_jk, v = sum_j b_j e_jk with e_jk = h_jk /
   // (2 alpha_j ln 2): u_k = -ln 2 (2 ha (r_k - o) + v).
+  constexpr int kPairs = 2;
   const float4 o = T.origin;
-  for (int k0 = lane; k0 < n && objective != SHP_OBJ_FO_CLOSED; k0 += 64) {
-    const bool has1 = k0 + 32 < n;
-    const float4 r0 = pts[k0];
-    const float4 r1 = has1 ? pts[k0 + 32] : r0;
-    const float2 ox = make_float2(r0.x - o.x, r1.x - o.x), oy = make_float2(r0.y - o.y, r1.y - o.y);
-    const float2 oz = make_float2(r0.z - o.z, r1.z - o.z);
-    const float2 rr = make_float2(fmaf(ox.x, ox.x, fmaf(oy.x, oy.x, oz.x * oz.x)),
-                                  fmaf(ox.y, ox.y, fmaf(oy.y, oy.y, oz.y * oz.y)));
-    const float2 w = make_float2(r0.w, has1 ? r1.w : 0.f);
-    float2 ha = make_float2(0.f, 0.f), vx = ha, vy = ha, vz = ha;
-    float2 F;
+  for (int k0 = lane; k0 < n && objective != SHP_OBJ_FO_CLOSED; k0 += 64 * kPairs) {
+    float4 rs[kPairs][2];
+    bool has[kPairs][2];
+    float2 ox[kPairs], oy[kPairs], oz[kPairs], rr[kPairs], w[kPairs];
+    float2 ha[kPairs], vx[kPairs], vy[kPairs], vz[kPairs], F[kPairs];
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = k0 + 64 * p + 32 * h;
+        has[p][h] = k < n;
+        rs[p][h] = pts[has[p][h] ? k : k0];
+      }
+      ox[p] = make_float2(rs[p][0].x - o.x, rs[p][1].x - o.x);
+      oy[p] = make_float2(rs[p][0].y - o.y, rs[p][1].y - o.y);
+      oz[p] = make_float2(rs[p][0].z - o.z, rs[p][1].z - o.z);
+      rr[p] = __ffma2_rn(ox[p], ox[p], __ffma2_rn(oy[p], oy[p], __fmul2_rn(oz[p], oz[p])));
+      w[p] = make_float2(has[p][0] ? rs[p][0].w : 0.f, has[p][1] ? rs[p][1].w : 0.f);
+      ha[p] = make_float2(0.f, 0.f); vx[p] = ha[p]; vy[p] = ha[p]; vz[p] = ha[p];
+    }
     if (objective == SHP_OBJ_FO) {
-      float2 m = make_float2(0.f, 0.f);
-#pragma unroll 4
+      float2 m[kPairs];
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p) m[p] = make_float2(0.f, 0.f);
+#pragma unroll 2
       for (int j = 0; j < nb; ++j) {
         const CoefA& k = T.coef[j];
-        const float2 g = g_expanded2(k, ox, oy, oz, rr);  // h = 2 alpha g
-        m = __fadd2_rn(m, g);
-        adj_add(k, g, ha, vx, vy, vz);
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+          const float2 g = g_expanded2(k, ox[p], oy[p], oz[p], rr[p]);  // h = 2 alpha g
+          m[p] = __fadd2_rn(m[p], g);
+          adj_add(k, g, ha[p], vx[p], vy[p], vz[p]);
+        }
       }
-      F = m;
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p) F[p] = m[p];
     } else {
       // one pass: with f_j = 1 - g_j (rounded once) and q = prod_j f_j, the
       // adjoint weight of atom j is w prod_{l != j} f_l g_j = w q g_j / f_j;
@@ -288,39 +305,49 @@ __device__ void value_grad(AlignTables& T, int nb, int na, const float4* __restr
       // cancel exactly. An f_j of exactly 0 is replaced by 2^-100: q then
       // carries that factor (u = w (1 - q) is unchanged to FP32) and q / f_j
       // still gives the other factors' product.
-      float2 q = make_float2(1.f, 1.f);
+      float2 q[kPairs];
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p) q[p] = make_float2(1.f, 1.f);
       const float2 one = make_float2(1.f, 1.f), m1 = make_float2(-1.f, -1.f);
 #pragma unroll 2
       for (int j = 0; j < nb; ++j) {
         const CoefA& k = T.coef[j];
-        const float2 g = g_expanded2(k, ox, oy, oz, rr);
-        float2 f = __ffma2_rn(g, m1, one);
-        f.x = f.x == 0.f ? 0x1p-100f : f.x;
-        f.y = f.y == 0.f ? 0x1p-100f : f.y;
-        q = __fmul2_rn(q, f);
-        const float2 e = make_float2(__fdividef(g.x, f.x), __fdividef(g.y, f.y));
-        adj_add(k, e, ha, vx, vy, vz);
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+          const float2 g = g_expanded2(k, ox[p], oy[p], oz[p], rr[p]);
+          float2 f = __ffma2_rn(g, m1, one);
+          f.x = f.x == 0.f ? 0x1p-100f : f.x;
+          f.y = f.y == 0.f ? 0x1p-100f : f.y;
+          q[p] = __fmul2_rn(q[p], f);
+          const float2 e = make_float2(__fdividef(g.x, f.x), __fdividef(g.y, f.y));
+          adj_add(k, e, ha[p], vx[p], vy[p], vz[p]);
+        }
       }
-      F = make_float2(w.x * (1.f - q.x), w.y * (1.f - q.y));
-      const float2 qw = __fmul2_rn(q, w);  // h = 2 alpha e qw
-      ha = __fmul2_rn(ha, qw);
-      vx = __fmul2_rn(vx, qw);
-      vy = __fmul2_rn(vy, qw);
-      vz = __fmul2_rn(vz, qw);
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p) {
+        F[p] = make_float2(w[p].x * (1.f - q[p].x), w[p].y * (1.f - q[p].y));
+        const float2 qw = __fmul2_rn(q[p], w[p]);  // h = 2 alpha e qw
+        ha[p] = __fmul2_rn(ha[p], qw);
+        vx[p] = __fmul2_rn(vx[p], qw);
+        vy[p] = __fmul2_rn(vy[p], qw);
+        vz[p] = __fmul2_rn(vz[p], qw);
+      }
     }
     const float kLn2 = 0.6931471805599453f;
-    const float4 rs[2] = {r0, r1};
-    const float2 hs[4] = {ha, vx, vy, vz};
-    for (int h = 0; h < 2; ++h) {
-      if (h == 1 && !has1) break;
-      const float oxh = h ? ox.y : ox.x, oyh = h ? oy.y : oy.x, ozh = h ? oz.y : oz.x;
-      const float hah = h ? hs[0].y : hs[0].x;
-      const float ux = -kLn2 * fmaf(2.f * hah, oxh, h ? hs[1].y : hs[1].x);
-      const float uy = -kLn2 * fmaf(2.f * hah, oyh, h ? hs[2].y : hs[2].x);
-      const float uz = -kLn2 * fmaf(2.f * hah, ozh, h ? hs[3].y : hs[3].x);
-      acc[0] += h ? F.y : F.x;
-      acc[1] += ux; acc[2] += uy; acc[3] += uz;
-      add_cross(acc, rs[h].x - t[0], rs[h].y - t[1], rs[h].z - t[2], ux, uy, uz);
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!has[p][h]) continue;
+        const float oxh = h ? ox[p].y : ox[p].x, oyh = h ? oy[p].y : oy[p].x, ozh = h ? oz[p].y : oz[p].x;
+        const float hah = h ? ha[p].y : ha[p].x;
+        const float ux = -kLn2 * fmaf(2.f * hah, oxh, h ? vx[p].y : vx[p].x);
+        const float uy = -kLn2 * fmaf(2.f * hah, oyh, h ? vy[p].y : vy[p].x);
+        const float uz = -kLn2 * fmaf(2.f * hah, ozh, h ? vz[p].y : vz[p].x);
+        acc[0] += h ? F[p].y : F[p].x;
+        acc[1] += ux; acc[2] += uy; acc[3] += uz;
+        add_cross(acc, rs[p][h].x - t[0], rs[p][h].y - t[1], rs[p][h].z - t[2], ux, uy, uz);
+      }
     }
   }
 #pragma unroll
