@@ -1429,16 +1429,17 @@ __device__ __forceinline__ float gauss_overlap(float4 ci, float lpi, float4 cj, 
   const float dx = ci.x - cj.x, dy = ci.y - cj.y, dz = ci.z - cj.z;
   const float inv = 1.0f / (ci.w + cj.w);
   const float t = kPi * inv;
-  return t * sqrtf(t) *
-         ex2_approx(fmaf(-kLog2e * ci.w * cj.w * inv, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), lpi + lpj));
+  const float aa = ci.w * cj.w;  // every operation is symmetric in (i, j): G_ij == G_ji bit for bit
+  return t * sqrtf(t) * ex2_approx(fmaf(-kLog2e * aa * inv, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), lpi + lpj));
 }
 
 // Least-squares control-variate weights, one warp per molecule: the
 // projection of u onto the molecule's own Gaussians, (G + lambda I) w = b
 // with b_j = Z E_q[(u/m) g_j] from nb batches of the molecule's own samples
 // (tag 6) and G_ij the closed-form overlaps, solved by conjugate gradients
-// (lanes own rows j and j + 32; G is recomputed in every product, nothing
-// N x N is stored; at most 4 N iterations, stopping at a relative residual of
+// (lanes own rows j and j + 32; G's lower triangle, N (N + 1) / 2 floats, is
+// formed once into the warp's staging tables, free after the sampling; at
+// most 4 N iterations, stopping at a relative residual of
 // 1e-6).
 __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_fit_kernel(const FitArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1502,6 +1503,21 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_fit_kernel(const FitArgs 
     const float trace =
         warp_sum((h0 ? gauss_overlap(c0, l0, c0, l0) : 0.f) + (h1 ? gauss_overlap(c1, l1, c1, l1) : 0.f));
     const float lambda = a.ridge * trace / (float)N;
+    // G's lower triangle, G_ij at i (i + 1) / 2 + j for j <= i, in the staging
+    // tables (the sampling is done with them)
+    float* G = reinterpret_cast<float*>(&T);
+    static_assert(sizeof(WarpTables) >= sizeof(float) * SHP_MAX_ATOMS * (SHP_MAX_ATOMS + 1) / 2,
+                  "the Gram triangle must fit the staging tables");
+    __syncwarp();
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) {
+      const float4 ci = a.S.atom[M.a0 + i];
+      const float li = a.S.aux[M.a0 + i].y;
+      for (int j = lane; j <= i; j += 32)
+        G[i * (i + 1) / 2 + j] = gauss_overlap(ci, li, a.S.atom[M.a0 + j], a.S.aux[M.a0 + j].y);
+    }
+    __syncwarp();
+    auto gram = [&](int i, int j) { return i >= j ? G[i * (i + 1) / 2 + j] : G[j * (j + 1) / 2 + i]; };
     float x0 = 0.f, x1 = 0.f;
     float r0 = h0 ? bsum[i0] * scale : 0.f, r1 = h1 ? bsum[i1] * scale : 0.f;
     float p0 = r0, p1 = r1;
@@ -1509,13 +1525,11 @@ __global__ void __launch_bounds__(kCVWarps * 32, 2) cv_fit_kernel(const FitArgs 
     const float tol = 1e-12f * rs;
     for (int it = 0; it < 4 * N && rs > tol; ++it) {
       float y0 = lambda * p0, y1 = lambda * p1;
-#pragma unroll 1
+#pragma unroll 4
       for (int j = 0; j < N; ++j) {
         const float pj = __shfl_sync(0xffffffffu, j < 32 ? p0 : p1, j & 31);
-        const float4 cj = a.S.atom[M.a0 + j];
-        const float lj = a.S.aux[M.a0 + j].y;
-        if (h0) y0 = fmaf(gauss_overlap(c0, l0, cj, lj), pj, y0);
-        if (h1) y1 = fmaf(gauss_overlap(c1, l1, cj, lj), pj, y1);
+        if (h0) y0 = fmaf(gram(i0, j), pj, y0);
+        if (h1) y1 = fmaf(gram(i1, j), pj, y1);
       }
       // warp_sum leaves the same bits in every lane, so these exits are
       // warp-uniform
