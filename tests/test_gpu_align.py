@@ -81,6 +81,33 @@ def test_pose_value_and_gradient(mols, objective):
         assert np.linalg.norm(grad[k] - g4) <= 1e-4 * np.linalg.norm(g4) + 1e-6 * ZQ, (k, grad[k], g4)
 
 
+def test_union_gradient_where_a_gaussian_equals_one():
+    """The union adjoint's weights w q g_j / f_j at a point where an atom's
+    g_j is exactly 1 (height 1, the point on the posed centre at the frame
+    origin, so the expanded exponent is exactly 0 and f_j = 0): the value and
+    gradient stay finite and equal the FP64 objective's."""
+    h = np.float32(1.0)
+    q = MolSet(np.zeros((1, 3), np.float32), np.array([1.7], np.float32), np.array([0, 1], np.int32),
+               np.zeros(1, np.uint8), np.array([h]))
+    xb = np.array([[0.0, 0.0, 0.0], [1.3, 0.4, -0.2], [-0.9, 1.1, 0.5]], np.float32)
+    b = MolSet(xb, np.array([1.7, 1.55, 1.52], np.float32), np.array([0, 3], np.int32), np.zeros(3, np.uint8),
+               np.array([h, 2.0 * np.sqrt(2.0), h], np.float32))
+    Sq, Sb = shp.shape_set_load(q), shp.shape_set_load(b)
+    rng = np.random.default_rng(2)
+    pts = np.concatenate([np.zeros((1, 3)), rng.normal(scale=1.2, size=(63, 3))]).astype(np.float32)
+    pts = np.concatenate([pts, rng.uniform(0.2, 1.0, size=(64, 1)).astype(np.float32)], 1)
+    ZQ = O.mixture_mass(q)[0]
+    pose = np.array([[1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0]], np.float32)
+    value, grad = shp.overlap_pose_grad(Sq, 0, torch.tensor(pts, device="cuda"), Sb, [0], pose,
+                                        objective=shp.OBJ_UNION)
+    value, grad = value.cpu().numpy(), grad.cpu().numpy()
+    assert np.all(np.isfinite(value)) and np.all(np.isfinite(grad))
+    F, g4 = O.pose_grad_fd(ZQ, pts.astype(np.float64), b, 0, pose[0].astype(np.float64), objective=shp.OBJ_UNION,
+                           h=1e-4)
+    assert value[0] == pytest.approx(F, rel=1e-5, abs=1e-7 * ZQ)
+    assert np.linalg.norm(grad[0] - g4) <= 1e-4 * np.linalg.norm(g4) + 1e-6 * ZQ, (grad[0], g4)
+
+
 def test_crn_first_order_gradient_estimates_analytic(mols):
     """The IS first-order gradient is an unbiased estimate of the gradient
     of the closed form (Eq. fo)."""
