@@ -12,7 +12,8 @@
 // product over l != j is w_k q_k g_j / f_j in one pass over the atoms, with
 // f_j = 1 - g_j rounded once and q_k the product of those same f: the
 // rounded factor cancels exactly (g_j can reach 1 when p > 1: an f_j of
-// exactly 0 is replaced by 2^-100, which keeps the other factors' product). The pose gradient is carried as the force
+// exactly 0 is replaced by 2^-100, which keeps the other factors' product).
+// The pose gradient is carried as the force
 // f = dF/dt = sum_j dF/dc'_j and the torque tau = sum_j (c'_j - t) x dF/dc'_j
 // (dF = tau . omega for the rotation c'_j - t -> (I + [omega]x)(c'_j - t)).
 // With u_k = sum_j (dF/dc'_j)_k, point k's share of the force, and
