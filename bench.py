@@ -561,7 +561,7 @@ def profile_case(shp, torch, case: str):
         for name, obj in (("union_crn", shp.OBJ_UNION), ("fo_closed", shp.OBJ_FO_CLOSED)):
             for k in range(2):
                 _, ms = timed(lambda: shp.align_rigid(Sq, 0, Sd, ib, sq, sd, seed=1, starts=8, steps=100, n_score=2,
-                                                      objective=obj))
+                                                      objective=obj, antithetic=False))
             out[name + "_ms"] = ms
     elif case == "self":
         q, d, _, _ = workload(N_DB, 0, 1)
@@ -964,7 +964,7 @@ def align_section(shp, torch, n_db: int, rank: int, lane_rate: float, n_copies: 
         torch.cuda.synchronize()
         return out, e0.elapsed_time(e1) / 1e3
 
-    arms = {"union_crn": dict(objective=shp.OBJ_UNION, n_crn=1024),
+    arms = {"union_crn": dict(objective=shp.OBJ_UNION, n_crn=1024, antithetic=False),
             "union_crn_antithetic": dict(objective=shp.OBJ_UNION, n_crn=1024, antithetic=True),
             "hybrid_fo_closed": dict(objective=shp.OBJ_FO_CLOSED, n_crn=1024)}
     pose_id = torch.tensor([[1, 0, 0, 0, 0, 0, 0]], dtype=torch.float32, device="cuda").expand(n_db, 7).contiguous()
@@ -1033,9 +1033,12 @@ def align_section(shp, torch, n_db: int, rank: int, lane_rate: float, n_copies: 
                      "known_copies": {"rmsd_median": float(np.median(rm)), "rmsd_max": float(rm.max()),
                                       "T_min": float(T_hi.min()), "T_median": float(np.median(T_hi)),
                                       "frac_T_ge_0.99": float((T_hi >= 0.99).mean())}}
-    # top-level keys of the union-objective arm (the workload's 1024-point CRN objective)
-    out.update(seconds=out["union_crn"]["seconds"], pairs_per_s=out["union_crn"]["pairs_per_s"],
-               mean_T_aligned=out["union_crn"]["mean_T_aligned"], frac_improved=out["union_crn"]["frac_improved"])
+    # top-level keys: the library's default union-objective alignment (the workload's 1024 CRN
+    # points, in antithetic pairs); union_crn is the same with independent points
+    dflt = out["union_crn_antithetic"]
+    out.update(default_arm="union_crn_antithetic", seconds=dflt["seconds"], pairs_per_s=dflt["pairs_per_s"],
+               mean_T_aligned=dflt["mean_T_aligned"], frac_improved=dflt["frac_improved"],
+               known_copies_frac_T_ge_0_99=dflt["known_copies"]["frac_T_ge_0.99"])
     return out
 
 

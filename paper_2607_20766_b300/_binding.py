@@ -543,11 +543,14 @@ def pose_overlap(pose, Q: ShapeSet, iq: int, points: torch.Tensor, B: ShapeSet, 
 def align_rigid(Q: ShapeSet, iq: int, B: ShapeSet, ib, self_q: torch.Tensor, self_db: torch.Tensor, seed: int = 0,
                 starts: int = 8, steps: int = 100, n_crn: int = 1024, objective: int = OBJ_UNION, lr: float = 0.02,
                 lr_t: float = 0.05, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, n_score: int = 4096,
-                stream_base: int = 0, with_starts: bool = False, stream=None, antithetic: bool = False):
+                stream_base: int = 0, with_starts: bool = False, stream=None, antithetic: bool = True):
     """Multi-start Adam alignment of B[ib[k]] onto Q[iq]. Returns dict pose
     ([n, 7]), T ([n]) and, with with_starts, T_starts ([n, starts]) and
-    pose_starts ([n, starts, 7], every start's final raw pose). antithetic:
-    the CRN points in antithetic pairs (same n_crn)."""
+    pose_starts ([n, starts, 7], every start's final raw pose). antithetic
+    (the default): the CRN points in antithetic pairs, each odd point the
+    reflection of the even one about its component centre (same n_crn), whose
+    union objective peaks at the exact superposition of a rigid copy; False:
+    independent points (SHP_ANTITHETIC off in shp_align.crn_flags)."""
     dev = Q.device
     ib = _device_i32(ib, dev)
     n = ib.numel()

@@ -197,7 +197,7 @@ def test_align_starts_and_first_adam_step(mols):
         Rp = Rotation.from_quat([pose0[k, 1], pose0[k, 2], pose0[k, 3], pose0[k, 0]]).as_matrix()
         assert min(np.abs(Rp - R).max() + np.abs(pose0[k, 4:] - t).max() for R, t in cands) < 1e-4
     # one Adam step from start 0 moves each raw parameter by lr * sign(grad) (then the quaternion is renormalised)
-    r1 = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=4, starts=1, steps=1, n_crn=1024, lr=1e-3, lr_t=2e-3,
+    r1 = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=4, starts=1, steps=1, n_crn=1024, lr=1e-3, lr_t=2e-3, antithetic=False,
                          n_score=256)
     r0s = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=4, starts=1, steps=0, n_score=256)
     p0 = r0s["pose"].cpu().numpy()
@@ -254,6 +254,7 @@ def test_adam_trajectories_match_the_oracle(mols, objective):
     pts = OA.crn(q, 0, seed=4, stream=0, n=1024)
     for K, tol in ((1, 1e-4), (3, 3e-4), (10, 1e-3)):
         PK = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=4, starts=starts, steps=K, n_crn=1024, objective=objective,
+                             antithetic=False,
                              n_score=256, with_starts=True)["pose_starts"].cpu().numpy()
         for k, i in enumerate(ib):
             for s in range(starts):
@@ -313,19 +314,20 @@ def test_recovers_known_superpositions():
     # 0.98-0.995. The gap is the estimator's, not the optimiser's: it
     # shrinks as n^-1/2, and with 8192 points the same optimiser recovers
     # every copy to T >= 0.99.
-    res = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=12, starts=8, steps=100, n_crn=1024, n_score=8192)
+    res = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=12, starts=8, steps=100, n_crn=1024, n_score=8192,
+                          antithetic=False)
     rmsd, T_hi = judged(res)
     assert np.all(rmsd < 0.3), rmsd
     assert np.all(T_hi >= 0.98) and np.median(T_hi) >= 0.985, T_hi
-    res8 = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=12, starts=8, steps=100, n_crn=8192, n_score=8192)
+    res8 = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=12, starts=8, steps=100, n_crn=8192, n_score=8192,
+                           antithetic=False)
     rmsd8, T8 = judged(res8)
     assert np.all(rmsd8 < 0.1) and np.median(rmsd8) < 0.6 * np.median(rmsd), (rmsd8, rmsd)
     assert np.all(T8 >= 0.99), T8
-    # the same 1024 points in antithetic pairs: the query atom a point was
-    # drawn from contributes an odd term to the gradient at the exact
-    # superposition, which each pair cancels, and every copy reaches 0.99
-    resa = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=12, starts=8, steps=100, n_crn=1024, n_score=8192,
-                           antithetic=True)
+    # the default: the same 1024 points in antithetic pairs. The query atom a
+    # point was drawn from contributes an odd term to the gradient at the
+    # exact superposition, which each pair cancels, and every copy reaches 0.99
+    resa = shp.align_rigid(Sq, 0, Sb, ib, sq, sb, seed=12, starts=8, steps=100, n_crn=1024, n_score=8192)
     rmsda, Ta = judged(resa)
     assert np.all(rmsda < 0.2) and np.median(rmsda) < np.median(rmsd), (rmsda, rmsd)
     assert np.all(Ta >= 0.99), Ta
