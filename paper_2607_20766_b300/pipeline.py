@@ -16,8 +16,18 @@ import torch
 from . import _binding as B
 
 
+# Relative SE of the kept database molecules' union self-overlaps. Each kept
+# molecule serves few pairs (1.6-4.4 at 5-25% kept of 16 queries), so a
+# looser self-overlap costs fewer samples than the longer pair runs it
+# causes under the full delta-method SE(T) (16 x 1M, tau 0.005: 5.5e-3 took
+# the 5% / 10% / 25% pipelines from 0.48 / 0.78 / 1.41 s at 3.5e-3 to
+# 0.40 / 0.67 / 1.30 s; 7e-3 was slower again).
+DEFAULT_SELF_REL_SE = 5.5e-3
+
+
 def hybrid_screen(Q: B.ShapeSet, D: B.ShapeSet, keep: float, tau: float = 0.005, cap: int = 65536,
-                  min_n: int = 1024, round: int = 256, self_rel_se: float = 3.5e-3, fit_samples: int = 4096,
+                  min_n: int = 1024, round: int = 256, self_rel_se: float = DEFAULT_SELF_REL_SE,
+                  fit_samples: int = 4096,
                   control_variate: bool = True, seed: int = 77, self_seed: int = 11, self_base_q: int = 0,
                   self_base_db: int = 16, fit_seed_q: int = 91, fit_seed_db: int = 92, stream=None) -> dict:
     """Screen every query of Q against D through the first-order prefilter.
