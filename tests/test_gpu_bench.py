@@ -68,7 +68,8 @@ def test_bench_json_line_small():
     assert 0.0 < line["control_variate"]["train_roofline"]["frac"] < 1.5
     assert 0.0 < a["roofline"]["frac"] < 1.5 and 0.0 < a["first_order_kernel"]["roofline"]["frac"] < 1.5
     for pf in a["first_order_prefilter"]:
-        assert pf["kept_pairs_equal_unfiltered"] and pf["molecules_kept"] > 0
+        assert pf["kept_pairs_equal_unfiltered_at_its_self_precision"] and pf["molecules_kept"] > 0
+        assert 0.0 <= pf["recall_at_100"]["min"] <= 1.0 and pf["frac_se_met"] > 0.99
 
 
 @pytest.mark.parametrize("case, keys", [("align", ("union_crn_ms", "fo_closed_ms")),
