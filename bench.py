@@ -72,7 +72,7 @@ def parse_args():
     p.add_argument("--self-rel-se", type=float, default=3.5e-3,
                    help="relative SE to which the adaptive screen estimates each database molecule's union "
                         "self-overlap (the queries: a quarter of it)")
-    p.add_argument("--profile-case", choices=["align", "prefilter", "self", "train"], default=None,
+    p.add_argument("--profile-case", choices=["align", "prefilter", "self", "train", "load"], default=None,
                    help="run one small case of a kernel family for a profiler capture, print its timings, exit")
     p.add_argument("--align-db", type=int, default=10_000,
                    help="database size of the alignment section (0 skips it)")
@@ -539,7 +539,10 @@ def profile_case(shp, torch, case: str):
       train:     one epoch of the control-variate network on the features
                  and attributions of 20,000 molecules, minibatches of 65,536
                  atoms (train_kernel launches 0-11 in the warm-up epoch, then
-                 the timed epoch's)"""
+                 the timed epoch's)
+      load:      three loads of the fixed-budget screen's 100,000 database
+                 molecules (host packing, upload, set_prep_kernel launches
+                 0-2)"""
     from paper_2607_20766_b300 import synth
     out = {"case": case}
 
@@ -569,6 +572,17 @@ def profile_case(shp, torch, case: str):
         for k in range(2):
             _, ms = timed(lambda: shp.union_volume_estimate(Sd, None, seed=1, n_samples=4096, stream_base=1))
         out["self_ms"] = ms
+    elif case == "load":
+        import time
+        q, d, _, _ = workload(N_DB, 0, 1)
+        stream = torch.cuda.current_stream()
+        for k in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            S, ms = timed(lambda: shp.shape_set_load(d))
+            out["host_ms"] = 1e3 * (time.perf_counter() - t0)
+            S.free(stream)
+        out["load_ms"] = ms
     elif case == "train":
         from paper_2607_20766_b300 import cv
         St = shp.shape_set_load(synth.generate(9100, synth.counts_uniform(9100, 20_000, 18, 60)))
@@ -1092,9 +1106,9 @@ def end_to_end(shp, torch, q, d, n, steps: int, warmup: int, start: int = 0, n_g
     screen_evals, self_evals = step_evals(q, d, n)
     atoms = q.n_atoms + d.n_atoms
     mols = q.n_mol + d.n_mol
-    # shape_set_load uploads per atom float4 + float2 + radius + uint32 + uint8, per molecule offset, Z,
-    # order and frame (12 floats)
-    h2d = atoms * (16 + 8 + 4 + 4 + 1) + (mols + 2) * 4 + mols * (8 + 4 + 48)
+    # shape_set_load uploads per atom x, y, z (a float4) and the radius, per molecule its offset and its
+    # place in the size order (the rest is computed on the device)
+    h2d = atoms * (16 + 4) + (mols + 2) * 4 + mols * 4
     d2h = npairs * 2 * 4 * 2
     return {"value": (screen_evals + self_evals) / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "seconds_per_step": dt,

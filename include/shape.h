@@ -93,11 +93,15 @@ int shp_fail_next_allocations(int32_t count);
  *   n_mol         >= 0
  * Builds per molecule the mixture mass Z, the integer alias table of the
  * component probabilities v_i / Z, and a largest-first order used to
- * balance screens. Host preparation runs on the host threads (OpenMP);
- * the device memory is allocated and filled on a library-owned upload
- * stream and `stream` is made to wait for the upload (work enqueued on
- * `stream` after the call sees the set, while kernels already queued on it
- * overlap the copy; other streams must order themselves after `stream`).
+ * balance screens. The host threads (OpenMP) validate the inputs and pack
+ * coordinates, radii (and heights) into a staging buffer; one copy uploads
+ * them (20 B per atom, 24 with heights) on a library-owned upload stream,
+ * where a kernel then computes alpha, the sampling width, log2 p, the
+ * volumes v_i = p_i (pi / alpha_i)^{3/2}, Z and the alias tables in FP64
+ * with IEEE-rounded operations (log2 p of given heights by CUDA's FP64
+ * log2). `stream` is made to wait for that work (work enqueued on `stream`
+ * after the call sees the set, while kernels already queued on it overlap
+ * the copy; other streams must order themselves after `stream`).
  * Not capturable into a CUDA graph. The host arrays may be reused as soon as the
  * call returns (they are copied into one of two library-owned pinned
  * staging buffers, and a call waits only for the upload made from the same

@@ -415,7 +415,7 @@ struct GradArgs {
   const float4* pts;
   int n_pts;
   int objective;
-  double scale;  // Z_Q / n for the CRN objectives, 1 for the closed form
+  uint32_t scale_n;  // n of the CRN objectives (scale Z_Q / n, Z_Q read on the device), 0 for the closed form (1)
   SetView Q;
   int32_t iq;
   int64_t n_items;
@@ -448,9 +448,10 @@ __global__ void __launch_bounds__(kAlignThreads) pose_grad_kernel(const GradArgs
   float acc[7];
   value_grad(T, nb, a.Q.off[a.iq + 1] - a.Q.off[a.iq], a.pts, a.n_pts, a.objective, pose + 4, lane, acc);
   if (lane == 0) {
+    const double scale = a.scale_n ? a.Q.Z[a.iq] / (double)a.scale_n : 1.0;
     float g[7];
-    pose_gradient(pose, acc, (float)a.scale, g);
-    a.value[item] = a.scale * (double)acc[0];
+    pose_gradient(pose, acc, (float)scale, g);
+    a.value[item] = scale * (double)acc[0];
     for (int d = 0; d < 7; ++d) a.grad[7 * item + d] = g[d];
   }
 }
@@ -463,7 +464,7 @@ struct AdamArgs {
   int starts, steps, objective;
   const float4* pts;
   int n_pts;
-  float scale;
+  uint32_t scale_n;  // as in GradArgs
   float lr, lr_t, beta1, beta2, eps;
   Key key;
   uint64_t stream;
@@ -523,6 +524,7 @@ __global__ void __launch_bounds__(kAlignThreads) align_adam_kernel(const AdamArg
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   AlignTables& T = reinterpret_cast<AlignTables*>(smem_raw)[warp];
   const int64_t n_items = a.n_pairs * a.starts;
+  const float scale = a.scale_n ? (float)(a.Q.Z[a.iq] / (double)a.scale_n) : 1.f;
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(a.queue, 1ull);
@@ -553,8 +555,8 @@ __global__ void __launch_bounds__(kAlignThreads) align_adam_kernel(const AdamArg
       float acc[7];
       value_grad(T, nb, na, a.pts, a.n_pts, a.objective, pose + 4, lane, acc);
       float g[7];
-      pose_gradient(pose, acc, a.scale, g);
-      value = a.scale * acc[0];
+      pose_gradient(pose, acc, scale, g);
+      value = scale * acc[0];
       b1t *= a.beta1;
       b2t *= a.beta2;
       // cosine step-size decay: constant-step Adam keeps moving by about the
@@ -668,7 +670,7 @@ extern "C" int overlap_pose_grad(shp_set Q, int32_t iq, const float* points, uin
   a.pts = reinterpret_cast<const float4*>(points);
   a.n_pts = closed ? 0 : (int)n_points;
   a.objective = (int)objective;
-  a.scale = closed ? 1.0 : Q->h_Z[iq] / (double)n_points;
+  a.scale_n = closed ? 0u : n_points;
   a.n_items = n_items;
   a.value = value;
   a.grad = grad;
@@ -737,7 +739,7 @@ extern "C" int align_rigid(shp_set Q, int32_t iq, shp_set B, const int32_t* ib, 
   a.objective = (int)cfg->objective;
   a.pts = pts;
   a.n_pts = cfg->objective == SHP_OBJ_FO_CLOSED ? 0 : (int)cfg->n_crn;
-  a.scale = cfg->objective == SHP_OBJ_FO_CLOSED ? 1.f : (float)(Q->h_Z[iq] / (double)cfg->n_crn);
+  a.scale_n = cfg->objective == SHP_OBJ_FO_CLOSED ? 0u : cfg->n_crn;
   a.lr = cfg->lr;
   a.lr_t = cfg->lr_t;
   a.beta1 = cfg->beta1;

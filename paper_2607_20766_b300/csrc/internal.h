@@ -31,9 +31,7 @@ struct shp_set_s {
   bool frames_ready = false;
   cudaEvent_t frames_done = nullptr;
   std::mutex frames_mu;
-  // host mirrors of Z (alignment scales its estimates on the host) and of
-  // the atom counts
-  std::vector<double> h_Z;
+  // host mirror of the atom counts
   std::vector<uint8_t> h_count;
   int32_t h_off_count(int32_t m) const { return h_count[m]; }
 };

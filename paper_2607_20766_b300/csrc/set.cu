@@ -1,5 +1,5 @@
-// Molecule sets: validation, per-atom parameters, mixture masses and alias
-// tables (Eq. occ, Eq. expectation), device upload. Host code.
+// Molecule sets: host validation, packing and upload; per-atom parameters,
+// mixture masses and alias tables on the device (Eq. occ, Eq. expectation).
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -29,40 +29,130 @@ int cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? SHP_ENOMEM : SHP_ECUDA;
 }
 
-// Integer alias table for weights v[0..n-1] (n <= 64). Column masses are in
-// units of 2^-32 of one column: M_i = floor((v_i / Z) * n 2^32), the
-// rounding remainder goes to the last atom; small (M < 2^32) and large
-// worklists are FIFO in atom order, and a large atom stays at the head of
-// its list until its residual mass turns small. Full columns get threshold
-// 2^32 - 1 and alias themselves.
-static void build_alias(int n, const double* v, uint32_t* thr, uint8_t* alias) {
-  const uint64_t kOne = 1ull << 32;
-  double Z = 0.0;
-  for (int i = 0; i < n; ++i) Z += v[i];
-  const double scale = (double)n * 4294967296.0;
-  uint64_t mass[SHP_MAX_ATOMS];
-  uint64_t sum = 0;
-  for (int i = 0; i < n; ++i) {
-    mass[i] = (uint64_t)std::floor((v[i] / Z) * scale);
-    sum += mass[i];
-  }
-  mass[n - 1] += (uint64_t)n * kOne - sum;
-  int sq[SHP_MAX_ATOMS], lq[SHP_MAX_ATOMS];
-  int sh = 0, st = 0, lh = 0, lt = 0;
-  for (int i = 0; i < n; ++i) (mass[i] < kOne ? sq[st++] : lq[lt++]) = i;
-  while (sh < st && lh < lt) {
-    const int s = sq[sh++];
-    const int l = lq[lh];
-    thr[s] = (uint32_t)mass[s];
-    alias[s] = (uint8_t)l;
-    mass[l] -= kOne - mass[s];
-    if (mass[l] < kOne) {
-      ++lh;
-      sq[st++] = l;
+// Per-molecule preparation on the device, one warp per molecule (molecules
+// taken in size order, so neighbouring warps do similar work). Per atom, from
+// the radius R and height p (FP64, IEEE-rounded operations throughout, so the
+// values do not depend on the compiler's contraction choices):
+//   alpha = c_alpha / R^2,  t = pi / alpha,  v = p t sqrt(t)   (Gaussian volume)
+//   sigma = 1 / sqrt(2 alpha) (sampling width),  log2 p,  Z = sum_i v_i in
+//   atom order.
+// Integer alias table of the v_i: column masses in units of 2^-32 of one
+// column, M_i = floor((v_i / Z) * n 2^32), the rounding remainder to the last
+// atom; small (M < 2^32) and large worklists are FIFO in atom order, and a
+// large atom stays at the head of its list until its residual mass turns
+// small. Full columns get threshold 2^32 - 1 and alias themselves. The list
+// building is sequential (lane 0) on the warp's shared-memory copy.
+constexpr int kRadiusClasses = 16;
+
+struct PrepArgs {
+  float4* atom;          // in: x, y, z; out: w = alpha
+  float2* aux;           // out: sigma, log2 p
+  const float* radius;   // [n_atoms]
+  const float* height;   // [n_atoms] heights staged in the threshold slots, or NULL: p_default
+  uint32_t* thr;         // out: alias thresholds (after the heights are read)
+  uint8_t* alias;        // out: alias targets
+  double* Z;             // out: [n_mol]
+  const int32_t* off;
+  const int32_t* order;
+  int32_t n_mol;
+  double c_alpha, p_default;
+  float log2p_default;
+  // radius classes: radii come from a few element types, so the host
+  // evaluates the terms that depend on R alone once per class (up to
+  // kRadiusClasses radii, bits ascending), with the same IEEE operations as
+  // the kernel; an atom whose radius has no class evaluates them itself.
+  int32_t n_cls;
+  uint32_t cls_bits[kRadiusClasses];
+  float cls_alpha[kRadiusClasses], cls_sigma[kRadiusClasses];
+  double cls_t[kRadiusClasses], cls_sqrt_t[kRadiusClasses];
+};
+
+constexpr int kPrepWarps = 8;
+
+struct PrepWarp {
+  double v[SHP_MAX_ATOMS];
+  unsigned long long mass[SHP_MAX_ATOMS];
+  uint8_t small[SHP_MAX_ATOMS], large[SHP_MAX_ATOMS];
+};
+
+__global__ void __launch_bounds__(32 * kPrepWarps) set_prep_kernel(const PrepArgs a) {
+  __shared__ PrepWarp W[kPrepWarps];
+  __shared__ uint32_t cls_bits[kRadiusClasses];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  PrepWarp& w = W[warp];
+  const unsigned long long kOne = 1ull << 32;
+  const double kPi = 3.14159265358979323846;
+  if (threadIdx.x < kRadiusClasses) cls_bits[threadIdx.x] = a.cls_bits[threadIdx.x];
+  __syncthreads();
+  for (int64_t k = (int64_t)blockIdx.x * kPrepWarps + warp; k < a.n_mol; k += (int64_t)gridDim.x * kPrepWarps) {
+    const int32_t m = a.order[k];
+    const int32_t a0 = a.off[m], n = a.off[m + 1] - a0;
+    for (int i = lane; i < n; i += 32) {
+      const float Rf = a.radius[a0 + i];
+      const double p = a.height ? (double)a.height[a0 + i] : a.p_default;
+      const uint32_t bits = __float_as_uint(Rf);
+      int c = 0;
+      for (int step = kRadiusClasses / 2; step; step >>= 1)
+        if (c + step < a.n_cls && cls_bits[c + step] <= bits) c += step;
+      double t, sqrt_t;
+      float alpha_f, sigma_f;
+      if (a.n_cls && cls_bits[c] == bits) {
+        t = a.cls_t[c];
+        sqrt_t = a.cls_sqrt_t[c];
+        alpha_f = a.cls_alpha[c];
+        sigma_f = a.cls_sigma[c];
+      } else {
+        const double R = Rf;
+        const double alpha = __ddiv_rn(a.c_alpha, __dmul_rn(R, R));
+        t = __ddiv_rn(kPi, alpha);
+        sqrt_t = __dsqrt_rn(t);
+        alpha_f = (float)alpha;
+        sigma_f = (float)__ddiv_rn(1.0, __dsqrt_rn(__dmul_rn(2.0, alpha)));
+      }
+      w.v[i] = __dmul_rn(__dmul_rn(p, t), sqrt_t);
+      reinterpret_cast<float*>(a.atom + a0 + i)[3] = alpha_f;
+      a.aux[a0 + i] = make_float2(sigma_f, a.height ? (float)log2(p) : a.log2p_default);
     }
+    __syncwarp();
+    double Z = 0.0;
+    if (lane == 0) {
+      for (int i = 0; i < n; ++i) Z = __dadd_rn(Z, w.v[i]);
+      a.Z[m] = Z;
+    }
+    Z = __shfl_sync(0xffffffffu, Z, 0);
+    const double scale = __dmul_rn((double)n, 4294967296.0);
+    unsigned long long sum = 0;
+    for (int i = lane; i < n; i += 32) {
+      // truncation = floor: 0 <= (v_i / Z) n 2^32 < 2^38
+      const unsigned long long M = (unsigned long long)(long long)__dmul_rn(__ddiv_rn(w.v[i], Z), scale);
+      w.mass[i] = M;
+      sum += M;
+    }
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    __syncwarp();
+    if (lane == 0) {
+      unsigned long long* mass = w.mass;
+      mass[n - 1] += (unsigned long long)n * kOne - sum;
+      uint32_t* thr = a.thr + a0;
+      uint8_t* alias = a.alias + a0;
+      int sh = 0, st = 0, lh = 0, lt = 0;
+      for (int i = 0; i < n; ++i) (mass[i] < kOne ? w.small[st++] : w.large[lt++]) = (uint8_t)i;
+      while (sh < st && lh < lt) {
+        const int sm = w.small[sh++];
+        const int lg = w.large[lh];
+        thr[sm] = (uint32_t)mass[sm];
+        alias[sm] = (uint8_t)lg;
+        mass[lg] -= kOne - mass[sm];
+        if (mass[lg] < kOne) {
+          ++lh;
+          w.small[st++] = (uint8_t)lg;
+        }
+      }
+      for (; sh < st; ++sh) { thr[w.small[sh]] = 0xFFFFFFFFu; alias[w.small[sh]] = w.small[sh]; }
+      for (; lh < lt; ++lh) { thr[w.large[lh]] = 0xFFFFFFFFu; alias[w.large[lh]] = w.large[lh]; }
+    }
+    __syncwarp();
   }
-  for (; sh < st; ++sh) { thr[sq[sh]] = 0xFFFFFFFFu; alias[sq[sh]] = (uint8_t)sq[sh]; }
-  for (; lh < lt; ++lh) { thr[lq[lh]] = 0xFFFFFFFFu; alias[lq[lh]] = (uint8_t)lq[lh]; }
 }
 
 // Gaussian volume v_i = p_i (pi/alpha_i)^{3/2} and centre of atom i, from
@@ -156,11 +246,12 @@ __global__ void frames_kernel(const float4* __restrict__ atom, const float2* __r
   principal_frame(off[m + 1] - a0, atom + a0, aux + a0, frame + 12 * (size_t)m);
 }
 
-// All device arrays of a set live in one stream-ordered allocation, filled
-// by one copy from one of two pinned staging buffers that the library keeps
-// (and grows) across loads; each buffer's event marks the end of its last
-// upload, so a load waits only for the upload two loads back, never for the
-// caller's kernels.
+// All device arrays of a set live in one stream-ordered allocation: one copy
+// of the inputs (20 B per atom, 24 with heights) from one of two pinned
+// staging buffers that the library keeps (and grows) across loads, then
+// set_prep_kernel writes the rest; each buffer's event marks the end of its
+// last use, so a load waits only for the upload two loads back, never for
+// the caller's kernels.
 struct SetLayout {
   size_t atom, aux, radius, thr, alias, off, Z, order, frame, total;
 };
@@ -170,14 +261,17 @@ static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 static SetLayout set_layout(int64_t n_atoms, int32_t n_mol) {
   SetLayout L{};
   size_t o = 0;
+  // uploaded from the host: atoms (x, y, z), radii, offsets, size order,
+  // then the thresholds' slots (which carry the heights when given)
   L.atom = o;   o = align16(o + sizeof(float4) * n_atoms);
-  L.aux = o;    o = align16(o + sizeof(float2) * n_atoms);
   L.radius = o; o = align16(o + sizeof(float) * n_atoms);
-  L.thr = o;    o = align16(o + sizeof(uint32_t) * n_atoms);
-  L.alias = o;  o = align16(o + n_atoms);
   L.off = o;    o = align16(o + sizeof(int32_t) * (n_mol + 1));
-  L.Z = o;      o = align16(o + sizeof(double) * n_mol);
   L.order = o;  o = align16(o + sizeof(int32_t) * n_mol);
+  L.thr = o;    o = align16(o + sizeof(uint32_t) * n_atoms);
+  // written on the device
+  L.aux = o;    o = align16(o + sizeof(float2) * n_atoms);
+  L.alias = o;  o = align16(o + n_atoms);
+  L.Z = o;      o = align16(o + sizeof(double) * n_mol);
   L.frame = o;  o = align16(o + sizeof(float) * 12 * n_mol);
   L.total = o;
   return L;
@@ -316,7 +410,6 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
   s->n_mol = n_mol;
   s->n_atoms = n_atoms;
   s->max_atoms = max_atoms;
-  s->h_Z.assign(n_mol, 0.0);
   s->h_count.resize(n_mol);
   for (int32_t m = 0; m < n_mol; ++m) s->h_count[m] = (uint8_t)(offsets[m + 1] - offsets[m]);
   const SetLayout L = set_layout(n_atoms, n_mol);
@@ -326,46 +419,28 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
   if (rc) { delete s; return rc; }
   unsigned char* hb = static_cast<unsigned char*>(sb->ptr);
   float4* atom = reinterpret_cast<float4*>(hb + L.atom);
-  float2* aux = reinterpret_cast<float2*>(hb + L.aux);
   float* rad = reinterpret_cast<float*>(hb + L.radius);
-  uint32_t* thr = reinterpret_cast<uint32_t*>(hb + L.thr);
-  uint8_t* alias = hb + L.alias;
-  double* Zs = reinterpret_cast<double*>(hb + L.Z);
-  // per-molecule preparation, molecules in parallel, written straight into
-  // the staging buffer
+  float* hgt = reinterpret_cast<float*>(hb + L.thr);
+  // host side: validate and pack (x, y, z, -) and R (and p) into the staging
+  // buffer, molecules in parallel; the arithmetic runs in set_prep_kernel
   int32_t bad_mol = -1;
 #pragma omp parallel for schedule(dynamic, 256)
   for (int32_t m = 0; m < n_mol; ++m) {
-    const int32_t a0 = offsets[m], n = offsets[m + 1] - a0;
-    double v[SHP_MAX_ATOMS];
-    double Z = 0.0;
+    const int64_t a0 = offsets[m], a1 = offsets[m + 1];
     bool ok = true;
-    for (int i = 0; i < n; ++i) {
-      const int64_t a = a0 + i;
-      const double x = xyz[3 * a], y = xyz[3 * a + 1], z = xyz[3 * a + 2];
-      const double R = radius[a];
-      const double p = height ? (double)height[a] : 2.0 * std::sqrt(2.0);
-      if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z) || !(R > 0) || !std::isfinite(R) ||
-          !(p > 0) || !std::isfinite(p)) {
-        ok = false;
-        break;
-      }
-      const double alpha = ca / (R * R);
-      const double t = kPi / alpha;
-      v[i] = p * t * std::sqrt(t);
-      Z += v[i];
-      atom[a] = make_float4((float)x, (float)y, (float)z, (float)alpha);
-      aux[a] = make_float2((float)(1.0 / std::sqrt(2.0 * alpha)), (float)std::log2(p));
-      rad[a] = radius[a];
+    for (int64_t a = a0; a < a1; ++a) {
+      const float x = xyz[3 * a], y = xyz[3 * a + 1], z = xyz[3 * a + 2], R = radius[a];
+      const float p = height ? height[a] : 1.f;
+      ok &= std::isfinite(x) && std::isfinite(y) && std::isfinite(z) && R > 0 && std::isfinite(R) && p > 0 &&
+            std::isfinite(p);
+      atom[a] = make_float4(x, y, z, 0.f);
+      rad[a] = R;
+      if (height) hgt[a] = p;
     }
     if (!ok) {
 #pragma omp critical
       { if (bad_mol < 0 || m < bad_mol) bad_mol = m; }
-      continue;
     }
-    s->h_Z[m] = Z;
-    Zs[m] = Z;
-    build_alias(n, v, thr + a0, alias + a0);
   }
   if (bad_mol >= 0) {
     set_error("shape_set_load: molecule %d has a non-finite or non-positive coordinate, radius or height", bad_mol);
@@ -374,9 +449,9 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
   }
   order_by_size(offsets, n_mol, reinterpret_cast<int32_t*>(hb + L.order));
   std::memcpy(hb + L.off, offsets, sizeof(int32_t) * (n_mol + 1));
-  // allocate and upload on the library's copy stream, then order the
-  // caller's stream after the upload: the copy overlaps kernels already
-  // queued on the caller's stream
+  // allocate and upload on the library's copy stream, prepare on the device
+  // there, then order the caller's stream after both: the copy overlaps
+  // kernels already queued on the caller's stream
   cudaStream_t st = (cudaStream_t)stream, cs = nullptr;
   rc = copy_stream(s->device, &cs);
   if (rc) { delete s; return rc; }
@@ -394,7 +469,54 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
   s->Z = reinterpret_cast<double*>(db + L.Z);
   s->order = reinterpret_cast<int32_t*>(db + L.order);
   s->frame = reinterpret_cast<float*>(db + L.frame);
-  e = cudaMemcpyAsync(db, hb, L.frame, cudaMemcpyHostToDevice, cs);  // the frames (last) are computed on demand
+  // the heights travel in the threshold slots, read before the thresholds
+  // are written
+  e = cudaMemcpyAsync(db, hb, height ? L.aux : L.thr, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess && n_mol > 0) {
+    PrepArgs pa{};
+    pa.atom = s->atom;
+    pa.aux = s->aux;
+    pa.radius = s->radius;
+    pa.height = height ? reinterpret_cast<const float*>(s->thr) : nullptr;
+    pa.thr = s->thr;
+    pa.alias = s->alias;
+    pa.Z = s->Z;
+    pa.off = s->off;
+    pa.order = s->order;
+    pa.n_mol = n_mol;
+    pa.c_alpha = ca;
+    pa.p_default = 2.0 * std::sqrt(2.0);
+    pa.log2p_default = (float)std::log2(pa.p_default);
+    // radius classes from the distinct radii of a strided sample of 4096
+    // atoms (the first kRadiusClasses found); a radius outside the table is
+    // evaluated by the kernel, so the sample decides speed, not values
+    uint32_t cls[kRadiusClasses];
+    int n_cls = 0;
+    const int64_t stride = std::max<int64_t>(1, n_atoms / 4096);
+    for (int64_t at = 0; at < n_atoms && n_cls < kRadiusClasses; at += stride) {
+      uint32_t bits;
+      std::memcpy(&bits, &radius[at], sizeof bits);
+      int k = 0;
+      while (k < n_cls && cls[k] != bits) ++k;
+      if (k == n_cls) cls[n_cls++] = bits;
+    }
+    std::sort(cls, cls + n_cls);
+    pa.n_cls = n_cls;
+    for (int k = 0; k < n_cls; ++k) {
+      float Rf;
+      std::memcpy(&Rf, &cls[k], sizeof Rf);
+      const double R = Rf;
+      const double alpha = ca / (R * R);
+      pa.cls_bits[k] = cls[k];
+      pa.cls_t[k] = kPi / alpha;
+      pa.cls_sqrt_t[k] = std::sqrt(pa.cls_t[k]);
+      pa.cls_alpha[k] = (float)alpha;
+      pa.cls_sigma[k] = (float)(1.0 / std::sqrt(2.0 * alpha));
+    }
+    const int64_t blocks = std::min<int64_t>((n_mol + kPrepWarps - 1) / kPrepWarps, 148 * 16);
+    set_prep_kernel<<<(unsigned)blocks, 32 * kPrepWarps, 0, cs>>>(pa);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaEventRecord(sb->done, cs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, sb->done, 0);
   if (e != cudaSuccess) {
@@ -445,9 +567,9 @@ extern "C" int shape_set_info(shp_set s, int32_t* n_mol, int64_t* n_atoms, int32
 extern "C" int shape_set_tables(shp_set s, double* Z, uint32_t* thr, uint8_t* alias) {
   clear_error();
   if (!s) { set_error("shape_set_tables: NULL set"); return SHP_EINVAL; }
-  if (Z && s->n_mol) std::memcpy(Z, s->h_Z.data(), sizeof(double) * s->n_mol);
-  if ((thr || alias) && s->n_atoms) {
+  if ((Z || thr || alias) && s->n_mol) {
     SHP_CUDA(cudaDeviceSynchronize());
+    if (Z) SHP_CUDA(cudaMemcpy(Z, s->Z, sizeof(double) * s->n_mol, cudaMemcpyDeviceToHost));
     if (thr) SHP_CUDA(cudaMemcpy(thr, s->thr, sizeof(uint32_t) * s->n_atoms, cudaMemcpyDeviceToHost));
     if (alias) SHP_CUDA(cudaMemcpy(alias, s->alias, s->n_atoms, cudaMemcpyDeviceToHost));
   }

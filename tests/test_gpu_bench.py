@@ -74,7 +74,8 @@ def test_bench_json_line_small():
 
 @pytest.mark.parametrize("case, keys", [("align", ("union_crn_ms", "fo_closed_ms")),
                                         ("prefilter", ("fo_tanimoto_ms", "select_ms")),
-                                        ("self", ("self_ms",)), ("train", ("epoch_ms", "atoms"))])
+                                        ("self", ("self_ms",)), ("train", ("epoch_ms", "atoms")),
+                                        ("load", ("load_ms", "host_ms"))])
 def test_profile_cases(case, keys):
     """The small standalone cases that the profiler captures run and report
     their timings (one JSON line)."""

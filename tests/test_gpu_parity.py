@@ -56,6 +56,36 @@ def test_tables_bit_exact(ragged):
             np.testing.assert_array_equal(al[lo:hi], t["alias"])
 
 
+def test_tables_with_heights_and_many_radii():
+    """The loader's two paths of per-atom terms: a set with more distinct
+    radii than its radius classes (the terms of most atoms evaluated on the
+    device, the rest looked up) and a set of a few radii (all looked up per
+    class), both with given heights: integer tables and Z bit-exact,
+    estimates at the oracle's values."""
+    rng = np.random.default_rng(11)
+    base = synth.centre(synth.generate(303, [7, 40, 64, 1, 23]))
+    height = rng.uniform(1.5, 3.2, base.n_atoms).astype(np.float32)
+    many = MolSet(base.xyz, rng.uniform(1.2, 2.0, base.n_atoms).astype(np.float32), base.offsets, base.elem,
+                  height)
+    few = MolSet(base.xyz, base.radius, base.offsets, base.elem, height)
+    assert len(np.unique(many.radius)) > 16 and len(np.unique(few.radius)) <= 16
+    sets = [(ms, shp.shape_set_load(ms)) for ms in (many, few)]
+    for ms, S in sets:
+        Z, thr, al = S.tables()
+        for i in range(ms.n_mol):
+            t = O.mol_tables(ms, i)
+            lo, hi = ms.offsets[i], ms.offsets[i + 1]
+            assert Z[i] == t["Z"]
+            np.testing.assert_array_equal(thr[lo:hi], t["thr"])
+            np.testing.assert_array_equal(al[lo:hi], t["alias"])
+    ia, ib = np.meshgrid(np.arange(many.n_mol), np.arange(few.n_mol), indexing="ij")
+    ia, ib = ia.ravel().astype(np.int32), ib.ravel().astype(np.int32)
+    est, se = shp.overlap_estimate(sets[0][1], ia, sets[1][1], ib, seed=5, n_samples=1024, flags=shp.SYMMETRIC)
+    e_o, s_o = O.overlap_estimate(many, ia, few, ib, seed=5, n=1024, flags=O.SYMMETRIC)
+    assert_close(est.cpu().numpy(), e_o, what="est")
+    assert_close(se.cpu().numpy(), s_o, what="se")
+
+
 @pytest.mark.parametrize("flags", [0, shp.SYMMETRIC, shp.SYMMETRIC | shp.ANTITHETIC])
 def test_single_pair_parity(pair, flags):
     a, b, SA, SB = pair
