@@ -29,8 +29,8 @@ int cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? SHP_ENOMEM : SHP_ECUDA;
 }
 
-// Per-molecule preparation on the device, one warp per molecule (molecules
-// taken in size order, so neighbouring warps do similar work). Per atom, from
+// Per-molecule preparation on the device (molecules taken in size order, so
+// the molecules a warp handles together have similar sizes). Per atom, from
 // the radius R and height p (FP64, IEEE-rounded operations throughout, so the
 // values do not depend on the compiler's contraction choices):
 //   alpha = c_alpha / R^2,  t = pi / alpha,  v = p t sqrt(t)   (Gaussian volume)
@@ -70,88 +70,116 @@ struct PrepArgs {
 constexpr int kPrepWarps = 8;
 
 struct PrepWarp {
-  double v[SHP_MAX_ATOMS];
   unsigned long long mass[SHP_MAX_ATOMS];
   uint8_t small[SHP_MAX_ATOMS], large[SHP_MAX_ATOMS];
 };
 
+// The terms of atom radius Rf that depend on R alone: from its class when
+// the radius has one, else evaluated (FP64, IEEE-rounded).
+__device__ __forceinline__ void radius_terms(const PrepArgs& a, const uint32_t* cls_bits, float Rf, double& t,
+                                             double& sqrt_t, float& alpha_f, float& sigma_f) {
+  const uint32_t bits = __float_as_uint(Rf);
+  int c = 0;
+  for (int step = kRadiusClasses / 2; step; step >>= 1)
+    if (c + step < a.n_cls && cls_bits[c + step] <= bits) c += step;
+  if (a.n_cls && cls_bits[c] == bits) {
+    t = a.cls_t[c];
+    sqrt_t = a.cls_sqrt_t[c];
+    alpha_f = a.cls_alpha[c];
+    sigma_f = a.cls_sigma[c];
+  } else {
+    const double kPi = 3.14159265358979323846;
+    const double R = Rf;
+    const double alpha = __ddiv_rn(a.c_alpha, __dmul_rn(R, R));
+    t = __ddiv_rn(kPi, alpha);
+    sqrt_t = __dsqrt_rn(t);
+    alpha_f = (float)alpha;
+    sigma_f = (float)__ddiv_rn(1.0, __dsqrt_rn(__dmul_rn(2.0, alpha)));
+  }
+}
+
+// A warp takes 32 molecules at a time (consecutive in size order). Phase 1,
+// per molecule with lanes over atoms: the volumes v_i, parked in the atoms'
+// aux slots (8 B, a double), and alpha. Phase 2, lane j: Z of molecule j
+// in atom order (a sequential FP64 sum, so every lane carries one). Phase 3,
+// per molecule: the masses, then sigma and log2 p over the parked volumes,
+// then the alias table (lane 0).
 __global__ void __launch_bounds__(32 * kPrepWarps) set_prep_kernel(const PrepArgs a) {
   __shared__ PrepWarp W[kPrepWarps];
   __shared__ uint32_t cls_bits[kRadiusClasses];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   PrepWarp& w = W[warp];
   const unsigned long long kOne = 1ull << 32;
-  const double kPi = 3.14159265358979323846;
+  const unsigned kAll = 0xffffffffu;
+  double* vol = reinterpret_cast<double*>(a.aux);
   if (threadIdx.x < kRadiusClasses) cls_bits[threadIdx.x] = a.cls_bits[threadIdx.x];
   __syncthreads();
-  for (int64_t k = (int64_t)blockIdx.x * kPrepWarps + warp; k < a.n_mol; k += (int64_t)gridDim.x * kPrepWarps) {
-    const int32_t m = a.order[k];
-    const int32_t a0 = a.off[m], n = a.off[m + 1] - a0;
-    for (int i = lane; i < n; i += 32) {
-      const float Rf = a.radius[a0 + i];
-      const double p = a.height ? (double)a.height[a0 + i] : a.p_default;
-      const uint32_t bits = __float_as_uint(Rf);
-      int c = 0;
-      for (int step = kRadiusClasses / 2; step; step >>= 1)
-        if (c + step < a.n_cls && cls_bits[c + step] <= bits) c += step;
-      double t, sqrt_t;
-      float alpha_f, sigma_f;
-      if (a.n_cls && cls_bits[c] == bits) {
-        t = a.cls_t[c];
-        sqrt_t = a.cls_sqrt_t[c];
-        alpha_f = a.cls_alpha[c];
-        sigma_f = a.cls_sigma[c];
-      } else {
-        const double R = Rf;
-        const double alpha = __ddiv_rn(a.c_alpha, __dmul_rn(R, R));
-        t = __ddiv_rn(kPi, alpha);
-        sqrt_t = __dsqrt_rn(t);
-        alpha_f = (float)alpha;
-        sigma_f = (float)__ddiv_rn(1.0, __dsqrt_rn(__dmul_rn(2.0, alpha)));
+  const int64_t n_groups = ((int64_t)a.n_mol + 31) / 32;
+  for (int64_t g = (int64_t)blockIdx.x * kPrepWarps + warp; g < n_groups; g += (int64_t)gridDim.x * kPrepWarps) {
+    const int64_t k0 = 32 * g;
+    const int nm = (int)min((int64_t)32, (int64_t)a.n_mol - k0);
+    int32_t my_m = 0, my_a0 = 0, my_n = 0;
+    if (lane < nm) {
+      my_m = a.order[k0 + lane];
+      my_a0 = a.off[my_m];
+      my_n = a.off[my_m + 1] - my_a0;
+    }
+    for (int j = 0; j < nm; ++j) {
+      const int32_t a0 = __shfl_sync(kAll, my_a0, j), n = __shfl_sync(kAll, my_n, j);
+      for (int i = lane; i < n; i += 32) {
+        const double p = a.height ? (double)a.height[a0 + i] : a.p_default;
+        double t, sqrt_t;
+        float alpha_f, sigma_f;
+        radius_terms(a, cls_bits, a.radius[a0 + i], t, sqrt_t, alpha_f, sigma_f);
+        vol[a0 + i] = __dmul_rn(__dmul_rn(p, t), sqrt_t);
+        reinterpret_cast<float*>(a.atom + a0 + i)[3] = alpha_f;
       }
-      w.v[i] = __dmul_rn(__dmul_rn(p, t), sqrt_t);
-      reinterpret_cast<float*>(a.atom + a0 + i)[3] = alpha_f;
-      a.aux[a0 + i] = make_float2(sigma_f, a.height ? (float)log2(p) : a.log2p_default);
     }
     __syncwarp();
-    double Z = 0.0;
-    if (lane == 0) {
-      for (int i = 0; i < n; ++i) Z = __dadd_rn(Z, w.v[i]);
-      a.Z[m] = Z;
-    }
-    Z = __shfl_sync(0xffffffffu, Z, 0);
-    const double scale = __dmul_rn((double)n, 4294967296.0);
-    unsigned long long sum = 0;
-    for (int i = lane; i < n; i += 32) {
-      // truncation = floor: 0 <= (v_i / Z) n 2^32 < 2^38
-      const unsigned long long M = (unsigned long long)(long long)__dmul_rn(__ddiv_rn(w.v[i], Z), scale);
-      w.mass[i] = M;
-      sum += M;
-    }
-    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    double my_Z = 0.0;
+    for (int i = 0; i < my_n; ++i) my_Z = __dadd_rn(my_Z, vol[my_a0 + i]);
+    if (lane < nm) a.Z[my_m] = my_Z;
     __syncwarp();
-    if (lane == 0) {
-      unsigned long long* mass = w.mass;
-      mass[n - 1] += (unsigned long long)n * kOne - sum;
-      uint32_t* thr = a.thr + a0;
-      uint8_t* alias = a.alias + a0;
-      int sh = 0, st = 0, lh = 0, lt = 0;
-      for (int i = 0; i < n; ++i) (mass[i] < kOne ? w.small[st++] : w.large[lt++]) = (uint8_t)i;
-      while (sh < st && lh < lt) {
-        const int sm = w.small[sh++];
-        const int lg = w.large[lh];
-        thr[sm] = (uint32_t)mass[sm];
-        alias[sm] = (uint8_t)lg;
-        mass[lg] -= kOne - mass[sm];
-        if (mass[lg] < kOne) {
-          ++lh;
-          w.small[st++] = (uint8_t)lg;
+    for (int j = 0; j < nm; ++j) {
+      const int32_t a0 = __shfl_sync(kAll, my_a0, j), n = __shfl_sync(kAll, my_n, j);
+      const double Z = __shfl_sync(kAll, my_Z, j);
+      const double scale = __dmul_rn((double)n, 4294967296.0);
+      unsigned long long sum = 0;
+      for (int i = lane; i < n; i += 32) {
+        // truncation = floor: 0 <= (v_i / Z) n 2^32 < 2^38
+        const unsigned long long M = (unsigned long long)(long long)__dmul_rn(__ddiv_rn(vol[a0 + i], Z), scale);
+        w.mass[i] = M;
+        sum += M;
+        double t, sqrt_t;
+        float alpha_f, sigma_f;
+        radius_terms(a, cls_bits, a.radius[a0 + i], t, sqrt_t, alpha_f, sigma_f);
+        a.aux[a0 + i] = make_float2(sigma_f, a.height ? (float)log2((double)a.height[a0 + i]) : a.log2p_default);
+      }
+      for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o);
+      __syncwarp();
+      if (lane == 0) {
+        unsigned long long* mass = w.mass;
+        mass[n - 1] += (unsigned long long)n * kOne - sum;
+        uint32_t* thr = a.thr + a0;  // overwrites this molecule's heights, all read above
+        uint8_t* alias = a.alias + a0;
+        int sh = 0, st = 0, lh = 0, lt = 0;
+        for (int i = 0; i < n; ++i) (mass[i] < kOne ? w.small[st++] : w.large[lt++]) = (uint8_t)i;
+        while (sh < st && lh < lt) {
+          const int sm = w.small[sh++];
+          const int lg = w.large[lh];
+          thr[sm] = (uint32_t)mass[sm];
+          alias[sm] = (uint8_t)lg;
+          mass[lg] -= kOne - mass[sm];
+          if (mass[lg] < kOne) {
+            ++lh;
+            w.small[st++] = (uint8_t)lg;
+          }
         }
+        for (; sh < st; ++sh) { thr[w.small[sh]] = 0xFFFFFFFFu; alias[w.small[sh]] = w.small[sh]; }
+        for (; lh < lt; ++lh) { thr[w.large[lh]] = 0xFFFFFFFFu; alias[w.large[lh]] = w.large[lh]; }
       }
-      for (; sh < st; ++sh) { thr[w.small[sh]] = 0xFFFFFFFFu; alias[w.small[sh]] = w.small[sh]; }
-      for (; lh < lt; ++lh) { thr[w.large[lh]] = 0xFFFFFFFFu; alias[w.large[lh]] = w.large[lh]; }
+      __syncwarp();
     }
-    __syncwarp();
   }
 }
 
@@ -513,7 +541,8 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
       pa.cls_alpha[k] = (float)alpha;
       pa.cls_sigma[k] = (float)(1.0 / std::sqrt(2.0 * alpha));
     }
-    const int64_t blocks = std::min<int64_t>((n_mol + kPrepWarps - 1) / kPrepWarps, 148 * 16);
+    const int64_t groups = (n_mol + 31) / 32;
+    const int64_t blocks = std::min<int64_t>((groups + kPrepWarps - 1) / kPrepWarps, 148 * 16);
     set_prep_kernel<<<(unsigned)blocks, 32 * kPrepWarps, 0, cs>>>(pa);
     e = cudaGetLastError();
   }

@@ -257,6 +257,27 @@ def test_edge_cases(ragged):
     assert out[0].numel() == 0
 
 
+@pytest.mark.parametrize("field, value", [("radius", 0.0), ("radius", np.inf), ("height", -1.0),
+                                          ("height", np.nan), ("xyz", np.inf)])
+def test_load_rejects_bad_values_naming_the_first_bad_molecule(field, value):
+    """Every non-finite or non-positive input is rejected with SHP_EINVAL
+    before any device work, naming the lowest bad molecule although the
+    host validates molecules in parallel."""
+    base = synth.generate(4, [5, 6, 7, 8])
+    ms = MolSet(base.xyz.copy(), base.radius.copy(), base.offsets, base.elem,
+                np.full(base.n_atoms, 2.0, np.float32))
+    arr = getattr(ms, field)
+    for m in (3, 1):
+        a = base.offsets[m] + 1
+        if field == "xyz":
+            arr[a, 2] = value
+        else:
+            arr[a] = value
+    with pytest.raises(shp.ShapeError) as ex:
+        shp.shape_set_load(ms)
+    assert ex.value.status == -1 and "molecule 1 " in str(ex.value)
+
+
 def test_pipelined_set_loads_match_sequential():
     """Database chunks loaded back to back while earlier screens still run
     (the staging ring is reused, sets are freed in stream order) give the same
