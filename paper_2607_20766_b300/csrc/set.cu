@@ -68,6 +68,7 @@ struct PrepArgs {
 };
 
 constexpr int kPrepWarps = 8;
+constexpr int kPrepGroup = 16;  // molecules a warp takes at a time (<= 32)
 
 struct PrepWarp {
   unsigned long long mass[SHP_MAX_ATOMS];
@@ -98,12 +99,13 @@ __device__ __forceinline__ void radius_terms(const PrepArgs& a, const uint32_t* 
   }
 }
 
-// A warp takes 32 molecules at a time (consecutive in size order). Phase 1,
-// per molecule with lanes over atoms: the volumes v_i, parked in the atoms'
-// aux slots (8 B, a double), and alpha. Phase 2, lane j: Z of molecule j
-// in atom order (a sequential FP64 sum, so every lane carries one). Phase 3,
-// per molecule: the masses, then sigma and log2 p over the parked volumes,
-// then the alias table (lane 0).
+// A warp takes kPrepGroup molecules at a time (consecutive in size order).
+// Phase 1, per molecule with lanes over atoms: the volumes v_i, parked in the
+// atoms' aux slots (8 B, a double), and alpha. Phase 2, lane j: Z of molecule
+// j in atom order (a sequential FP64 sum, one per lane: on one lane per
+// molecule each addition would still take a whole warp instruction of the
+// slow FP64 pipe). Phase 3, per molecule: the masses, then sigma and log2 p
+// over the parked volumes, then the alias table (lane 0).
 __global__ void __launch_bounds__(32 * kPrepWarps) set_prep_kernel(const PrepArgs a) {
   __shared__ PrepWarp W[kPrepWarps];
   __shared__ uint32_t cls_bits[kRadiusClasses];
@@ -114,10 +116,10 @@ __global__ void __launch_bounds__(32 * kPrepWarps) set_prep_kernel(const PrepArg
   double* vol = reinterpret_cast<double*>(a.aux);
   if (threadIdx.x < kRadiusClasses) cls_bits[threadIdx.x] = a.cls_bits[threadIdx.x];
   __syncthreads();
-  const int64_t n_groups = ((int64_t)a.n_mol + 31) / 32;
+  const int64_t n_groups = ((int64_t)a.n_mol + kPrepGroup - 1) / kPrepGroup;
   for (int64_t g = (int64_t)blockIdx.x * kPrepWarps + warp; g < n_groups; g += (int64_t)gridDim.x * kPrepWarps) {
-    const int64_t k0 = 32 * g;
-    const int nm = (int)min((int64_t)32, (int64_t)a.n_mol - k0);
+    const int64_t k0 = (int64_t)kPrepGroup * g;
+    const int nm = (int)min((int64_t)kPrepGroup, (int64_t)a.n_mol - k0);
     int32_t my_m = 0, my_a0 = 0, my_n = 0;
     if (lane < nm) {
       my_m = a.order[k0 + lane];
@@ -541,7 +543,7 @@ extern "C" int shape_set_load(const float* xyz, const float* radius, const float
       pa.cls_alpha[k] = (float)alpha;
       pa.cls_sigma[k] = (float)(1.0 / std::sqrt(2.0 * alpha));
     }
-    const int64_t groups = (n_mol + 31) / 32;
+    const int64_t groups = (n_mol + kPrepGroup - 1) / kPrepGroup;
     const int64_t blocks = std::min<int64_t>((groups + kPrepWarps - 1) / kPrepWarps, 148 * 16);
     set_prep_kernel<<<(unsigned)blocks, 32 * kPrepWarps, 0, cs>>>(pa);
     e = cudaGetLastError();
