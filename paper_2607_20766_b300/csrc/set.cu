@@ -46,7 +46,7 @@ constexpr int kRadiusClasses = 16;
 
 struct PrepArgs {
   float4* atom;          // in: x, y, z; out: w = alpha
-  float2* aux;           // out: sigma, log2 p
+  float2* aux;           // out: sigma, log2 p (the volumes, as doubles, between phases)
   const float* radius;   // [n_atoms]
   const float* height;   // [n_atoms] heights staged in the threshold slots, or NULL: p_default
   uint32_t* thr;         // out: alias thresholds (after the heights are read)
